@@ -1,0 +1,303 @@
+"""Benchmark of the Monte Carlo transport hot path on GB300.
+
+Metric: superphotons tracked per second (emitted + scattered, as counted in the paper's
+throughput figure), plain FP64 form, on the scattering synchrotron sphere: Schwarzschild
+sphere of radius 10 GM/c^2, Theta_e = 4, B = 10 G, 1024 x 128 grid, Thomson depth
+tau_T in {1e-4, 1e-3, 1e-2, 1e-1}, N_s = 1e7 per run, seeds 1-4.  One step = one whole
+mc_run (weights, zone counts, emission, transport of every generation, binning) of one
+(tau_T, seed) pair, cycling through the 16 pairs.  Inputs are synthetic (seeded), resident in
+HBM before the timed region; L2 is flushed (256 MiB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) each rank runs its own independent jobs (seed offset by rank; no
+collective on the data path): weak scaling, value = all ranks' superphotons / slowest rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "superphotons tracked/sec on 1 GB300: plain FP64 vs batched+surrogate at <=1% spectrum err"
+UNIT = "superphotons/s"
+TAUS = (1e-4, 1e-3, 1e-2, 1e-1)
+N_S = 1e7
+WORKLOAD = ("scattering synchrotron sphere, Schwarzschild a=0, R=10 GM/c^2, Theta_e=4, B=10 G, "
+            "tau_T in {1e-4,1e-3,1e-2,1e-1}, grid 1024x128, N_s=1e7 per run, seeds 1-4, 200 log bins 1e8-1e24 Hz")
+
+# Algorithmic FP64 operations (add/mul/div/sqrt = 1, FMA = 2, each transcendental = 1), hand-counted
+# from the formulas of the FP64 path: per geodesic step outside the Verlet predictor loop (step size,
+# position update, metric and its x1/x2 derivatives, fluid interpolation, plasma state, j_nu, B_nu,
+# sigma_h lookup, optical depths, weight update), per predictor iteration (acceleration contraction
+# and convergence test), per emission and per scattering event.
+FLOP_STEP = 460.0
+FLOP_ITER = 110.0
+FLOP_EMIT = 2000.0
+FLOP_EVENT = 1500.0
+GEN_LAUNCHES = 7          # zone prep, weight partials, weight final, counts, 3 scan kernels
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(p, g, seed, budget_s, nthreads, first_n=None):
+    """Times the CPU oracle as it stands on a bounded sample (the first uids of the job)."""
+    import oracle
+    om = oracle.Model(p, g)
+    tot = om.prepare(N_S, seed)
+    n = first_n or 256
+    while True:
+        t = time.perf_counter()
+        r = om.run(0, min(n, tot), nthreads=nthreads)
+        dt = time.perf_counter() - t
+        if first_n or dt > 0.3 * budget_s or n >= tot:
+            break
+        n = int(n * min(8.0, max(2.0, 0.5 * budget_s / max(dt, 1e-3))))
+    st = r["stats"]
+    units = st["n_emit"] + st["n_child"]
+    return units / dt, units, dt, min(n, tot)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2602_13198_gb300 import synth
+
+    cores = os.cpu_count() or 1
+    if args.impl == "reference":
+        # the reference arm is the CPU oracle (there is no reference implementation to install):
+        # rank 0 times it on the host cores, a bounded sample of the same workload per step
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        models = [synth.scattering_sphere(t) for t in TAUS]
+        for w in range(args.warmup):
+            p, g = models[w % 4]
+            oracle_rate(p, g, 1, 2.0, cores, first_n=64)
+        units, secs = 0, 0.0
+        samples = []
+        for k in range(args.steps):
+            p, g = models[k % 4]
+            seed = 1 + (k // 4) % 4
+            rate, u, dt, n = oracle_rate(p, g, seed, 12.0, cores)
+            units += u
+            secs += dt
+            samples.append(n)
+        v = units / secs
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "n_s_per_run": N_S},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": "first %s primaries (and their scattered descendants) of each step's job" % samples},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2602_13198_gb300 import build, mc
+    build.build()
+    dev = torch.cuda.current_device()
+    models, ctxs = [], []
+    for t in TAUS:
+        p, g = synth.scattering_sphere(t)
+        m = mc.Model(p, device=dev, precision=args.precision)
+        m.set_grid(g)
+        models.append((p, g))
+        ctxs.append(m)
+    fp64_peak = mc.fma_peak(dev, True)
+    fp32_peak = mc.fma_peak(dev, False)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one(k, ctx_seed_offset=0):
+        i = k % 4
+        seed = 1 + (k // 4) % 4 + 1000 * rank + ctx_seed_offset
+        return ctxs[i].run(N_S, seed, stream=stream)
+
+    for w in range(args.warmup):
+        one(w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        stats.append(one(k))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    units = sum(s["n_emit"] + s["n_child"] for s in stats)
+    t_transport = sum(s["transport_ms"] for s in stats) / 1e3
+    launches = sum(s["transport_launches"] for s in stats)
+    flops = sum(FLOP_STEP * s["n_steps"] + FLOP_ITER * s["n_iters"] + FLOP_EMIT * s["n_emit"] + FLOP_EVENT * s["n_events"]
+                for s in stats)
+    if dist:
+        t = torch.tensor([dev_s, float(units)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        dev_s_max, units_all = float(tmax[0]), float(t[1])
+    else:
+        dev_s_max, units_all = dev_s, float(units)
+    value = units_all / dev_s_max
+
+    # end to end through the public API with host buffers: grid H2D each step, spectrum D2H
+    import numpy as np
+    host_prims = []
+    for p, g in models:
+        hp = torch.from_numpy(np.ascontiguousarray(g["prim"])).pin_memory()
+        host_prims.append(hp)
+    e2e_units, t_e2e = 0, 0.0
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        i = k % 4
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctxs[i].set_grid(models[i][1], prim=host_prims[i].numpy())
+        s = ctxs[i].run(N_S, 1 + (k // 4) % 4 + 1000 * rank, stream=stream)
+        spec = ctxs[i].spectrum()
+        t_e2e += time.perf_counter() - t0
+        e2e_units += s["n_emit"] + s["n_child"]
+    h2d = int(host_prims[0].numel() * 8)
+    d2h = int(ctxs[0].n_incl * ctxs[0].n_bins * 3 * 8)
+    if dist:
+        t = torch.tensor([t_e2e, float(e2e_units)], dtype=torch.float64, device="cuda")
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_value = float(t[1]) / float(tm[0])
+    else:
+        e2e_value = e2e_units / t_e2e
+
+    achieved = flops / t_transport / 1e12
+    peak = fp64_peak / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "k_transport<fp64> (persistent, one launch per scattering generation)",
+                "peak_source": "measured: project FP64 FMA-chain microbenchmark on this GPU (mc_fma_peak)",
+                "fp32_peak_tflops": fp32_peak / 1e12,
+                "algorithmic_flops": flops, "transport_s": t_transport}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        p, g = models[2]
+        rate, u, dt, n = oracle_rate(p, g, 1, 15.0, cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "first %d primaries (+ scattered descendants, %d superphotons) of the tau_T=1e-2 seed-1 job, "
+                         "%.1f s" % (n, u, dt)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "form": "plain FP64" if args.precision == "fp64" else "mixed FP64/FP32",
+                           "n_s_per_run": N_S, "grid": [1024, 128, 1], "l2": "flushed (256 MiB write) between timed steps",
+                           "parallelism": "replicas (independent jobs per rank)" if world > 1 else "single GPU"},
+                "clocks": clocks, "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                                          "d2h_bytes_per_step": d2h},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "gpu_launches": int(launches + GEN_LAUNCHES * args.steps),
+                "detail": {"superphotons": units, "scattered": sum(s["n_child"] for s in stats),
+                           "steps_per_superphoton": sum(s["n_steps"] for s in stats) / max(units, 1),
+                           "iters_per_step": sum(s["n_iters"] for s in stats) / max(1, sum(s["n_steps"] for s in stats)),
+                           "step_ms": step_ms, "wall_s": t_wall,
+                           "generate_ms": [s["generate_ms"] for s in stats],
+                           "scatterings_per_s": sum(s["n_events"] for s in stats) / dev_s}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

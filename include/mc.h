@@ -1,0 +1,194 @@
+/* mc.h -- C ABI of the GB300 (sm_103a) Monte Carlo radiative-transfer hot path.
+ *
+ * The library computes the emergent spectrum nu L_nu of a relativistic plasma by the
+ * superphoton Monte Carlo method of GPUmonty (arXiv 2602.13198): superphoton generation
+ * per grid zone from the thermal synchrotron emissivity (sections 2.1-2.3), transport
+ * along Kerr-Schild null geodesics by iterated velocity Verlet (section 2.4) with
+ * synchrotron absorption (sections 2.5-2.6), biased Compton scattering off thermal
+ * electrons (section 2.7), and binning of escaping superphotons (section 3).
+ *
+ * Conventions (all entry points):
+ *   - return MC_OK (0) on success, a negative MC_ERR_* code on failure; no exception
+ *     or longjmp crosses the boundary; mc_last_error() gives a message;
+ *   - pointers are plain host or device pointers as stated per argument; sizes are in
+ *     elements unless stated; nothing is retained beyond the call unless stated;
+ *   - a context is not thread-safe; use one context per host thread;
+ *   - device memory is obtained through the caller's allocator callbacks when given
+ *     (PyTorch's caching allocator from Python), else cudaMalloc.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_OK 0
+#define MC_ERR_INVALID_ARG (-1)
+#define MC_ERR_NO_DEVICE (-2)
+#define MC_ERR_OOM (-3)
+#define MC_ERR_TIMEOUT (-4)
+#define MC_ERR_QUEUE_OVERFLOW (-5)
+#define MC_ERR_NAN_INPUT (-6)
+#define MC_ERR_SIZE (-7)
+#define MC_ERR_STATE (-8)
+#define MC_ERR_CUDA (-9)
+
+enum { MC_PREC_FP64 = 0, MC_PREC_MIXED = 1 };
+enum { MC_DTYPE_F64 = 0, MC_DTYPE_F32 = 1 };
+enum { MC_LOC_HOST = 0, MC_LOC_DEVICE = 1 };
+enum { MC_BIAS_CONST = 0, MC_BIAS_GENERATION = 1, MC_BIAS_THETAE2 = 2 };
+
+typedef struct mc_ctx mc_ctx;
+
+/* Device allocator callbacks: alloc returns a device pointer aligned to 256 bytes, or NULL. */
+typedef void *(*mc_alloc_fn)(size_t bytes, void *user);
+typedef void (*mc_free_fn)(void *ptr, void *user);
+
+/* Model parameters: the problem statement of the paper (metric and units, section 4.3;
+ * emission band and weight floor, sections 2.1-2.3 and 4.3; Verlet tolerance, section
+ * 2.4; bias b >= 1, section 2.7; record radius and spectrum bins, sections 4.1-4.3). */
+typedef struct mc_model_params {
+  double a;            /* black-hole spin a/M */
+  double mass;         /* 1: Kerr-Schild with M = 1 (code units); 0: flat spacetime */
+  double hslope;       /* modified Kerr-Schild theta(x2) = pi x2 + (1-hslope)/2 sin(2 pi x2) */
+  double L_unit;       /* code length [cm] (GM/c^2 for mass 1) */
+  double M_unit;       /* mass unit [g]: rho_unit = M_unit / L_unit^3 */
+  double R_high, R_low;/* electron temperature model T_i/T_e = (R_high beta^2 + R_low)/(1 + beta^2) */
+  double gam;          /* adiabatic index used by the temperature model */
+  double thetae_min;   /* no synchrotron emission below this Theta_e */
+  double thetae_max;   /* Theta_e ceiling */
+  double nu_min, nu_max;   /* emission band [Hz] */
+  double w_min;        /* superphoton weight floor */
+  double n_s;          /* unused by mc_run (pass N_s there); kept for layout symmetry */
+  double eps_geo;      /* step control: each internal coordinate moves at most eps_geo of its scale */
+  double verlet_tol;   /* relative error bound of the Verlet predictor loop (paper: 1e-3) */
+  double r_record;     /* record superphotons at r >= r_record [code lengths] */
+  double dh;           /* capture at r <= r_h (1 + dh) */
+  double bias_p0;      /* bias parameter; see bias_mode */
+  double lnu_lo, lnu_hi;   /* spectrum range, log10(nu/Hz) */
+  double roulette_w, roulette_p;  /* Russian roulette when w < roulette_w * w_birth, survival roulette_p */
+  int64_t max_steps;   /* drop a superphoton after this many steps */
+  int32_t n_nu;        /* weight-table nodes in ln nu (>= 2) */
+  int32_t verlet_maxit;/* cap on Verlet predictor iterations */
+  int32_t bias_mode;   /* MC_BIAS_CONST: b = max(1,p0); _GENERATION: max(1, p0 (n_sc+1)^2); _THETAE2: max(1, p0 Theta_e^2) */
+  int32_t n_sc_max;    /* largest scattering generation that is produced */
+  int32_t n_bins, n_incl;  /* spectrum bins in log nu, inclination bins over [0, pi/2] (hemispheres folded) */
+  int32_t k2_mode;     /* 0: exact K2(1/Theta_e); 1: K2 ~ 2 Theta_e^2 (section 2.2) */
+  int32_t scatter;     /* 0: Compton scattering off */
+  /* --- execution (not part of the physics) --- */
+  int32_t precision;   /* MC_PREC_FP64: everything FP64; MC_PREC_MIXED: FP64 geodesics, FP32 plasma coefficients */
+  int32_t surrogate;   /* 0: closed forms and tables; 1: MLP surrogate for the coefficients (needs weights) */
+  int32_t block;       /* threads per CTA of the transport kernel (0: default 128) */
+  int32_t ctas_per_sm; /* resident CTAs per SM for the persistent launch (0: occupancy maximum) */
+  int32_t device;      /* CUDA device ordinal */
+  int32_t pad0;
+  mc_alloc_fn alloc;   /* optional device allocator (NULL: cudaMalloc) */
+  mc_free_fn free;
+  void *alloc_user;
+} mc_model_params;
+
+/* Fluid grid: primitives rho, u, B^1..3, U^1..3 (U^i: 4-velocity relative to the normal
+ * observer; B^i: field 3-vector; modified Kerr-Schild internal coordinates x1 = ln r,
+ * x2 in [0,1], x3 = phi), laid out [8][n1*n2*n3] with zone index (i*n2 + j)*n3 + k. */
+typedef struct mc_grid_desc {
+  int32_t n1, n2, n3;
+  int32_t dtype;       /* MC_DTYPE_F64 or MC_DTYPE_F32 */
+  double x1_0, dx1, x2_0, dx2, x3_0, dx3;
+  int32_t location;    /* MC_LOC_HOST: copied into the context; MC_LOC_DEVICE: copied device-to-device */
+  int32_t pad0;
+  const void *prim;    /* 8 * n1*n2*n3 elements of dtype */
+} mc_grid_desc;
+
+/* Counters of one run (sums over all generations). */
+typedef struct mc_run_stats {
+  int64_t n_emit;      /* primaries emitted */
+  int64_t n_child;     /* scattered superphotons created */
+  int64_t n_rec, n_abs, n_capt, n_maxst;   /* recorded / absorbed / captured / dropped at max_steps */
+  int64_t n_steps;     /* geodesic steps */
+  int64_t n_iters;     /* Verlet predictor iterations */
+  int64_t n_nonconv;   /* steps whose predictor loop hit verlet_maxit */
+  int64_t n_roul_surv; /* roulette survivals */
+  int64_t n_rej_cap;   /* rejection loops that hit their cap */
+  int64_t n_events;    /* scattering events */
+  int64_t n_total;     /* primaries of the whole job (all shards) */
+  int64_t err_flags;   /* bit 0: child queue overflow; bit 1: log overflow */
+  int64_t transport_launches;  /* transport kernel launches (one per generation and batch) */
+  double transport_ms; /* summed device time of those launches (CUDA events on the launching stream) */
+  double generate_ms;  /* device time of weights, counts and scan */
+} mc_run_stats;
+
+/* One finished superphoton, for per-photon parity checks (layout matches the test oracle's). */
+typedef struct mc_log_rec {
+  uint64_t id;         /* random-stream id: the primary's uid, or the child's derived id */
+  int32_t gen, status; /* scattering generation; 1 recorded, 2 absorbed, 3 captured, 4 max steps */
+  double X[4], K[4];   /* end position (internal coordinates) and wavevector */
+  double w;            /* end weight */
+  int64_t nsteps;
+  int32_t nev, pad;    /* scattering events of this superphoton */
+} mc_log_rec;
+
+/* Creates a context on p->device, builds the device tables (synchrotron angle integral,
+ * K2, hot cross-section; sections 2.2 and 2.7).  *out owned by the library until mc_free.
+ * Errors: INVALID_ARG (bad parameters), NO_DEVICE, OOM, CUDA. */
+int mc_init_model(mc_ctx **out, const mc_model_params *p);
+
+/* Sets the fluid grid (section 3: "reading data from external files"); the library keeps
+ * its own copy in a zone-major layout.  Errors: INVALID_ARG, NAN_INPUT (non-finite
+ * primitive), OOM, CUDA. */
+int mc_set_grid(mc_ctx *c, const mc_grid_desc *g);
+
+/* Runs the whole hot path for N_s target superphotons and Philox seed `seed`: weights
+ * (eq. weight_calc), zone counts (section 2.3), then transport of the primaries of shard
+ * `shard` of `n_shards` (contiguous uid ranges) and of all their scattered descendants,
+ * generation by generation (section 3).  The spectrum sums are reset at the start of the
+ * call.  `stream` is a cudaStream_t (NULL: default stream); the call returns after the
+ * work on `stream` is complete (it reads the counters back).  stats may be NULL.
+ * Errors: STATE (no grid), INVALID_ARG, QUEUE_OVERFLOW (scattered superphotons exceeded
+ * the queue; results invalid), OOM, CUDA. */
+int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards, void *stream,
+           mc_run_stats *stats);
+
+/* Spectrum of the last mc_run: nu L_nu [erg/s] per (inclination, frequency) bin, its Monte
+ * Carlo standard error, and the superphoton count, each n_incl*n_bins host doubles
+ * (inclination-major).  Any pointer may be NULL.  Errors: SIZE if n_elems != n_incl*n_bins. */
+int mc_get_spectrum(mc_ctx *c, double *nuLnu, double *sigma, double *counts, size_t n_elems);
+
+/* Raw spectrum sums (sum w E, sum (w E)^2, count) [n_incl][n_bins][3] into host memory, for
+ * reductions across shards.  Errors: SIZE if n_elems != 3*n_incl*n_bins. */
+int mc_get_spectrum_sums(mc_ctx *c, double *sums, size_t n_elems);
+
+/* Zone superphoton counts of the last mc_run (int64, n1*n2*n3 host elements).
+ * Errors: STATE before any run, SIZE. */
+int mc_get_zone_counts(mc_ctx *c, int64_t *counts, size_t n_elems);
+
+/* Transports only the listed primaries (host array of uids of the job defined by N_s and
+ * seed) and their descendants, writing one mc_log_rec per finished superphoton to the host
+ * buffer `out` (capacity `cap`, number written in *n_out).  The spectrum sums of these
+ * superphotons replace the context's.  Errors: SIZE (uid out of range), STATE, CUDA. */
+int mc_trace(mc_ctx *c, double n_s, uint64_t seed, const int64_t *uids, size_t n_uids, mc_log_rec *out,
+             size_t cap, size_t *n_out, void *stream);
+
+/* Measures the arithmetic pipe throughput of the current device with a chain of independent
+ * fused multiply-adds (no memory traffic): dtype MC_DTYPE_F64 or MC_DTYPE_F32; writes the achieved
+ * FLOP/s (2 per FMA) to *flops.  Used as the roofline peak of the FP64 and FP32 pipes, which the
+ * paper's compute-bound transport kernels are measured against (section 5).  Errors: INVALID_ARG,
+ * NO_DEVICE, CUDA. */
+int mc_fma_peak(int device, int dtype, double *flops);
+
+/* Releases the context and all its device memory.  NULL is a no-op. */
+void mc_free(mc_ctx *c);
+
+/* Message of the last failing call on c (or of the last mc_init_model failure when c is NULL). */
+const char *mc_last_error(const mc_ctx *c);
+
+/* Library version string. */
+const char *mc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

@@ -435,7 +435,7 @@ void fluid_from_prims(const or_params &P, const Units &un, const double pr[8], c
 // coordinates between zone centres, clamped to the edge zones in x1 and x2, periodic
 // in x3; no plasma outside the radial extent of the grid).
 struct Model;
-void fluid_at(const Model &M, const double X[4], const double g[4][4], Fluid &F);
+void fluid_at(const Model &M, const double X[4], const double g[4][4], Fluid &F, bool clamp_radial = false);
 
 // Synchrotron emissivity, eq. emissivity (Leung et al. 2011 fit), with
 // nu_s = (2/9) (e B / 2 pi m_e c) Theta_e^2 sin(theta).
@@ -797,9 +797,9 @@ void zone_prims(const Model &M, int64_t z, double pr[8]) {
   for (int f = 0; f < 8; ++f) pr[f] = M.prim[(size_t)f * M.nz + z];
 }
 
-void fluid_at(const Model &M, const double X[4], const double g[4][4], Fluid &F) {
+void fluid_at(const Model &M, const double X[4], const double g[4][4], Fluid &F, bool clamp_radial) {
   double lo = M.x1_0, hi = M.x1_0 + M.n1 * M.dx1;
-  if (X[1] < lo || X[1] > hi) {
+  if (!clamp_radial && (X[1] < lo || X[1] > hi)) {
     F.plasma = false;
     F.ne = F.thetae = F.B = 0.0;
     return;
@@ -816,7 +816,7 @@ void fluid_at(const Model &M, const double X[4], const double g[4][4], Fluid &F)
   };
   int i, j;
   double di, dj;
-  idx(X[1], M.x1_0, M.dx1, M.n1, &i, &di);
+  idx(std::min(std::max(X[1], lo), hi), M.x1_0, M.dx1, M.n1, &i, &di);
   idx(X[2], M.x2_0, M.dx2, M.n2, &j, &dj);
   int k0 = 0, k1 = 0;
   double dk = 0.0;
@@ -951,7 +951,9 @@ void scatter_child(const Model &M, const double Xe[4], const double Ke[4], doubl
   double g[4][4];
   gcov_at(M.P, Xe, g);
   Fluid F;
-  fluid_at(M, Xe, g, F);
+  // reading: an event located by linear fraction just outside the radial grid takes the plasma
+  // of the nearest grid edge (the step's scattering depth came from inside the grid)
+  fluid_at(M, Xe, g, F, true);
   Stream s{M.seed, cid, 0u};
   double e[4][4];
   tetrad_scatter(g, F, e);

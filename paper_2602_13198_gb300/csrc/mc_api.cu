@@ -1,0 +1,600 @@
+// mc_api.cu -- host side of the C ABI declared in include/mc.h.
+//
+// Owns the context: device tables, the zone-major copy of the fluid grid, per-run generation
+// buffers, the two scattered-superphoton queues and the spectrum sums.  mc_run orchestrates one
+// whole pass of the hot path on the caller's stream: weights and zone counts (a handful of small
+// kernels), then the persistent transport kernel once per scattering generation, batching the
+// primaries so the queues stay within their capacity (the paper's memory batching, section 3).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mc_internal.h"
+
+using namespace mcgb;
+
+struct mc_ctx {
+  mc_model_params p;
+  std::string err;
+  int sms = 0;
+  // allocations made through the caller's allocator (or cudaMalloc)
+  std::vector<void *> allocs;
+  // tables
+  double *lnF = nullptr, *lnK2 = nullptr, *hot = nullptr, *gl = nullptr;
+  int nF = 0, nK2 = 0;
+  // grid
+  bool have_grid = false;
+  void *prim = nullptr;
+  int prim_f32 = 0;
+  int n1 = 0, n2 = 0, n3 = 0;
+  int64_t nz = 0;
+  double x1_0 = 0, dx1 = 0, x2_0 = 0, dx2 = 0, x3_0 = 0, dx3 = 0;
+  // per-run generation data
+  double *zvol = nullptr, *zpref = nullptr, *zlnuc = nullptr, *zgmax = nullptr, *znbar = nullptr;
+  int64_t *counts = nullptr, *start = nullptr, *bsum = nullptr;
+  double *partial = nullptr, *lnw = nullptr, *winv = nullptr;
+  int *bad = nullptr;
+  int nchunks = 0;
+  // transport
+  ChildBuf q[2];
+  int64_t qcap = 0;
+  unsigned long long *cnt = nullptr;
+  int64_t *total_dev = nullptr;
+  double *spec = nullptr;
+  unsigned long long *cnt_host = nullptr;   // pinned
+  bool have_run = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double t_transport = 0.0, t_generate = 0.0;
+  int64_t n_launch = 0;
+  int64_t last_total = 0;
+  uint64_t last_seed = 0;
+  double last_ns = 0.0;
+};
+
+static std::string g_init_err;
+
+static int fail(mc_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_init_err = msg;
+  return code;
+}
+
+static void *dev_alloc(mc_ctx *c, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void *ptr = nullptr;
+  if (c->p.alloc) {
+    ptr = c->p.alloc(bytes, c->p.alloc_user);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (ptr) c->allocs.push_back(ptr);
+  return ptr;
+}
+
+static void dev_free(mc_ctx *c, void *ptr) {
+  if (!ptr) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), ptr);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  if (c->p.free) c->p.free(ptr, c->p.alloc_user);
+  else cudaFree(ptr);
+}
+
+#define CU(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return fail(c, MC_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Gauss-Legendre nodes and weights on [a, b] by Newton iteration on P_n (three-term recurrence).
+static void gauss_legendre(int n, double a, double b, double *x, double *w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int iter = 0; iter < 100; ++iter) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int k = 1; k <= n; ++k) {
+        double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+      }
+      dp = n * (z * p1 - p2) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p1 = 1.0, p2 = 0.0;
+    for (int k = 1; k <= n; ++k) {
+      double p3 = p2;
+      p2 = p1;
+      p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+    }
+    dp = n * (z * p1 - p2) / (z * z - 1.0);
+    double wt = 2.0 / ((1.0 - z * z) * dp * dp);
+    double h = 0.5 * (b - a), mid = 0.5 * (b + a);
+    x[i] = mid - h * z;
+    x[n - 1 - i] = mid + h * z;
+    w[i] = w[n - 1 - i] = h * wt;
+  }
+}
+
+static DevModel make_model(const mc_ctx *c) {
+  const mc_model_params &p = c->p;
+  DevModel m;
+  std::memset(&m, 0, sizeof(m));
+  m.a = p.a;
+  m.mass = p.mass;
+  m.hslope = p.hslope;
+  m.r_h = (p.mass > 0.0) ? 1.0 + std::sqrt(1.0 - p.a * p.a) : 0.0;
+  double L = p.L_unit;
+  m.L3 = L * L * L;
+  m.rho_unit = p.M_unit / m.L3;
+  m.B_unit = kCL * std::sqrt(4.0 * kPI * m.rho_unit);
+  m.Ne_unit = m.rho_unit / (kMP + kME);
+  m.Ccoef = kHPL * L / (kME * kCL * kCL);
+  m.R_high = p.R_high;
+  m.R_low = p.R_low;
+  m.gam = p.gam;
+  m.thetae_min = p.thetae_min;
+  m.thetae_max = p.thetae_max;
+  m.n_nu = p.n_nu;
+  m.lnu_min = std::log(p.nu_min);
+  m.dlntot = std::log(p.nu_max / p.nu_min);
+  m.dlnu = m.dlntot / (p.n_nu - 1);
+  m.eps_geo = p.eps_geo;
+  m.verlet_tol = p.verlet_tol;
+  m.verlet_maxit = p.verlet_maxit;
+  m.r_record = p.r_record;
+  m.r_capture = (p.mass > 0.0) ? m.r_h * (1.0 + p.dh) : -1.0;
+  m.bias_mode = p.bias_mode;
+  m.bias_p0 = p.bias_p0;
+  m.n_sc_max = p.n_sc_max;
+  m.scatter = p.scatter;
+  m.k2_mode = p.k2_mode;
+  m.roulette_w = p.roulette_w;
+  m.roulette_p = p.roulette_p;
+  m.max_steps = p.max_steps;
+  m.lnu_lo = p.lnu_lo;
+  m.dlog_bin = (p.lnu_hi - p.lnu_lo) / p.n_bins;
+  m.n_bins = p.n_bins;
+  m.n_incl = p.n_incl;
+  m.n1 = c->n1;
+  m.n2 = c->n2;
+  m.n3 = c->n3;
+  m.nz = c->nz;
+  m.prim_f32 = c->prim_f32;
+  m.x1_0 = c->x1_0;
+  m.dx1 = c->dx1;
+  m.x2_0 = c->x2_0;
+  m.dx2 = c->dx2;
+  m.x3_0 = c->x3_0;
+  m.dx3 = c->dx3;
+  m.x1_hi = c->x1_0 + c->n1 * c->dx1;
+  m.prim64 = c->prim_f32 ? nullptr : (const double *)c->prim;
+  m.prim32 = c->prim_f32 ? (const float *)c->prim : nullptr;
+  m.lnF = c->lnF;
+  m.nF = c->nF;
+  m.lnK2 = c->lnK2;
+  m.nK2 = c->nK2;
+  m.hot = c->hot;
+  m.start = c->start;
+  m.zpref = c->zpref;
+  m.zlnuc = c->zlnuc;
+  m.zgmax = c->zgmax;
+  m.lnw = c->lnw;
+  m.winv = c->winv;
+  return m;
+}
+
+static int check_params(const mc_model_params *p, std::string &why) {
+  auto bad = [&](const char *s) { why = s; return MC_ERR_INVALID_ARG; };
+  if (!(p->mass == 0.0 || p->mass == 1.0)) return bad("mass must be 0 (flat) or 1 (Kerr-Schild)");
+  if (!(std::fabs(p->a) < 1.0)) return bad("|a| must be < 1");
+  if (!(p->hslope > 0.0 && p->hslope <= 1.0)) return bad("hslope must be in (0, 1]");
+  if (!(p->L_unit > 0.0 && p->M_unit > 0.0)) return bad("L_unit and M_unit must be positive");
+  if (!(p->nu_min > 0.0 && p->nu_max > p->nu_min)) return bad("need 0 < nu_min < nu_max");
+  if (p->n_nu < 2 || p->n_nu > 100000) return bad("n_nu must be in [2, 100000]");
+  if (!(p->w_min > 0.0)) return bad("w_min must be positive");
+  if (!(p->eps_geo > 0.0 && p->eps_geo < 1.0)) return bad("eps_geo must be in (0, 1)");
+  if (!(p->verlet_tol > 0.0) || p->verlet_maxit < 1) return bad("verlet_tol > 0 and verlet_maxit >= 1 required");
+  if (!(p->r_record > 0.0)) return bad("r_record must be positive");
+  if (p->n_bins < 1 || p->n_incl < 1 || !(p->lnu_hi > p->lnu_lo)) return bad("bad spectrum bins");
+  if (p->n_incl * (int64_t)p->n_bins > (1 << 24)) return bad("too many spectrum bins");
+  if (p->bias_mode < 0 || p->bias_mode > 2) return bad("bias_mode must be 0, 1 or 2");
+  if (p->n_sc_max < 0 || p->n_sc_max > 1000) return bad("n_sc_max out of range");
+  if (!(p->roulette_p > 0.0 && p->roulette_p <= 1.0) || !(p->roulette_w >= 0.0)) return bad("bad roulette");
+  if (p->max_steps < 1 || p->max_steps > 2000000000LL) return bad("max_steps out of range");
+  if (p->precision != MC_PREC_FP64 && p->precision != MC_PREC_MIXED) return bad("unknown precision");
+  if (p->surrogate != 0) return bad("surrogate coefficients are not available in this build of mc_run");
+  if (p->block != 0 && (p->block < 32 || p->block > 128 || p->block % 32)) return bad("block must be 32..128, multiple of 32");
+  if (!(p->thetae_min >= 0.0 && p->thetae_max > 0.0)) return bad("bad Theta_e bounds");
+  if (!(p->gam > 1.0)) return bad("gam must exceed 1");
+  return MC_OK;
+}
+
+extern "C" {
+
+const char *mc_version(void) { return "mcgb 0.1 (sm_103a)"; }
+
+const char *mc_last_error(const mc_ctx *c) { return c ? c->err.c_str() : g_init_err.c_str(); }
+
+void mc_free(mc_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->p.device);
+  cudaDeviceSynchronize();
+  std::vector<void *> a = c->allocs;
+  for (void *ptr : a) dev_free(c, ptr);
+  if (c->cnt_host) cudaFreeHost(c->cnt_host);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+int mc_init_model(mc_ctx **out, const mc_model_params *p) {
+  if (!out || !p) return fail(nullptr, MC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  std::string why;
+  int rc = check_params(p, why);
+  if (rc) return fail(nullptr, rc, why);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, MC_ERR_NO_DEVICE, "no CUDA device");
+  }
+  if (p->device < 0 || p->device >= ndev) return fail(nullptr, MC_ERR_NO_DEVICE, "device ordinal out of range");
+  mc_ctx *c = new (std::nothrow) mc_ctx();
+  if (!c) return fail(nullptr, MC_ERR_OOM, "host allocation failed");
+  c->p = *p;
+  if (cudaSetDevice(p->device) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, MC_ERR_CUDA, "cudaSetDevice failed");
+  }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, p->device);
+  c->nF = (int)std::floor((kFLnK1 - kFLnK0) / kFStep + 0.5) + 1;
+  c->nK2 = (int)std::floor((kK2LnT1 - kK2LnT0) / kK2Step + 0.5) + 1;
+  c->lnF = (double *)dev_alloc(c, sizeof(double) * c->nF);
+  c->lnK2 = (double *)dev_alloc(c, sizeof(double) * c->nK2);
+  c->hot = (double *)dev_alloc(c, sizeof(double) * kHotNT * kHotNE);
+  c->gl = (double *)dev_alloc(c, sizeof(double) * (128 + 128 + 64));
+  c->cnt = (unsigned long long *)dev_alloc(c, sizeof(unsigned long long) * CNT_N);
+  c->total_dev = (int64_t *)dev_alloc(c, sizeof(int64_t));
+  size_t nspec = (size_t)p->n_incl * p->n_bins * 3;
+  c->spec = (double *)dev_alloc(c, sizeof(double) * nspec);
+  c->lnw = (double *)dev_alloc(c, sizeof(double) * p->n_nu);
+  c->winv = (double *)dev_alloc(c, sizeof(double) * p->n_nu);
+  c->bad = (int *)dev_alloc(c, sizeof(int));
+  if (!c->lnF || !c->lnK2 || !c->hot || !c->gl || !c->cnt || !c->total_dev || !c->spec || !c->lnw || !c->winv || !c->bad) {
+    mc_free(c);
+    return fail(nullptr, MC_ERR_OOM, "device allocation failed");
+  }
+  if (cudaMallocHost(&c->cnt_host, sizeof(unsigned long long) * (CNT_N + 8)) != cudaSuccess) {
+    cudaGetLastError();
+    c->cnt_host = nullptr;
+    mc_free(c);
+    return fail(nullptr, MC_ERR_OOM, "pinned host allocation failed");
+  }
+  for (int k = 0; k < 4; ++k) {
+    if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
+      mc_free(c);
+      return fail(nullptr, MC_ERR_CUDA, "event creation failed");
+    }
+  }
+  std::vector<double> gl(320);
+  gauss_legendre(64, 0.0, 0.5 * kPI, gl.data(), gl.data() + 64);      // angle integral
+  gauss_legendre(64, 0.0, 8.0, gl.data() + 128, gl.data() + 192);     // hot cross-section, s
+  gauss_legendre(32, -1.0, 1.0, gl.data() + 256, gl.data() + 288);    // hot cross-section, mu
+  if (cudaMemcpy(c->gl, gl.data(), sizeof(double) * 320, cudaMemcpyHostToDevice) != cudaSuccess) {
+    mc_free(c);
+    return fail(nullptr, MC_ERR_CUDA, "table upload failed");
+  }
+  DevModel m = make_model(c);
+  launch_tables(m, c->lnF, c->lnK2, c->hot, c->gl, c->gl + 128, c->gl + 256, 0);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    std::string msg = std::string("table build failed: ") + cudaGetErrorString(e);
+    mc_free(c);
+    return fail(nullptr, MC_ERR_CUDA, msg);
+  }
+  *out = c;
+  return MC_OK;
+}
+
+int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
+  if (!c || !g || !g->prim) return fail(c, MC_ERR_INVALID_ARG, "null argument");
+  if (g->n1 < 1 || g->n2 < 1 || g->n3 < 1) return fail(c, MC_ERR_INVALID_ARG, "grid dimensions must be >= 1");
+  if (g->dtype != MC_DTYPE_F64 && g->dtype != MC_DTYPE_F32) return fail(c, MC_ERR_INVALID_ARG, "bad dtype");
+  if (g->location != MC_LOC_HOST && g->location != MC_LOC_DEVICE) return fail(c, MC_ERR_INVALID_ARG, "bad location");
+  if (!(g->dx1 > 0 && g->dx2 > 0 && g->dx3 > 0)) return fail(c, MC_ERR_INVALID_ARG, "grid spacings must be positive");
+  if (!(g->x2_0 >= 0.0 && g->x2_0 + g->n2 * g->dx2 <= 1.0 + 1e-12)) return fail(c, MC_ERR_INVALID_ARG, "x2 range must lie in [0, 1]");
+  CU(cudaSetDevice(c->p.device));
+  int64_t nz = (int64_t)g->n1 * g->n2 * g->n3;
+  size_t esz = (g->dtype == MC_DTYPE_F32) ? 4 : 8;
+  // free per-grid buffers
+  void *old[] = {c->prim, c->zvol, c->zpref, c->zlnuc, c->zgmax, c->znbar, c->counts, c->start, c->bsum, c->partial};
+  for (void *ptr : old) dev_free(c, ptr);
+  c->prim = nullptr;
+  c->have_grid = false;
+  c->have_run = false;
+  c->n1 = g->n1; c->n2 = g->n2; c->n3 = g->n3; c->nz = nz;
+  c->x1_0 = g->x1_0; c->dx1 = g->dx1; c->x2_0 = g->x2_0; c->dx2 = g->dx2; c->x3_0 = g->x3_0; c->dx3 = g->dx3;
+  c->prim_f32 = (g->dtype == MC_DTYPE_F32);
+  c->prim = dev_alloc(c, esz * 8 * nz);
+  c->zvol = (double *)dev_alloc(c, 8 * nz);
+  c->zpref = (double *)dev_alloc(c, 8 * nz);
+  c->zlnuc = (double *)dev_alloc(c, 8 * nz);
+  c->zgmax = (double *)dev_alloc(c, 8 * nz);
+  c->znbar = (double *)dev_alloc(c, 8 * nz);
+  c->counts = (int64_t *)dev_alloc(c, 8 * nz);
+  c->start = (int64_t *)dev_alloc(c, 8 * nz);
+  c->bsum = (int64_t *)dev_alloc(c, 8 * ((nz + 1023) / 1024 + 1));
+  c->nchunks = (int)((nz + 2047) / 2048);
+  c->partial = (double *)dev_alloc(c, 8 * (size_t)c->nchunks * c->p.n_nu);
+  if (!c->prim || !c->zvol || !c->zpref || !c->zlnuc || !c->zgmax || !c->znbar || !c->counts || !c->start || !c->bsum || !c->partial)
+    return fail(c, MC_ERR_OOM, "grid allocation failed");
+  const void *src = g->prim;
+  void *staging = nullptr;
+  if (g->location == MC_LOC_HOST) {
+    staging = dev_alloc(c, esz * 8 * nz);
+    if (!staging) return fail(c, MC_ERR_OOM, "staging allocation failed");
+    CU(cudaMemcpy(staging, g->prim, esz * 8 * nz, cudaMemcpyHostToDevice));
+    src = staging;
+  }
+  CU(cudaMemset(c->bad, 0, sizeof(int)));
+  launch_grid_to_aos(src, c->prim_f32, c->prim, c->prim_f32, nz, c->bad, 0);
+  int bad = 0;
+  CU(cudaMemcpy(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost));
+  if (staging) dev_free(c, staging);
+  if (bad) return fail(c, MC_ERR_NAN_INPUT, "grid primitives contain non-finite values");
+  c->have_grid = true;
+  return MC_OK;
+}
+
+static int ensure_queues(mc_ctx *c, int64_t cap) {
+  if (cap <= c->qcap) return MC_OK;
+  for (int b = 0; b < 2; ++b) {
+    ChildBuf &q = c->q[b];
+    for (int k = 0; k < 4; ++k) { dev_free(c, q.X[k]); dev_free(c, q.K[k]); }
+    dev_free(c, q.w); dev_free(c, q.id); dev_free(c, q.ctr); dev_free(c, q.nsc);
+    std::memset(&q, 0, sizeof(q));
+  }
+  c->qcap = 0;
+  for (int b = 0; b < 2; ++b) {
+    ChildBuf &q = c->q[b];
+    for (int k = 0; k < 4; ++k) {
+      q.X[k] = (double *)dev_alloc(c, 8 * cap);
+      q.K[k] = (double *)dev_alloc(c, 8 * cap);
+      if (!q.X[k] || !q.K[k]) return fail(c, MC_ERR_OOM, "queue allocation failed");
+    }
+    q.w = (double *)dev_alloc(c, 8 * cap);
+    q.id = (uint64_t *)dev_alloc(c, 8 * cap);
+    q.ctr = (uint32_t *)dev_alloc(c, 4 * cap);
+    q.nsc = (int32_t *)dev_alloc(c, 4 * cap);
+    if (!q.w || !q.id || !q.ctr || !q.nsc) return fail(c, MC_ERR_OOM, "queue allocation failed");
+  }
+  c->qcap = cap;
+  return MC_OK;
+}
+
+// Weights, counts and scan for (N_s, seed); leaves the job's primary total in c->last_total.
+static int generate(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st) {
+  DevModel m = make_model(c);
+  m.seed = seed;
+  CU(cudaEventRecord(c->ev[2], st));
+  CU(cudaMemsetAsync(c->bad, 0, sizeof(int), st));
+  launch_zone_prep(m, c->zvol, c->zpref, c->zlnuc, c->bad, st);
+  launch_weights(m, c->zvol, c->zpref, c->zlnuc, c->partial, c->nchunks, n_s, c->p.w_min, c->lnw, c->winv, st);
+  m = make_model(c);
+  m.seed = seed;
+  launch_counts(m, c->zvol, c->zpref, c->zlnuc, c->zgmax, c->znbar, c->counts, st);
+  launch_scan(c->counts, c->start, c->bsum, c->nz, c->total_dev, st);
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(c->ev[3], st));
+  CU(cudaMemcpyAsync(c->cnt_host + CNT_N, c->total_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(c->cnt_host + CNT_N + 1, c->bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  int bad = (int)(c->cnt_host[CNT_N + 1] & 0xffffffffu);
+  if (bad) return fail(c, MC_ERR_NAN_INPUT, "non-finite zone state");
+  float ms = 0.0f;
+  CU(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+  c->t_generate = ms;
+  c->last_total = (int64_t)c->cnt_host[CNT_N];
+  c->last_seed = seed;
+  c->last_ns = n_s;
+  return MC_OK;
+}
+
+// Transports primaries [u0, u1) (or the uid list) and all their descendants.
+static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_dev, int64_t n_list, mc_log_rec *log_dev,
+                     int64_t log_cap, uint64_t seed, cudaStream_t st) {
+  DevModel m = make_model(c);
+  m.seed = seed;
+  int block = c->p.block ? c->p.block : 128;
+  int mixed = c->p.precision == MC_PREC_MIXED;
+  int occ = transport_max_blocks_per_sm(mixed, block);
+  if (occ < 1) occ = 1;
+  if (c->p.ctas_per_sm > 0) occ = std::min(occ, (int)c->p.ctas_per_sm);
+  const int64_t n_prim = uid_list_dev ? n_list : (u1 - u0);
+  const int64_t batch_max = 1 << 24;
+  int64_t batch = std::min<int64_t>(std::max<int64_t>(n_prim, 1), batch_max);
+  int rc = ensure_queues(c, std::max<int64_t>(1 << 20, 2 * batch));
+  if (rc) return rc;
+  RoundIO io;
+  std::memset(&io, 0, sizeof(io));
+  io.spec = c->spec;
+  io.cnt = c->cnt;
+  io.log = log_dev;
+  io.log_cap = log_cap;
+  io.out_cap = c->qcap;
+  for (int64_t b0 = 0; b0 < n_prim; b0 += batch) {
+    int64_t nb = std::min(batch, n_prim - b0);
+    int gen = 0;
+    int64_t n_items = nb;
+    while (n_items > 0) {
+      io.n_items = n_items;
+      if (gen == 0) {
+        io.mode = uid_list_dev ? 1 : 0;
+        io.uid0 = u0 + b0;
+        io.uids = uid_list_dev ? uid_list_dev + b0 : nullptr;
+      } else {
+        io.mode = 2;
+        io.in = c->q[(gen - 1) & 1];
+      }
+      io.out = c->q[gen & 1];
+      CU(cudaMemsetAsync(c->cnt + CNT_NEXT, 0, 2 * sizeof(unsigned long long), st));
+      int64_t want = (n_items + block - 1) / block;
+      int grid = (int)std::min<int64_t>((int64_t)c->sms * occ, want);
+      CU(cudaEventRecord(c->ev[0], st));
+      launch_transport(m, io, mixed, grid, block, st);
+      CU(cudaGetLastError());
+      CU(cudaEventRecord(c->ev[1], st));
+      CU(cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      float ms = 0.0f;
+      CU(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      c->t_transport += ms;
+      c->n_launch++;
+      if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
+      n_items = (int64_t)c->cnt_host[CNT_OUT];
+      ++gen;
+    }
+  }
+  return MC_OK;
+}
+
+static void fill_stats(mc_ctx *c, mc_run_stats *s) {
+  if (!s) return;
+  const unsigned long long *h = c->cnt_host;
+  s->n_emit = h[CNT_EMIT]; s->n_child = h[CNT_CHILD]; s->n_rec = h[CNT_REC]; s->n_abs = h[CNT_ABS];
+  s->n_capt = h[CNT_CAPT]; s->n_maxst = h[CNT_MAXST]; s->n_steps = h[CNT_STEPS]; s->n_iters = h[CNT_ITERS];
+  s->n_nonconv = h[CNT_NONCONV]; s->n_roul_surv = h[CNT_ROUL]; s->n_rej_cap = h[CNT_REJCAP];
+  s->n_events = h[CNT_EVENTS]; s->n_total = c->last_total; s->err_flags = (int64_t)h[CNT_ERR];
+  s->transport_launches = c->n_launch;
+  s->transport_ms = c->t_transport;
+  s->generate_ms = c->t_generate;
+}
+
+int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards, void *stream, mc_run_stats *stats) {
+  if (!c) return fail(nullptr, MC_ERR_INVALID_ARG, "null context");
+  if (!c->have_grid) return fail(c, MC_ERR_STATE, "mc_set_grid must be called before mc_run");
+  if (!(n_s > 0.0) || n_shards < 1 || shard < 0 || shard >= n_shards) return fail(c, MC_ERR_INVALID_ARG, "bad N_s or shard");
+  CU(cudaSetDevice(c->p.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = generate(c, n_s, seed, st);
+  if (rc) return rc;
+  int64_t T = c->last_total;
+  int64_t u0 = (int64_t)((__int128)T * shard / n_shards), u1 = (int64_t)((__int128)T * (shard + 1) / n_shards);
+  size_t nspec = (size_t)c->p.n_incl * c->p.n_bins * 3;
+  CU(cudaMemsetAsync(c->spec, 0, sizeof(double) * nspec, st));
+  CU(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
+  c->t_transport = 0.0;
+  c->n_launch = 0;
+  rc = transport(c, u0, u1, nullptr, 0, nullptr, 0, seed, st);
+  if (rc) return rc;
+  c->have_run = true;
+  fill_stats(c, stats);
+  return MC_OK;
+}
+
+int mc_trace(mc_ctx *c, double n_s, uint64_t seed, const int64_t *uids, size_t n_uids, mc_log_rec *out, size_t cap,
+             size_t *n_out, void *stream) {
+  if (!c || !uids || !out || !n_out) return fail(c, MC_ERR_INVALID_ARG, "null argument");
+  if (!c->have_grid) return fail(c, MC_ERR_STATE, "mc_set_grid must be called before mc_trace");
+  CU(cudaSetDevice(c->p.device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = generate(c, n_s, seed, st);
+  if (rc) return rc;
+  for (size_t i = 0; i < n_uids; ++i)
+    if (uids[i] < 0 || uids[i] >= c->last_total) return fail(c, MC_ERR_SIZE, "uid out of range");
+  int64_t *ud = (int64_t *)dev_alloc(c, 8 * std::max<size_t>(n_uids, 1));
+  mc_log_rec *ld = (mc_log_rec *)dev_alloc(c, sizeof(mc_log_rec) * std::max<size_t>(cap, 1));
+  if (!ud || !ld) {
+    dev_free(c, ud);
+    dev_free(c, ld);
+    return fail(c, MC_ERR_OOM, "trace buffers");
+  }
+  size_t nspec = (size_t)c->p.n_incl * c->p.n_bins * 3;
+  cudaError_t e = cudaMemcpyAsync(ud, uids, 8 * n_uids, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->spec, 0, sizeof(double) * nspec, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * CNT_N, st);
+  if (e != cudaSuccess) {
+    dev_free(c, ud);
+    dev_free(c, ld);
+    return fail(c, MC_ERR_CUDA, cudaGetErrorString(e));
+  }
+  rc = (n_uids > 0) ? transport(c, 0, 0, ud, (int64_t)n_uids, ld, (int64_t)cap, seed, st) : MC_OK;
+  if (rc == MC_OK) {
+    size_t n = std::min<size_t>((size_t)c->cnt_host[CNT_LOG], cap);
+    e = cudaMemcpyAsync(out, ld, sizeof(mc_log_rec) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = fail(c, MC_ERR_CUDA, cudaGetErrorString(e));
+    *n_out = n;
+    c->have_run = true;
+  }
+  dev_free(c, ud);
+  dev_free(c, ld);
+  return rc;
+}
+
+int mc_get_spectrum_sums(mc_ctx *c, double *sums, size_t n_elems) {
+  if (!c || !sums) return fail(c, MC_ERR_INVALID_ARG, "null argument");
+  size_t nspec = (size_t)c->p.n_incl * c->p.n_bins * 3;
+  if (n_elems != nspec) return fail(c, MC_ERR_SIZE, "sums buffer must hold 3*n_incl*n_bins doubles");
+  if (!c->have_run) return fail(c, MC_ERR_STATE, "no run yet");
+  CU(cudaSetDevice(c->p.device));
+  CU(cudaMemcpy(sums, c->spec, sizeof(double) * nspec, cudaMemcpyDeviceToHost));
+  return MC_OK;
+}
+
+int mc_get_spectrum(mc_ctx *c, double *nuLnu, double *sigma, double *counts, size_t n_elems) {
+  if (!c) return fail(nullptr, MC_ERR_INVALID_ARG, "null context");
+  size_t nb = (size_t)c->p.n_incl * c->p.n_bins;
+  if (n_elems != nb) return fail(c, MC_ERR_SIZE, "buffers must hold n_incl*n_bins doubles");
+  if (!c->have_run) return fail(c, MC_ERR_STATE, "no run yet");
+  std::vector<double> s(nb * 3);
+  int rc = mc_get_spectrum_sums(c, s.data(), nb * 3);
+  if (rc) return rc;
+  // nu L_nu = sum(w E) m_e c^2 / (dt dln nu_bin) * 4 pi / dOmega_incl, dt = 1 (section 3, eq. weight_calc)
+  double dln = (c->p.lnu_hi - c->p.lnu_lo) / c->p.n_bins * std::log(10.0);
+  for (int i = 0; i < c->p.n_incl; ++i) {
+    double t0 = 0.5 * kPI * i / c->p.n_incl, t1 = 0.5 * kPI * (i + 1) / c->p.n_incl;
+    double dom = 2.0 * 2.0 * kPI * (std::cos(t0) - std::cos(t1));   // both hemispheres
+    double f = kME * kCL * kCL / dln * (4.0 * kPI / dom);
+    for (int b = 0; b < c->p.n_bins; ++b) {
+      size_t k = (size_t)i * c->p.n_bins + b;
+      if (nuLnu) nuLnu[k] = s[3 * k] * f;
+      if (sigma) sigma[k] = std::sqrt(s[3 * k + 1]) * f;
+      if (counts) counts[k] = s[3 * k + 2];
+    }
+  }
+  return MC_OK;
+}
+
+int mc_fma_peak(int device, int dtype, double *flops) {
+  if (!flops || (dtype != MC_DTYPE_F64 && dtype != MC_DTYPE_F32)) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(nullptr, MC_ERR_NO_DEVICE, "no such CUDA device");
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, MC_ERR_CUDA, "cudaSetDevice failed");
+  double f = 0.0;
+  cudaError_t e = fma_peak(dtype == MC_DTYPE_F64, &f);
+  if (e != cudaSuccess) return fail(nullptr, MC_ERR_CUDA, cudaGetErrorString(e));
+  *flops = f;
+  return MC_OK;
+}
+
+int mc_get_zone_counts(mc_ctx *c, int64_t *counts, size_t n_elems) {
+  if (!c || !counts) return fail(c, MC_ERR_INVALID_ARG, "null argument");
+  if (!c->have_grid || c->last_ns == 0.0) return fail(c, MC_ERR_STATE, "no run yet");
+  if (n_elems != (size_t)c->nz) return fail(c, MC_ERR_SIZE, "counts buffer must hold n1*n2*n3 elements");
+  CU(cudaSetDevice(c->p.device));
+  CU(cudaMemcpy(counts, c->counts, 8 * c->nz, cudaMemcpyDeviceToHost));
+  return MC_OK;
+}
+
+}  // extern "C"

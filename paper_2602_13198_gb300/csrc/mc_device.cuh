@@ -1,0 +1,770 @@
+// mc_device.cuh -- device-side arithmetic of the Monte Carlo transport hot path
+// (GPUmonty, arXiv 2602.13198), written for sm_103a.
+//
+// Everything a superphoton needs per step lives here: the Kerr-Schild metric in modified
+// Kerr-Schild coordinates with closed-form first derivatives (section 2.4), the geodesic
+// acceleration -Gamma^mu_ab k^a k^b contracted without forming the 40 Christoffel symbols,
+// the iterated velocity-Verlet step (section 2.4), fluid interpolation and the invariant
+// synchrotron / Compton coefficients (sections 2.2, 2.5-2.7), Philox4x32-10 streams keyed
+// per superphoton, tetrads, and the thermal Compton kinematics (section 2.7).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcgb {
+
+// ---------------------------------------------------------------- physical constants (CGS, CODATA 2018)
+constexpr double kEE = 4.803204712570263e-10;
+constexpr double kME = 9.1093837015e-28;
+constexpr double kMP = 1.67262192369e-24;
+constexpr double kCL = 2.99792458e10;
+constexpr double kHPL = 6.62607015e-27;
+constexpr double kSIGT = 6.6524587321e-25;
+constexpr double kPI = 3.14159265358979323846;
+
+// Hot cross-section table domain: ln Theta in [ln 1e-3, ln 1e3] (121), ln eps in [ln 1e-12, ln 1e6] (181)
+constexpr int kHotNT = 121, kHotNE = 181;
+constexpr double kHotLT0 = -6.907755278982137, kHotLT1 = 6.907755278982137;
+constexpr double kHotLE0 = -27.631021115928547, kHotLE1 = 13.815510557964274;
+// Angle-integral table: ln F on ln K in [ln 1e-10, ln 1e8], spacing 0.005
+constexpr double kFLnK0 = -23.025850929940457, kFLnK1 = 18.420680743952367, kFStep = 0.005;
+// K2(1/Theta) table: ln K2 on ln Theta in [ln 0.01, ln 1e4], spacing 0.002
+constexpr double kK2LnT0 = -4.605170185988091, kK2LnT1 = 9.210340371976184, kK2Step = 0.002;
+
+// ---------------------------------------------------------------- model view passed to kernels
+struct DevModel {
+  // metric and units
+  double a, mass, hslope, r_h;
+  double rho_unit, B_unit, Ne_unit, Ccoef, L3;   // Ccoef = h L / (m_e c^2), L3 = L_unit^3
+  double R_high, R_low, gam, thetae_min, thetae_max;
+  // emission band / weights
+  double lnu_min, dlnu, dlntot;
+  int n_nu;
+  // transport
+  double eps_geo, verlet_tol, r_record, r_capture;
+  int verlet_maxit, bias_mode, n_sc_max, scatter, k2_mode;
+  double bias_p0, roulette_w, roulette_p;
+  int64_t max_steps;
+  // record
+  double lnu_lo, dlog_bin;
+  int n_bins, n_incl;
+  // grid (zone-major primitives prim[z*8 + f])
+  int n1, n2, n3, prim_f32;
+  int64_t nz;
+  double x1_0, dx1, x2_0, dx2, x3_0, dx3, x1_hi;
+  const double *prim64;
+  const float *prim32;
+  // tables
+  const double *lnF;      // angle integral
+  int nF;
+  const double *lnK2;
+  int nK2;
+  const double *hot;      // ln(sigma_h / sigma_T) [kHotNT][kHotNE]
+  // per-run generation data
+  const int64_t *start;   // exclusive scan of zone counts
+  const double *zpref;    // 4 pi A nu_c per zone (int dOmega j_nu = zpref F(nu/nu_c))
+  const double *zlnuc;    // ln nu_c per zone
+  const double *zgmax;    // max_j g_ij per zone
+  const double *lnw;      // ln w_j (n_nu)
+  const double *winv;     // 1 / w_j (n_nu)
+  uint64_t seed;
+};
+
+// ---------------------------------------------------------------- Philox4x32-10 (Salmon et al. 2011)
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Per-superphoton stream: key = seed, counter = (draw/2, 0, id_lo, id_hi); a double per half block.
+struct Rng {
+  uint64_t id;
+  uint32_t n;
+  uint32_t cache_blk;
+  uint32_t cache[4];
+};
+
+__device__ __forceinline__ void rng_init(Rng &s, uint64_t id, uint32_t n) {
+  s.id = id;
+  s.n = n;
+  s.cache_blk = 0xFFFFFFFFu;
+}
+
+__device__ __forceinline__ double rng_u(Rng &s, uint64_t seed) {
+  uint32_t blk = s.n >> 1;
+  if (blk != s.cache_blk) {
+    s.cache[0] = blk;
+    s.cache[1] = 0u;
+    s.cache[2] = (uint32_t)s.id;
+    s.cache[3] = (uint32_t)(s.id >> 32);
+    philox(s.cache, (uint32_t)seed, (uint32_t)(seed >> 32));
+    s.cache_blk = blk;
+  }
+  uint32_t a = (s.n & 1u) ? s.cache[2] : s.cache[0];
+  uint32_t b = (s.n & 1u) ? s.cache[3] : s.cache[1];
+  s.n++;
+  uint64_t m = ((uint64_t)a << 21) | (uint64_t)(b >> 11);
+  return ((double)m + 0.5) * 1.1102230246251565e-16;   // 2^-53
+}
+
+// Child stream id: splitmix64 output (Steele, Lea & Flood 2014) of parent + (event+1) * golden gamma.
+__host__ __device__ __forceinline__ uint64_t child_id(uint64_t parent, uint32_t ev) {
+  uint64_t z = parent + 0x9E3779B97F4A7C15ull * (uint64_t)(ev + 1u);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+constexpr uint64_t kZoneTag = 0xC000000000000000ull;
+
+// ---------------------------------------------------------------- metric (section 2.4)
+// Nonzero components of the MKS Kerr-Schild metric (symmetric): 00 01 03 11 13 22 33; its
+// inverse has 00 01 11 13 22 33.  d1 / d2: derivatives with respect to x1 and x2.
+struct Geo {
+  double g00, g01, g03, g11, g13, g22, g33;
+  double G00, G01, G11, G13, G22, G33;
+  double d100, d101, d103, d111, d113, d122, d133;
+  double d200, d201, d203, d211, d213, d222, d233;
+  double r, sth, cth;
+};
+
+// theta(x2) = pi x2 + (1-h)/2 sin(2 pi x2) and its first two derivatives.
+__device__ __forceinline__ void theta_map(double h, double x2, double &th, double &dth, double &d2th) {
+  if (h == 1.0) {
+    th = kPI * x2;
+    dth = kPI;
+    d2th = 0.0;
+    return;
+  }
+  double s2, c2;
+  sincospi(2.0 * x2, &s2, &c2);
+  th = kPI * x2 + 0.5 * (1.0 - h) * s2;
+  dth = kPI * (1.0 + (1.0 - h) * c2);
+  d2th = -2.0 * kPI * kPI * (1.0 - h) * s2;
+}
+
+template <bool DERIV>
+__device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double x2, Geo &G) {
+  const double a = m.a, M = m.mass, a2 = a * a;
+  double r = exp(x1);
+  double th, dth, d2th;
+  theta_map(m.hslope, x2, th, dth, d2th);
+  double s, c;
+  if (m.hslope == 1.0) sincospi(x2, &s, &c);
+  else sincos(th, &s, &c);
+  double s2 = s * s, c2 = c * c;
+  double sig = r * r + a2 * c2;
+  double isig = 1.0 / sig;
+  double f = 2.0 * M * r * isig;
+  double opf = 1.0 + f;
+  // Kerr-Schild components (t, r, theta, phi)
+  double Gtt = f - 1.0, Gtr = f, Gtp = -a * f * s2, Grr = opf, Grp = -a * s2 * opf, Ghh = sig;
+  double Gpp = s2 * (sig + a2 * s2 * opf);
+  G.r = r;
+  G.sth = s;
+  G.cth = c;
+  G.g00 = Gtt;
+  G.g01 = Gtr * r;
+  G.g03 = Gtp;
+  G.g11 = Grr * r * r;
+  G.g13 = Grp * r;
+  G.g22 = Ghh * dth * dth;
+  G.g33 = Gpp;
+  // inverse: g^tt = -(1+f), g^tr = f, g^rr = (r^2 - 2Mr + a^2)/Sigma, g^rphi = a/Sigma,
+  // g^thth = 1/Sigma, g^phph = 1/(Sigma sin^2); divided by the Jacobian factors
+  double ir = 1.0 / r, idth = 1.0 / dth;
+  G.G00 = -opf;
+  G.G01 = f * ir;
+  G.G11 = (r * r - 2.0 * M * r + a2) * isig * ir * ir;
+  G.G13 = a * isig * ir;
+  G.G22 = isig * idth * idth;
+  G.G33 = isig / s2;
+  if (!DERIV) return;
+  // derivatives of the KS components with respect to r and theta
+  double dfr = 2.0 * M * (sig - 2.0 * r * r) * isig * isig;
+  double dft = 4.0 * M * r * a2 * s * c * isig * isig;
+  double dGtp_r = -a * s2 * dfr, dGtp_t = -a * (dft * s2 + 2.0 * f * s * c);
+  double dGrp_r = -a * s2 * dfr, dGrp_t = -a * (2.0 * s * c * opf + s2 * dft);
+  double dGhh_r = 2.0 * r, dGhh_t = -2.0 * a2 * s * c;
+  double dGpp_r = 2.0 * r * s2 + a2 * s2 * s2 * dfr;
+  double dGpp_t = 2.0 * s * c * sig + s2 * (-2.0 * a2 * s * c) + a2 * (4.0 * s2 * s * c * opf + s2 * s2 * dft);
+  // d/dx1 = r d/dr (Jacobian factor r also varies with x1)
+  G.d100 = r * dfr;
+  G.d101 = r * (r * dfr + Gtr);
+  G.d103 = r * dGtp_r;
+  G.d111 = r * r * (r * dfr + 2.0 * Grr);
+  G.d113 = r * (r * dGrp_r + Grp);
+  G.d122 = r * dGhh_r * dth * dth;
+  G.d133 = r * dGpp_r;
+  // d/dx2 = dth d/dtheta (Jacobian factor dth also varies with x2)
+  G.d200 = dth * dft;
+  G.d201 = dth * dft * r;
+  G.d203 = dth * dGtp_t;
+  G.d211 = dth * dft * r * r;
+  G.d213 = dth * dGrp_t * r;
+  G.d222 = dth * dGhh_t * dth * dth + Ghh * 2.0 * dth * d2th;
+  G.d233 = dth * dGpp_t;
+}
+
+__device__ __forceinline__ void lower(const Geo &G, const double v[4], double o[4]) {
+  o[0] = G.g00 * v[0] + G.g01 * v[1] + G.g03 * v[3];
+  o[1] = G.g01 * v[0] + G.g11 * v[1] + G.g13 * v[3];
+  o[2] = G.g22 * v[2];
+  o[3] = G.g03 * v[0] + G.g13 * v[1] + G.g33 * v[3];
+}
+
+__device__ __forceinline__ double dot(const Geo &G, const double a[4], const double b[4]) {
+  double lb[4];
+  lower(G, b, lb);
+  return a[0] * lb[0] + a[1] * lb[1] + a[2] * lb[2] + a[3] * lb[3];
+}
+
+// dk^mu/dlambda = -Gamma^mu_ab k^a k^b = -g^{mu nu} (k^1 (d1 g k)_nu + k^2 (d2 g k)_nu - 1/2 d_nu g_ab k^a k^b)
+__device__ __forceinline__ void accel(const Geo &G, const double k[4], double A[4]) {
+  double p0 = G.d100 * k[0] + G.d101 * k[1] + G.d103 * k[3];
+  double p1 = G.d101 * k[0] + G.d111 * k[1] + G.d113 * k[3];
+  double p2 = G.d122 * k[2];
+  double p3 = G.d103 * k[0] + G.d113 * k[1] + G.d133 * k[3];
+  double q0 = G.d200 * k[0] + G.d201 * k[1] + G.d203 * k[3];
+  double q1 = G.d201 * k[0] + G.d211 * k[1] + G.d213 * k[3];
+  double q2 = G.d222 * k[2];
+  double q3 = G.d203 * k[0] + G.d213 * k[1] + G.d233 * k[3];
+  double kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
+  double kDk2 = k[0] * q0 + k[1] * q1 + k[2] * q2 + k[3] * q3;
+  double w0 = k[1] * p0 + k[2] * q0;
+  double w1 = k[1] * p1 + k[2] * q1 - 0.5 * kDk1;
+  double w2 = k[1] * p2 + k[2] * q2 - 0.5 * kDk2;
+  double w3 = k[1] * p3 + k[2] * q3;
+  A[0] = -(G.G00 * w0 + G.G01 * w1);
+  A[1] = -(G.G01 * w0 + G.G11 * w1 + G.G13 * w3);
+  A[2] = -(G.G22 * w2);
+  A[3] = -(G.G13 * w1 + G.G33 * w3);
+}
+
+// Step size (reading; the paper gives none): each internal coordinate moves at most eps_geo of
+// its scale (1 for ln r and phi, the distance to the nearer pole for x2).
+__device__ __forceinline__ double stepsize(const DevModel &m, const double X[4], const double K[4]) {
+  const double SMALL = 1e-40;
+  double x2n = fmin(fabs(X[2]), fabs(1.0 - X[2]));
+  double d1 = m.eps_geo / (fabs(K[1]) + SMALL);
+  double d2 = m.eps_geo * x2n / (fabs(K[2]) + SMALL);
+  double d3 = m.eps_geo / (fabs(K[3]) + SMALL);
+  return 1.0 / (1.0 / d1 + 1.0 / d2 + 1.0 / d3);
+}
+
+// ---------------------------------------------------------------- tables
+__device__ __forceinline__ double cubic_table(const double *t, int n, double x0, double step, double x) {
+  double f = (x - x0) / step;
+  int i = (int)floor(f);
+  i = max(1, min(i, n - 3));
+  double u = f - i;
+  double y0 = t[i - 1], y1 = t[i], y2 = t[i + 1], y3 = t[i + 2];
+  // 4-point Lagrange through nodes i-1 .. i+2 at offset u from node i
+  double um1 = u + 1.0, u1 = u - 1.0, u2 = u - 2.0;
+  return -y0 * u * u1 * u2 / 6.0 + y1 * um1 * u1 * u2 / 2.0 - y2 * um1 * u * u2 / 2.0 + y3 * um1 * u * u1 / 6.0;
+}
+
+// int_0^{pi/2} sin^2 G(K / sin) dth from the table (0 beyond the table's upper end)
+__device__ __forceinline__ double F_of_lnK(const DevModel &m, double lnK) {
+  if (lnK >= kFLnK1) return 0.0;
+  if (lnK <= kFLnK0) {
+    // small-K power law F ~ K^(1/3) continued from the first node
+    return exp(m.lnF[0] + (lnK - kFLnK0) / 3.0);
+  }
+  return exp(cubic_table(m.lnF, m.nF, kFLnK0, kFStep, lnK));
+}
+
+__device__ __forceinline__ double K2_of(const DevModel &m, double thetae) {
+  if (m.k2_mode == 1) return 2.0 * thetae * thetae;
+  return exp(cubic_table(m.lnK2, m.nK2, kK2LnT0, kK2Step, log(thetae)));
+}
+
+__device__ __forceinline__ float K2_of_f(const DevModel &m, float thetae) {
+  if (m.k2_mode == 1) return 2.0f * thetae * thetae;
+  float f = (__logf(thetae) - (float)kK2LnT0) * (float)(1.0 / kK2Step);
+  int i = max(0, min((int)f, m.nK2 - 2));
+  float u = f - i;
+  float l = (1.0f - u) * (float)m.lnK2[i] + u * (float)m.lnK2[i + 1];
+  return __expf(l);
+}
+
+__device__ __forceinline__ double hot_lookup(const DevModel &m, double thetae, double eps) {
+  double lt = log(thetae), le = log(eps);
+  double ft = (lt - kHotLT0) / (kHotLT1 - kHotLT0) * (kHotNT - 1);
+  double fe = (le - kHotLE0) / (kHotLE1 - kHotLE0) * (kHotNE - 1);
+  ft = fmin(fmax(ft, 0.0), (double)(kHotNT - 1));
+  fe = fmin(fmax(fe, 0.0), (double)(kHotNE - 1));
+  int i = min((int)ft, kHotNT - 2), j = min((int)fe, kHotNE - 2);
+  double a = ft - i, b = fe - j;
+  const double *h = m.hot;
+  double v00 = h[i * kHotNE + j], v01 = h[i * kHotNE + j + 1];
+  double v10 = h[(i + 1) * kHotNE + j], v11 = h[(i + 1) * kHotNE + j + 1];
+  double l = (1 - a) * (1 - b) * v00 + (1 - a) * b * v01 + a * (1 - b) * v10 + a * b * v11;
+  return kSIGT * exp(l);
+}
+
+__device__ __forceinline__ float hot_lookup_f(const DevModel &m, float thetae, float eps) {
+  float ft = (__logf(thetae) - (float)kHotLT0) * (float)((kHotNT - 1) / (kHotLT1 - kHotLT0));
+  float fe = (__logf(eps) - (float)kHotLE0) * (float)((kHotNE - 1) / (kHotLE1 - kHotLE0));
+  ft = fminf(fmaxf(ft, 0.0f), (float)(kHotNT - 1));
+  fe = fminf(fmaxf(fe, 0.0f), (float)(kHotNE - 1));
+  int i = min((int)ft, kHotNT - 2), j = min((int)fe, kHotNE - 2);
+  float a = ft - i, b = fe - j;
+  const double *h = m.hot;
+  float v00 = (float)h[i * kHotNE + j], v01 = (float)h[i * kHotNE + j + 1];
+  float v10 = (float)h[(i + 1) * kHotNE + j], v11 = (float)h[(i + 1) * kHotNE + j + 1];
+  float l = (1 - a) * (1 - b) * v00 + (1 - a) * b * v01 + a * (1 - b) * v10 + a * b * v11;
+  return (float)kSIGT * __expf(l);
+}
+
+// ---------------------------------------------------------------- synchrotron (section 2.2)
+// G(X) = (X^1/2 + 2^11/12 X^1/6)^2 exp(-X^1/3)
+__device__ __forceinline__ double Gsyn(double X) {
+  double x6 = cbrt(sqrt(X));
+  double x3 = x6 * x6;
+  double t = x6 * x6 * x6 + 1.8877486253633870 * x6;   // 2^(11/12)
+  return t * t * exp(-x3);
+}
+
+// ---------------------------------------------------------------- fluid (sections 2.5-2.7)
+template <typename T>
+struct Plasma {
+  T ne, thetae, B;
+  T ucov[4], bcov[4];
+  T bsq;
+  bool on;
+};
+
+// Primitives interpolated linearly in internal coordinates between zone centres (reading):
+// clamped to the edge zones in x1 and x2, periodic in x3, no plasma outside the radial range.
+template <typename T>
+__device__ __forceinline__ bool interp_prims(const DevModel &m, const double X[4], T pr[8]) {
+  if (X[1] < m.x1_0 || X[1] > m.x1_hi) return false;
+  int i, j;
+  double di, dj;
+  {
+    double f = (X[1] - m.x1_0) / m.dx1 - 0.5;
+    i = (int)floor(f);
+    di = f - i;
+    if (m.n1 == 1) { i = 0; di = 0.0; }
+    else if (i < 0) { i = 0; di = 0.0; }
+    else if (i > m.n1 - 2) { i = m.n1 - 2; di = 1.0; }
+  }
+  {
+    double f = (X[2] - m.x2_0) / m.dx2 - 0.5;
+    j = (int)floor(f);
+    dj = f - j;
+    if (m.n2 == 1) { j = 0; dj = 0.0; }
+    else if (j < 0) { j = 0; dj = 0.0; }
+    else if (j > m.n2 - 2) { j = m.n2 - 2; dj = 1.0; }
+  }
+  int k0 = 0, k1 = 0;
+  double dk = 0.0;
+  if (m.n3 > 1) {
+    double f = (X[3] - m.x3_0) / m.dx3 - 0.5;
+    double fl = floor(f);
+    dk = f - fl;
+    long long kk = (long long)fl;
+    k0 = (int)(((kk % m.n3) + m.n3) % m.n3);
+    k1 = (k0 + 1) % m.n3;
+  }
+  int i1 = (m.n1 > 1) ? i + 1 : i, j1 = (m.n2 > 1) ? j + 1 : j;
+  int64_t z00 = ((int64_t)i * m.n2 + j) * m.n3, z01 = ((int64_t)i * m.n2 + j1) * m.n3;
+  int64_t z10 = ((int64_t)i1 * m.n2 + j) * m.n3, z11 = ((int64_t)i1 * m.n2 + j1) * m.n3;
+  T w00 = (T)((1 - di) * (1 - dj)), w01 = (T)((1 - di) * dj), w10 = (T)(di * (1 - dj)), w11 = (T)(di * dj);
+  T wk0 = (T)(1 - dk), wk1 = (T)dk;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) pr[f] = (T)0;
+  auto acc = [&](int64_t zb, T w) {
+    if (m.prim_f32) {
+      const float4 *p0 = reinterpret_cast<const float4 *>(m.prim32 + (zb + k0) * 8);
+      float4 a0 = __ldg(p0), a1 = __ldg(p0 + 1);
+      T ww = w * wk0;
+      pr[0] += ww * (T)a0.x; pr[1] += ww * (T)a0.y; pr[2] += ww * (T)a0.z; pr[3] += ww * (T)a0.w;
+      pr[4] += ww * (T)a1.x; pr[5] += ww * (T)a1.y; pr[6] += ww * (T)a1.z; pr[7] += ww * (T)a1.w;
+      if (m.n3 > 1) {
+        const float4 *p1 = reinterpret_cast<const float4 *>(m.prim32 + (zb + k1) * 8);
+        float4 b0 = __ldg(p1), b1 = __ldg(p1 + 1);
+        ww = w * wk1;
+        pr[0] += ww * (T)b0.x; pr[1] += ww * (T)b0.y; pr[2] += ww * (T)b0.z; pr[3] += ww * (T)b0.w;
+        pr[4] += ww * (T)b1.x; pr[5] += ww * (T)b1.y; pr[6] += ww * (T)b1.z; pr[7] += ww * (T)b1.w;
+      }
+    } else {
+      const double2 *p0 = reinterpret_cast<const double2 *>(m.prim64 + (zb + k0) * 8);
+      T ww = w * wk0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double2 v = __ldg(p0 + q);
+        pr[2 * q] += ww * (T)v.x;
+        pr[2 * q + 1] += ww * (T)v.y;
+      }
+      if (m.n3 > 1) {
+        const double2 *p1 = reinterpret_cast<const double2 *>(m.prim64 + (zb + k1) * 8);
+        ww = w * wk1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          double2 v = __ldg(p1 + q);
+          pr[2 * q] += ww * (T)v.x;
+          pr[2 * q + 1] += ww * (T)v.y;
+        }
+      }
+    }
+  };
+  // same weights and order as a plain bilinear/trilinear blend
+  acc(z00, w00);
+  acc(z01, w01);
+  acc(z10, w10);
+  acc(z11, w11);
+  return true;
+}
+
+// Fluid-frame quantities from primitives with metric G: 4-velocity from the normal-observer
+// velocity, magnetic 4-vector b, n_e, |B| [G] and Theta_e from the R_high/R_low model.
+template <typename T>
+__device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &G, const T pr[8], Plasma<T> &P,
+                                                  T ucon_out[4], T bcon_out[4]) {
+  T g00 = (T)G.g00, g01 = (T)G.g01, g03 = (T)G.g03, g11 = (T)G.g11, g13 = (T)G.g13, g22 = (T)G.g22, g33 = (T)G.g33;
+  T rho = pr[0], uu = pr[1];
+  T U1 = pr[5], U2 = pr[6], U3 = pr[7];
+  T alpha = (T)1 / sqrt(-(T)G.G00);
+  T q = g11 * U1 * U1 + g22 * U2 * U2 + g33 * U3 * U3 + (T)2 * g13 * U1 * U3;
+  T gamma = sqrt((T)1 + q);
+  T u0 = gamma / alpha;
+  T u1 = U1 - gamma * alpha * (T)G.G01;
+  T u2 = U2, u3 = U3;
+  T uc0 = g00 * u0 + g01 * u1 + g03 * u3;
+  T uc1 = g01 * u0 + g11 * u1 + g13 * u3;
+  T uc2 = g22 * u2;
+  T uc3 = g03 * u0 + g13 * u1 + g33 * u3;
+  T b0 = pr[2] * uc1 + pr[3] * uc2 + pr[4] * uc3;
+  T b1 = (pr[2] + b0 * u1) / u0, b2 = (pr[3] + b0 * u2) / u0, b3 = (pr[4] + b0 * u3) / u0;
+  T bc0 = g00 * b0 + g01 * b1 + g03 * b3;
+  T bc1 = g01 * b0 + g11 * b1 + g13 * b3;
+  T bc2 = g22 * b2;
+  T bc3 = g03 * b0 + g13 * b1 + g33 * b3;
+  P.ucov[0] = uc0; P.ucov[1] = uc1; P.ucov[2] = uc2; P.ucov[3] = uc3;
+  P.bcov[0] = bc0; P.bcov[1] = bc1; P.bcov[2] = bc2; P.bcov[3] = bc3;
+  if (ucon_out) { ucon_out[0] = u0; ucon_out[1] = u1; ucon_out[2] = u2; ucon_out[3] = u3; }
+  if (bcon_out) { bcon_out[0] = b0; bcon_out[1] = b1; bcon_out[2] = b2; bcon_out[3] = b3; }
+  P.bsq = b0 * bc0 + b1 * bc1 + b2 * bc2 + b3 * bc3;
+  P.ne = (rho > (T)0) ? rho * (T)m.Ne_unit : (T)0;
+  P.B = sqrt(fmax(P.bsq, (T)0)) * (T)m.B_unit;
+  if (rho > (T)0 && uu > (T)0) {
+    T trat;
+    if (P.bsq > (T)0) {
+      T beta = uu * ((T)m.gam - (T)1) / ((T)0.5 * P.bsq);
+      T b2x = beta * beta;
+      trat = (T)m.R_high * b2x / ((T)1 + b2x) + (T)m.R_low / ((T)1 + b2x);
+    } else {
+      trat = (T)m.R_high;
+    }
+    T th = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu / rho / ((T)1 + trat);
+    P.thetae = fmin(th, (T)m.thetae_max);
+  } else {
+    P.thetae = (T)0;
+  }
+  P.on = P.ne > (T)0;
+}
+
+// Invariant absorption nu alpha_nu (j/B_nu, section 2.5) and scattering nu n_e sigma_h (section 2.7).
+struct Coef {
+  double ana, ans, thetae;
+};
+
+__device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, const double X[4], const double K[4],
+                                               bool want_s, Coef &c) {
+  c.ana = c.ans = c.thetae = 0.0;
+  double pr[8];
+  if (!interp_prims<double>(m, X, pr)) return;
+  Plasma<double> P;
+  plasma_from_prims<double>(m, G, pr, P, nullptr, nullptr);
+  c.thetae = P.thetae;
+  if (!P.on) return;
+  double eps = -(K[0] * P.ucov[0] + K[1] * P.ucov[1] + K[2] * P.ucov[2] + K[3] * P.ucov[3]);
+  if (!(eps > 0.0)) return;
+  double nu = eps * (kME * kCL * kCL / kHPL);
+  if (P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
+    double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
+    double cth = fmin(1.0, fmax(-1.0, kb / (eps * sqrt(P.bsq))));
+    double s2 = 1.0 - cth * cth;
+    if (s2 > 0.0) {
+      double sth = sqrt(s2);
+      double nus = (2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL)) * P.B * P.thetae * P.thetae * sth;
+      double j = 1.4142135623730951 * kPI * kEE * kEE * P.ne * nus / (3.0 * kCL * K2_of(m, P.thetae)) * Gsyn(nu / nus);
+      if (j > 0.0) {
+        // B_nu = 2 h nu^3 / c^2 / expm1(h nu / kT), kT = Theta_e m_e c^2 so h nu / kT = eps / Theta_e
+        double bnu = 2.0 * kHPL * nu * nu * nu / (kCL * kCL) / expm1(eps / P.thetae);
+        c.ana = nu * j / bnu;
+      }
+    }
+  }
+  if (want_s) c.ans = nu * P.ne * hot_lookup(m, fmax(P.thetae, 1e-300), eps);
+}
+
+// Mixed precision: the same quantities with FP32 plasma state and coefficient arithmetic.
+__device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, const double X[4], const double K[4],
+                                               bool want_s, Coef &c) {
+  c.ana = c.ans = c.thetae = 0.0;
+  float pr[8];
+  if (!interp_prims<float>(m, X, pr)) return;
+  Plasma<float> P;
+  plasma_from_prims<float>(m, G, pr, P, nullptr, nullptr);
+  c.thetae = P.thetae;
+  if (!P.on) return;
+  float kf[4] = {(float)K[0], (float)K[1], (float)K[2], (float)K[3]};
+  float eps = -(kf[0] * P.ucov[0] + kf[1] * P.ucov[1] + kf[2] * P.ucov[2] + kf[3] * P.ucov[3]);
+  if (!(eps > 0.0f)) return;
+  // frequencies and emissivities span ~1e-40..1e40: keep the products in ranges float holds
+  float nu9 = eps * (float)(kME * kCL * kCL / kHPL * 1e-9);   // nu / 1e9 Hz
+  float ana = 0.0f;
+  if (P.thetae >= (float)m.thetae_min && P.B > 0.0f && P.bsq > 0.0f) {
+    float kb = kf[0] * P.bcov[0] + kf[1] * P.bcov[1] + kf[2] * P.bcov[2] + kf[3] * P.bcov[3];
+    float cth = fminf(1.0f, fmaxf(-1.0f, kb / (eps * sqrtf(P.bsq))));
+    float s2 = 1.0f - cth * cth;
+    if (s2 > 0.0f) {
+      float sth = sqrtf(s2);
+      // nu_s / 1e9 Hz
+      float nus9 = (float)((2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL)) * 1e-9) * P.B * P.thetae * P.thetae * sth;
+      float X = nu9 / nus9;
+      float x6 = cbrtf(sqrtf(X));
+      float t = x6 * x6 * x6 + 1.887748625f * x6;
+      float Gs = t * t * __expf(-x6 * x6);
+      // nu alpha_nu = nu j / B_nu = j c^2 expm1(eps/Theta) / (2 h nu^2)
+      //            = [sqrt2 pi e^2 n_e nus / (3 c K2) G] c^2 expm1 / (2 h nu^2)
+      float em1 = expm1f(eps / P.thetae);
+      float pre = (float)(1.4142135623730951 * kPI * kEE * kEE / (3.0 * kCL) * kCL * kCL / (2.0 * kHPL) * 1e-9);
+      // units: n_e [cm^-3] * nus9 / nu9^2 carries the 1e9 scalings: nus/nu^2 = 1e-9 nus9/nu9^2
+      ana = pre * P.ne * nus9 / (nu9 * nu9) / K2_of_f(m, P.thetae) * Gs * em1;
+    }
+  }
+  c.ana = (double)ana;
+  if (want_s) {
+    float sh = hot_lookup_f(m, fmaxf(P.thetae, 1e-30f), eps);
+    c.ans = (double)(nu9 * P.ne * (sh * 1e9f));
+  }
+}
+
+// ---------------------------------------------------------------- bias (section 2.7)
+__device__ __forceinline__ double bias_of(const DevModel &m, double thetae, int nsc) {
+  double b;
+  if (m.bias_mode == 1) b = m.bias_p0 * (nsc + 1.0) * (nsc + 1.0);
+  else if (m.bias_mode == 2) b = m.bias_p0 * thetae * thetae;
+  else b = m.bias_p0;
+  return fmax(1.0, b);
+}
+
+// ---------------------------------------------------------------- tetrads (sections 2.1, 2.7)
+__device__ __forceinline__ void gs_step(const Geo &G, double v[4], const double e[4], double sign) {
+  double d = dot(G, v, e);
+  // sign = +1 for the timelike e0 (e0.e0 = -1), -1 for spacelike unit vectors
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] += sign * d * e[q];
+}
+
+__device__ __forceinline__ bool normalize_space(const Geo &G, double v[4]) {
+  double n2 = dot(G, v, v);
+  if (!(n2 > 1e-30)) return false;
+  double in = 1.0 / sqrt(n2);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] *= in;
+  return true;
+}
+
+__device__ __forceinline__ double gdiag(const Geo &G, int k) {
+  return (k == 1) ? G.g11 : ((k == 2) ? G.g22 : G.g33);
+}
+
+// Emission tetrad: e0 = u, e3 = b/|b|, e1 and e2 from the coordinate directions keeping the
+// largest part after projection (first index on ties).
+static __device__ void tetrad_emission(const Geo &G, const double u[4], const double b[4], double bsq, double e[4][4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[0][q] = u[q];
+  double ib = 1.0 / sqrt(bsq);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[3][q] = b[q] * ib;
+  double best = -1.0;
+  double t1[4] = {0, 0, 0, 0};
+  int pick = 1;
+  for (int k = 1; k < 4; ++k) {
+    double t[4] = {0, 0, 0, 0};
+    t[k] = 1.0;
+    gs_step(G, t, e[0], 1.0);
+    gs_step(G, t, e[3], -1.0);
+    double fr = dot(G, t, t) / gdiag(G, k);
+    if (fr > best) {
+      best = fr;
+      pick = k;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t1[q] = t[q];
+    }
+  }
+  normalize_space(G, t1);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[1][q] = t1[q];
+  best = -1.0;
+  double t2[4] = {0, 0, 0, 0};
+  for (int k = 1; k < 4; ++k) {
+    if (k == pick) continue;
+    double t[4] = {0, 0, 0, 0};
+    t[k] = 1.0;
+    gs_step(G, t, e[0], 1.0);
+    gs_step(G, t, e[3], -1.0);
+    gs_step(G, t, e[1], -1.0);
+    double fr = dot(G, t, t) / gdiag(G, k);
+    if (fr > best) {
+      best = fr;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t2[q] = t[q];
+    }
+  }
+  normalize_space(G, t2);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[2][q] = t2[q];
+}
+
+// Scattering tetrad: e0 = u, e1..e3 from the x1, x2, x3 directions by Gram-Schmidt.
+static __device__ void tetrad_scatter(const Geo &G, const double u[4], double e[4][4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[0][q] = u[q];
+  for (int k = 1; k < 4; ++k) {
+    double t[4] = {0, 0, 0, 0};
+    t[k] = 1.0;
+    gs_step(G, t, e[0], 1.0);
+    for (int p = 1; p < k; ++p) gs_step(G, t, e[p], -1.0);
+    normalize_space(G, t);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[k][q] = t[q];
+  }
+}
+
+// ---------------------------------------------------------------- Compton kinematics (section 2.7)
+__device__ __forceinline__ double sigma_kn_ratio(double e) {
+  if (e < 1e-3) return 1.0 - 2.0 * e;
+  double e2 = e * e, o2 = 1.0 + 2.0 * e;
+  return 0.75 / e2 * (2.0 + e2 * (1.0 + e) / (o2 * o2) + (e2 - 2.0 * e - 2.0) / (2.0 * e) * log1p(2.0 * e));
+}
+
+constexpr int kMaxTry = 10000;
+
+// Maxwell-Juettner Lorentz factor: Sobol's method (Pozdnyakov, Sobol & Sunyaev 1983) for
+// Theta >= 0.25; below, rejection from the Gamma(3/2, 5/2, 7/2) mixture bounding
+// sqrt(t) (1+t) sqrt(t+2) e^{-t/Theta}, t = gamma - 1.
+static __device__ double sample_mj(double th, Rng &s, uint64_t seed) {
+  if (th >= 0.25) {
+    for (int it = 0; it < kMaxTry; ++it) {
+      double u1 = rng_u(s, seed), u2 = rng_u(s, seed), u3 = rng_u(s, seed), u4 = rng_u(s, seed);
+      double p = -th * log(u1 * u2 * u3);
+      double eta = p - th * log(u4);
+      if (eta * eta - p * p > 1.0 || it == kMaxTry - 1) return sqrt(1.0 + p * p);
+    }
+  }
+  double c1 = 0.886226925452758 * pow(th, 1.5);
+  double c2 = 1.25 * 1.329340388179137 * pow(th, 2.5);
+  double c3 = 0.25 * 3.323350970447843 * pow(th, 3.5);
+  double ct = c1 + c2 + c3;
+  double t = 0.0;
+  for (int it = 0; it < kMaxTry; ++it) {
+    double uc = rng_u(s, seed) * ct;
+    int k = (uc < c1) ? 1 : ((uc < c1 + c2) ? 2 : 3);
+    double prod = 1.0;
+    for (int i = 0; i < k; ++i) prod *= rng_u(s, seed);
+    double ua = rng_u(s, seed), ub = rng_u(s, seed);
+    double z = sqrt(-2.0 * log(ua)) * cospi(2.0 * ub);
+    t = th * (-log(prod) + 0.5 * z * z);
+    double acc = (1.0 + t) * sqrt(t + 2.0) / (1.4142135623730951 * (1.0 + 1.25 * t + 0.25 * t * t));
+    if (rng_u(s, seed) < acc) break;
+  }
+  return 1.0 + t;
+}
+
+__device__ __forceinline__ void perp_basis(const double n[3], double e1[3], double e2[3]) {
+  double a0 = 1.0, a1 = 0.0;
+  if (fabs(n[0]) >= 0.6) { a0 = 0.0; a1 = 1.0; }
+  double d = a0 * n[0] + a1 * n[1];
+  e1[0] = a0 - d * n[0];
+  e1[1] = a1 - d * n[1];
+  e1[2] = -d * n[2];
+  double il = 1.0 / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  e1[0] *= il; e1[1] *= il; e1[2] *= il;
+  e2[0] = n[1] * e1[2] - n[2] * e1[1];
+  e2[1] = n[2] * e1[0] - n[0] * e1[2];
+  e2[2] = n[0] * e1[1] - n[1] * e1[0];
+}
+
+__device__ __forceinline__ void boost3(double E, const double p[3], double beta, const double v[3], double &Eo,
+                                       double po[3]) {
+  double gam = 1.0 / sqrt(1.0 - beta * beta);
+  double pv = p[0] * v[0] + p[1] * v[1] + p[2] * v[2];
+  Eo = gam * (E - beta * pv);
+  double ppar = gam * (pv - beta * E);
+  po[0] = p[0] + (ppar - pv) * v[0];
+  po[1] = p[1] + (ppar - pv) * v[1];
+  po[2] = p[2] + (ppar - pv) * v[2];
+}
+
+// Scattered photon in the plasma frame for incoming energy eps along unit n; draws in the order
+// [gamma (MJ), mu_e, accept]*, phi_e, [cos, accept]*, phi.
+static __device__ void compton_fluid(double th, double eps, const double n[3], Rng &s, uint64_t seed, double &eo,
+                              double dir[3], int &rejcap) {
+  double gam = 1.0, mue = 0.0, beta = 0.0;
+  int it;
+  for (it = 0; it < kMaxTry; ++it) {
+    gam = sample_mj(th, s, seed);
+    mue = 2.0 * rng_u(s, seed) - 1.0;
+    beta = sqrt(1.0 - 1.0 / (gam * gam));
+    double om = 1.0 - beta * mue;
+    double acc = om * sigma_kn_ratio(eps * gam * om) * 0.5;
+    if (rng_u(s, seed) < acc) break;
+  }
+  if (it == kMaxTry) rejcap++;
+  double phie = 2.0 * rng_u(s, seed);   // in units of pi
+  double e1[3], e2[3];
+  perp_basis(n, e1, e2);
+  double se = sqrt(fmax(0.0, 1.0 - mue * mue));
+  double sp, cp;
+  sincospi(phie, &sp, &cp);
+  double v[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = mue * n[i] + se * (cp * e1[i] + sp * e2[i]);
+  double pin[3] = {eps * n[0], eps * n[1], eps * n[2]};
+  double ee, pe[3];
+  boost3(eps, pin, beta, v, ee, pe);
+  double il = 1.0 / sqrt(pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]);
+  double ne[3] = {pe[0] * il, pe[1] * il, pe[2] * il};
+  double ct = 1.0, ep = ee;
+  for (it = 0; it < kMaxTry; ++it) {
+    ct = 2.0 * rng_u(s, seed) - 1.0;
+    ep = ee / (1.0 + ee * (1.0 - ct));
+    double P;
+    if (ee < 1e-4) {
+      P = 0.5 * (1.0 + ct * ct);
+    } else {
+      double r = ep / ee;
+      P = 0.5 * r * r * (r + 1.0 / r - (1.0 - ct * ct));
+    }
+    if (rng_u(s, seed) < P) break;
+  }
+  if (it == kMaxTry) rejcap++;
+  double phi = 2.0 * rng_u(s, seed);
+  double f1[3], f2[3];
+  perp_basis(ne, f1, f2);
+  double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+  sincospi(phi, &sp, &cp);
+  double pp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pp[i] = ep * (ct * ne[i] + st * (cp * f1[i] + sp * f2[i]));
+  double Ef, pf[3];
+  boost3(ep, pp, -beta, v, Ef, pf);
+  eo = Ef;
+  dir[0] = pf[0];
+  dir[1] = pf[1];
+  dir[2] = pf[2];
+}
+
+}  // namespace mcgb

@@ -1,0 +1,62 @@
+// mc_internal.h -- declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mc.h"
+#include "mc_device.cuh"
+
+namespace mcgb {
+
+// Scattered-superphoton queue of one generation (structure of arrays).
+struct ChildBuf {
+  double *X[4];
+  double *K[4];
+  double *w;
+  uint64_t *id;
+  uint32_t *ctr;
+  int32_t *nsc;
+};
+
+// Counters written by the transport kernel (unsigned 64-bit for atomics).
+enum {
+  CNT_NEXT = 0,   // work-item cursor
+  CNT_OUT,        // children appended
+  CNT_LOG,        // log records appended
+  CNT_ERR,        // error bits
+  CNT_EMIT, CNT_CHILD, CNT_REC, CNT_ABS, CNT_CAPT, CNT_MAXST,
+  CNT_STEPS, CNT_ITERS, CNT_NONCONV, CNT_ROUL, CNT_REJCAP, CNT_EVENTS,
+  CNT_N
+};
+
+struct RoundIO {
+  int mode;                 // 0: primaries uid0 .. uid0+n_items; 1: uid list; 2: children
+  int64_t uid0, n_items;
+  const int64_t *uids;
+  ChildBuf in, out;
+  int64_t out_cap;
+  double *spec;             // [n_incl][n_bins][3]
+  unsigned long long *cnt;  // CNT_N counters
+  mc_log_rec *log;
+  int64_t log_cap;
+};
+
+// tables (mc_tables.cu)
+void launch_tables(const DevModel &m, double *lnF, double *lnK2, double *hot, const double *gl_ang,
+                   const double *gl_s, const double *gl_mu, cudaStream_t st);
+// generation (mc_tables.cu)
+void launch_zone_prep(const DevModel &m, double *zvol, double *zpref, double *zlnuc, int *bad, cudaStream_t st);
+void launch_weights(const DevModel &m, const double *zvol, const double *zpref, const double *zlnuc, double *partial,
+                    int nchunks, double n_s, double w_min, double *lnw, double *winv, cudaStream_t st);
+void launch_counts(const DevModel &m, const double *zvol, const double *zpref, const double *zlnuc, double *zgmax,
+                   double *znbar, int64_t *counts, cudaStream_t st);
+void launch_scan(const int64_t *counts, int64_t *start, int64_t *bsum, int64_t n, int64_t *total_dev, cudaStream_t st);
+// grid conversion (mc_tables.cu): caller layout [8][nz] -> zone-major [nz][8]
+void launch_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, int64_t nz, int *bad, cudaStream_t st);
+// FMA-chain throughput of the FP64 or FP32 pipe in FLOP/s (mc_tables.cu)
+cudaError_t fma_peak(bool fp64, double *flops);
+// transport (mc_transport.cu)
+int transport_max_blocks_per_sm(int mixed, int block);
+void launch_transport(const DevModel &m, const RoundIO &io, int mixed, int grid, int block, cudaStream_t st);
+
+}  // namespace mcgb

@@ -1,0 +1,340 @@
+// mc_tables.cu -- lookup tables and per-run superphoton generation (sections 2.1-2.3, 2.7).
+//
+// Tables built once per context on the device:
+//   * ln F(K), F(K) = int_0^{pi/2} sin^2(th) G(K/sin th) dth, G(X) = (X^1/2 + 2^11/12 X^1/6)^2 e^{-X^1/3}:
+//     the angle-integrated emissivity is int dOmega j_nu = 4 pi A nu_c F(nu/nu_c) (64-node Gauss-Legendre);
+//   * ln K2(1/Theta) from K_2(x) = int_0^inf exp(-x cosh t) cosh 2t dt (trapezoid rule, which converges
+//     geometrically for this entire integrand);
+//   * ln(sigma_h / sigma_T) on the (Theta_e, eps) grid: Maxwell-Juettner average of (1 - mu beta)
+//     sigma_KN with gamma = 1 + Theta s^2 (64 nodes, s in [0, 8]) and mu (32 nodes).
+// Per run: zone volumes and emission prefactors, the weight table w(nu_j) (eq. weight_calc, a
+// deterministic two-pass reduction over zones), expected zone counts, their stochastic rounding
+// with the zone's Philox stream, and an exclusive scan giving each zone's first superphoton uid.
+#include "mc_internal.h"
+
+namespace mcgb {
+
+// ---------------------------------------------------------------- tables
+__global__ void k_table_F(double *lnF, int n, const double *glx, const double *glw) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double K = exp(kFLnK0 + i * kFStep);
+  double s = 0.0;
+  for (int q = 0; q < 64; ++q) {
+    double st = sin(glx[q]);
+    s += glw[q] * st * st * Gsyn(K / st);
+  }
+  lnF[i] = log(s);
+}
+
+__global__ void k_table_K2(double *lnK2, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x = exp(-(kK2LnT0 + i * kK2Step));   // x = 1 / Theta
+  const double h = 1.0 / 64.0;
+  double s = 0.5 * exp(-x);
+  for (int q = 1; q < 4096; ++q) {
+    double t = q * h;
+    double ch = cosh(t);
+    if (x * ch > 800.0) break;
+    s += exp(-x * ch) * cosh(2.0 * t);
+  }
+  lnK2[i] = log(s * h);
+}
+
+__global__ void k_table_hot(double *hot, const double *gsx, const double *gsw, const double *gmx, const double *gmw) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kHotNT * kHotNE) return;
+  int i = idx / kHotNE, j = idx % kHotNE;
+  double th = exp(kHotLT0 + (kHotLT1 - kHotLT0) * i / (kHotNT - 1));
+  double e = exp(kHotLE0 + (kHotLE1 - kHotLE0) * j / (kHotNE - 1));
+  double num = 0.0, den = 0.0;
+  for (int a = 0; a < 64; ++a) {
+    double s = gsx[a];
+    double gam = 1.0 + th * s * s;
+    double hs = gam * s * s * sqrt(th * (2.0 + th * s * s)) * exp(-s * s);
+    double beta = sqrt(1.0 - 1.0 / (gam * gam));
+    double q = 0.0;
+    for (int b = 0; b < 32; ++b) {
+      double om = 1.0 - gmx[b] * beta;
+      q += gmw[b] * om * sigma_kn_ratio(e * gam * om);
+    }
+    num += gsw[a] * hs * 0.5 * q;
+    den += gsw[a] * hs;
+  }
+  hot[idx] = log(num / den);
+}
+
+void launch_tables(const DevModel &m, double *lnF, double *lnK2, double *hot, const double *gl_ang, const double *gl_s,
+                   const double *gl_mu, cudaStream_t st) {
+  k_table_F<<<(m.nF + 127) / 128, 128, 0, st>>>(lnF, m.nF, gl_ang, gl_ang + 64);
+  k_table_K2<<<(m.nK2 + 127) / 128, 128, 0, st>>>(lnK2, m.nK2);
+  k_table_hot<<<(kHotNT * kHotNE + 127) / 128, 128, 0, st>>>(hot, gl_s, gl_s + 64, gl_mu, gl_mu + 32);
+}
+
+// ---------------------------------------------------------------- grid layout
+__global__ void k_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, int64_t nz, int *bad) {
+  int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  for (int f = 0; f < 8; ++f) {
+    double v = src_f32 ? (double)((const float *)src)[f * nz + z] : ((const double *)src)[f * nz + z];
+    if (!isfinite(v)) atomicOr(bad, 1);
+    if (dst_f32) ((float *)dst)[z * 8 + f] = (float)v;
+    else ((double *)dst)[z * 8 + f] = v;
+  }
+}
+
+void launch_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, int64_t nz, int *bad, cudaStream_t st) {
+  k_grid_to_aos<<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(src, src_f32, dst, dst_f32, nz, bad);
+}
+
+// ---------------------------------------------------------------- zones
+__device__ __forceinline__ void zone_centre(const DevModel &m, int64_t z, double X[4]) {
+  int64_t i = z / ((int64_t)m.n2 * m.n3);
+  int64_t j = (z / m.n3) % m.n2;
+  int64_t k = z % m.n3;
+  X[0] = 0.0;
+  X[1] = m.x1_0 + (i + 0.5) * m.dx1;
+  X[2] = m.x2_0 + (j + 0.5) * m.dx2;
+  X[3] = m.x3_0 + (k + 0.5) * m.dx3;
+}
+
+__device__ __forceinline__ void zone_prims(const DevModel &m, int64_t z, double pr[8]) {
+  if (m.prim_f32) {
+    for (int f = 0; f < 8; ++f) pr[f] = (double)m.prim32[z * 8 + f];
+  } else {
+    for (int f = 0; f < 8; ++f) pr[f] = m.prim64[z * 8 + f];
+  }
+}
+
+// Zone volume sqrt(-g) d^3x L^3 (sqrt(-g) = Sigma sin(theta) r dtheta/dx2 for MKS Kerr-Schild) and the
+// emission prefactor 4 pi A nu_c, A = sqrt(2) pi e^2 n_e / (3 c K2(1/Theta_e)), from the zone-centre state.
+__global__ void k_zone_prep(DevModel m, double *zvol, double *zpref, double *zlnuc, int *bad) {
+  int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= m.nz) return;
+  double X[4];
+  zone_centre(m, z, X);
+  Geo G;
+  metric_eval<false>(m, X[1], X[2], G);
+  double th, dth, d2th;
+  theta_map(m.hslope, X[2], th, dth, d2th);
+  double sig = G.r * G.r + m.a * m.a * G.cth * G.cth;
+  zvol[z] = sig * G.sth * G.r * dth * m.dx1 * m.dx2 * m.dx3 * m.L3;
+  double pr[8];
+  zone_prims(m, z, pr);
+  Plasma<double> P;
+  plasma_from_prims<double>(m, G, pr, P, nullptr, nullptr);
+  if (!isfinite(P.thetae) || !isfinite(P.B) || !isfinite(P.ne)) atomicOr(bad, 2);
+  double pref = 0.0, lnuc = 0.0;
+  if (P.thetae >= m.thetae_min && P.ne > 0.0 && P.B > 0.0) {
+    double nuc = (2.0 / 9.0) * (kEE * P.B / (2.0 * kPI * kME * kCL)) * P.thetae * P.thetae;
+    double A = 1.4142135623730951 * kPI * kEE * kEE * P.ne / (3.0 * kCL * K2_of(m, P.thetae));
+    pref = 4.0 * kPI * A * nuc;
+    lnuc = log(nuc);
+  }
+  zpref[z] = pref;
+  zlnuc[z] = lnuc;
+}
+
+void launch_zone_prep(const DevModel &m, double *zvol, double *zpref, double *zlnuc, int *bad, cudaStream_t st) {
+  k_zone_prep<<<(unsigned)((m.nz + 127) / 128), 128, 0, st>>>(m, zvol, zpref, zlnuc, bad);
+}
+
+// int dOmega j_nu at node j for a zone (0 when the zone does not emit)
+__device__ __forceinline__ double zone_E(const DevModel &m, double pref, double lnuc, int j) {
+  if (pref == 0.0) return 0.0;
+  return pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc);
+}
+
+constexpr int kChunk = 2048;
+
+// partial[j][chunk] = sum over the chunk's zones of V_i int dOmega j_nu(nu_j): fixed assignment and a
+// fixed reduction tree, so the weights are bit-reproducible run to run.
+__global__ void k_weight_partial(DevModel m, const double *zvol, const double *zpref, const double *zlnuc,
+                                 double *partial, int nchunks) {
+  __shared__ double red[256];
+  int chunk = blockIdx.x, j = blockIdx.y;
+  int64_t z0 = (int64_t)chunk * kChunk;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
+    int64_t z = z0 + q;
+    if (z < m.nz) s += zvol[z] * zone_E(m, zpref[z], zlnuc[z], j);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(int64_t)j * nchunks + chunk] = red[0];
+}
+
+// w_j = max(w_min, dt dln(nu)_tot / (h N_s) sum_i V_i int dOmega j_nu(nu_j)), dt = 1 (cancels in nu L_nu)
+__global__ void k_weight_final(DevModel m, const double *partial, int nchunks, double n_s, double w_min, double *lnw,
+                               double *winv) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m.n_nu) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += partial[(int64_t)j * nchunks + c];
+  double w = fmax(w_min, m.dlntot / (kHPL * n_s) * s);
+  lnw[j] = log(w);
+  winv[j] = 1.0 / w;
+}
+
+void launch_weights(const DevModel &m, const double *zvol, const double *zpref, const double *zlnuc, double *partial,
+                    int nchunks, double n_s, double w_min, double *lnw, double *winv, cudaStream_t st) {
+  dim3 grid(nchunks, m.n_nu);
+  k_weight_partial<<<grid, 256, 0, st>>>(m, zvol, zpref, zlnuc, partial, nchunks);
+  k_weight_final<<<(m.n_nu + 127) / 128, 128, 0, st>>>(m, partial, nchunks, n_s, w_min, lnw, winv);
+}
+
+// Expected count nbar_i = V_i sum_j T_j g_ij / h (trapezoid in ln nu, g_ij = int dOmega j_nu / w_j), its
+// maximum g over nodes (rejection bound), and N_i = floor(nbar) + [u_i < frac(nbar)], u_i the first
+// uniform of the zone's stream.
+__global__ void k_zone_counts(DevModel m, const double *zvol, const double *zpref, const double *zlnuc, double *zgmax,
+                              double *znbar, int64_t *counts) {
+  int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= m.nz) return;
+  double pref = zpref[z], lnuc = zlnuc[z];
+  double s = 0.0, gm = 0.0;
+  if (pref != 0.0) {
+    for (int j = 0; j < m.n_nu; ++j) {
+      double g = zone_E(m, pref, lnuc, j) * m.winv[j];
+      double t = (j == 0 || j == m.n_nu - 1) ? 0.5 * m.dlnu : m.dlnu;
+      s += t * g;
+      gm = fmax(gm, g);
+    }
+  }
+  double nb = zvol[z] * s / kHPL;
+  znbar[z] = nb;
+  zgmax[z] = gm;
+  double fl = floor(nb);
+  Rng r;
+  rng_init(r, kZoneTag | (uint64_t)z, 0u);
+  double u = rng_u(r, m.seed);
+  counts[z] = (int64_t)fl + ((u < nb - fl) ? 1 : 0);
+}
+
+void launch_counts(const DevModel &m, const double *zvol, const double *zpref, const double *zlnuc, double *zgmax,
+                   double *znbar, int64_t *counts, cudaStream_t st) {
+  k_zone_counts<<<(unsigned)((m.nz + 127) / 128), 128, 0, st>>>(m, zvol, zpref, zlnuc, zgmax, znbar, counts);
+}
+
+// ---------------------------------------------------------------- exclusive scan (int64)
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t *sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  if (wid > 0) v += sh[wid - 1];
+  return v;
+}
+
+__global__ void k_scan_local(const int64_t *in, int64_t *out, int64_t *bsum, int64_t n) {
+  __shared__ int64_t sh[32];
+  int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  int64_t v = (i < n) ? in[i] : 0;
+  int64_t inc = block_incl_scan(v, sh);
+  if (i < n) out[i] = inc - v;
+  if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = inc;
+}
+
+__global__ void k_scan_sums(int64_t *bsum, int64_t nb, int64_t *total) {
+  __shared__ int64_t sh[32];
+  // each thread owns a contiguous run of block sums
+  int64_t per = (nb + kScanBlock - 1) / kScanBlock;
+  int64_t b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+  int64_t loc = 0;
+  for (int64_t b = b0; b < b1; ++b) loc += bsum[b];
+  int64_t inc = block_incl_scan(loc, sh);
+  int64_t run = inc - loc;
+  for (int64_t b = b0; b < b1; ++b) {
+    int64_t v = bsum[b];
+    bsum[b] = run;
+    run += v;
+  }
+  if (threadIdx.x == kScanBlock - 1) *total = inc;
+}
+
+__global__ void k_scan_add(int64_t *out, const int64_t *bsum, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+void launch_scan(const int64_t *counts, int64_t *start, int64_t *bsum, int64_t n, int64_t *total_dev, cudaStream_t st) {
+  int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  k_scan_local<<<(unsigned)nb, kScanBlock, 0, st>>>(counts, start, bsum, n);
+  k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, nb, total_dev);
+  k_scan_add<<<(unsigned)nb, kScanBlock, 0, st>>>(start, bsum, n);
+}
+
+// ---------------------------------------------------------------- pipe peak (FMA chains)
+// Eight independent FMA chains per thread keep the pipe busy without memory traffic; the result
+// is stored only under a data-dependent condition that never holds, so nothing is optimised away.
+template <typename T>
+__global__ void k_fma_chain(T *sink, int iters, T seed) {
+  T a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  const T m = (T)0.999999, c = (T)1e-7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      a0 = a0 * m + c; a1 = a1 * m + c; a2 = a2 * m + c; a3 = a3 * m + c;
+      a4 = a4 * m + c; a5 = a5 * m + c; a6 = a6 * m + c; a7 = a7 * m + c;
+    }
+  }
+  T s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == (T)-12345.0) sink[threadIdx.x] = s;
+}
+
+template <typename T>
+static cudaError_t fma_peak_t(double *flops) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  T *sink = nullptr;
+  cudaError_t e = cudaMalloc(&sink, 1024 * sizeof(T));
+  if (e != cudaSuccess) return e;
+  const int block = 256, grid = sms * 8;
+  const int iters = sizeof(T) == 8 ? 256 : 4096;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fma_chain<T><<<grid, block>>>(sink, iters / 8, (T)1);   // warm-up
+  double best = 0.0;
+  for (int rep = 0; rep < 5; ++rep) {
+    cudaEventRecord(e0);
+    k_fma_chain<T><<<grid, block>>>(sink, iters, (T)1);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    double fl = 2.0 * 8.0 * 16.0 * (double)iters * (double)grid * block;
+    best = fmax(best, fl / (ms * 1e-3));
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  *flops = best;
+  return e;
+}
+
+cudaError_t fma_peak(bool fp64, double *flops) { return fp64 ? fma_peak_t<double>(flops) : fma_peak_t<float>(flops); }
+
+}  // namespace mcgb

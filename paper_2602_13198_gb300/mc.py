@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C ABI in ``include/mc.h`` (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library ``libmcgb.so``; this module only
+fills the parameter structs, hands PyTorch's caching allocator to the library, and
+copies results out.  Importing works without a GPU; creating a :class:`Model` without
+one raises :class:`MCError` (``MC_ERR_NO_DEVICE``).  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmcgb.so")
+
+MC_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "NO_DEVICE", -3: "OOM", -4: "TIMEOUT", -5: "QUEUE_OVERFLOW",
+          -6: "NAN_INPUT", -7: "SIZE", -8: "STATE", -9: "CUDA"}
+PREC = {"fp64": 0, "mixed": 1}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class MCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class ModelParams(C.Structure):
+    _fields_ = [
+        ("a", C.c_double), ("mass", C.c_double), ("hslope", C.c_double),
+        ("L_unit", C.c_double), ("M_unit", C.c_double),
+        ("R_high", C.c_double), ("R_low", C.c_double), ("gam", C.c_double),
+        ("thetae_min", C.c_double), ("thetae_max", C.c_double),
+        ("nu_min", C.c_double), ("nu_max", C.c_double), ("w_min", C.c_double), ("n_s", C.c_double),
+        ("eps_geo", C.c_double), ("verlet_tol", C.c_double), ("r_record", C.c_double), ("dh", C.c_double),
+        ("bias_p0", C.c_double), ("lnu_lo", C.c_double), ("lnu_hi", C.c_double),
+        ("roulette_w", C.c_double), ("roulette_p", C.c_double),
+        ("max_steps", C.c_int64),
+        ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32), ("n_sc_max", C.c_int32),
+        ("n_bins", C.c_int32), ("n_incl", C.c_int32), ("k2_mode", C.c_int32), ("scatter", C.c_int32),
+        ("precision", C.c_int32), ("surrogate", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
+        ("device", C.c_int32), ("pad0", C.c_int32),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+    ]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [
+        ("n1", C.c_int32), ("n2", C.c_int32), ("n3", C.c_int32), ("dtype", C.c_int32),
+        ("x1_0", C.c_double), ("dx1", C.c_double), ("x2_0", C.c_double), ("dx2", C.c_double),
+        ("x3_0", C.c_double), ("dx3", C.c_double),
+        ("location", C.c_int32), ("pad0", C.c_int32), ("prim", C.c_void_p),
+    ]
+
+
+STAT_NAMES = ("n_emit", "n_child", "n_rec", "n_abs", "n_capt", "n_maxst", "n_steps", "n_iters",
+              "n_nonconv", "n_roul_surv", "n_rej_cap", "n_events", "n_total", "err_flags",
+              "transport_launches", "transport_ms", "generate_ms")
+
+
+class RunStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in STAT_NAMES[:-2]] + [("transport_ms", C.c_double), ("generate_ms", C.c_double)]
+
+    def as_dict(self):
+        d = {n: int(getattr(self, n)) for n in STAT_NAMES[:-2]}
+        d["transport_ms"] = float(self.transport_ms)
+        d["generate_ms"] = float(self.generate_ms)
+        return d
+
+
+LOG_DTYPE = np.dtype([
+    ("id", np.uint64), ("gen", np.int32), ("status", np.int32),
+    ("X", np.float64, 4), ("K", np.float64, 4), ("w", np.float64),
+    ("nsteps", np.int64), ("nev", np.int32), ("pad", np.int32)])
+
+_lib = None
+
+
+def lib():
+    """Loads libmcgb.so; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MCError(-9, "CUDA library %s missing: run paper_2602_13198_gb300.build.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i64, u64, sz, dp = C.c_void_p, C.c_int64, C.c_uint64, C.c_size_t, C.POINTER(C.c_double)
+        L.mc_init_model.argtypes = [C.POINTER(vp), C.POINTER(ModelParams)]
+        L.mc_set_grid.argtypes = [vp, C.POINTER(GridDesc)]
+        L.mc_run.argtypes = [vp, C.c_double, u64, i64, i64, vp, C.POINTER(RunStats)]
+        L.mc_get_spectrum.argtypes = [vp, dp, dp, dp, sz]
+        L.mc_get_spectrum_sums.argtypes = [vp, dp, sz]
+        L.mc_get_zone_counts.argtypes = [vp, C.POINTER(i64), sz]
+        L.mc_trace.argtypes = [vp, C.c_double, u64, C.POINTER(i64), sz, vp, sz, C.POINTER(sz), vp]
+        L.mc_free.argtypes = [vp]
+        L.mc_free.restype = None
+        L.mc_last_error.argtypes = [vp]
+        L.mc_last_error.restype = C.c_char_p
+        L.mc_version.restype = C.c_char_p
+        L.mc_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
+        L.mc_fma_peak.restype = C.c_int
+        for f in ("mc_init_model", "mc_set_grid", "mc_run", "mc_get_spectrum", "mc_get_spectrum_sums",
+                  "mc_get_zone_counts", "mc_trace"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _torch_allocator():
+    """Device allocator callbacks backed by PyTorch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, user):
+        dev = torch.cuda.current_device()
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev))
+
+    def _free(ptr, user):
+        if ptr:
+            torch.cuda.caching_allocator_delete(ptr)
+    return ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+class Model:
+    """One model context: ``Model(params, device=0)`` then ``set_grid`` and ``run``."""
+
+    def __init__(self, params: dict, device: int = 0, precision: str = "fp64", use_torch_allocator: bool = True,
+                 block: int = 0, ctas_per_sm: int = 0):
+        L = lib()
+        p = ModelParams()
+        for name, _ in ModelParams._fields_:
+            if name in params and name not in ("alloc", "free", "alloc_user"):
+                setattr(p, name, params[name])
+        p.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        p.surrogate = 0
+        p.block = block
+        p.ctas_per_sm = ctas_per_sm
+        p.device = device
+        self._cb = None
+        if use_torch_allocator:
+            import torch
+            torch.cuda.set_device(device)
+            self._cb = _torch_allocator()
+            p.alloc, p.free = self._cb
+        self.params = dict(params)
+        self._p = p
+        h = C.c_void_p()
+        rc = L.mc_init_model(C.byref(h), C.byref(p))
+        if rc != MC_OK:
+            raise MCError(rc, L.mc_last_error(None).decode())
+        self._h = h
+        self.n_incl = int(params["n_incl"])
+        self.n_bins = int(params["n_bins"])
+        self.nz = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != MC_OK:
+            raise MCError(rc, lib().mc_last_error(self._h).decode())
+
+    def set_grid(self, grid: dict, prim=None):
+        """``grid`` from :mod:`synth`; ``prim`` may be a CUDA torch tensor [8, nz] (device copy) or
+        None to pass ``grid['prim']`` (a numpy array) from host memory."""
+        g = GridDesc()
+        g.n1, g.n2, g.n3 = grid["n1"], grid["n2"], grid["n3"]
+        for k in ("x1_0", "dx1", "x2_0", "dx2", "x3_0", "dx3"):
+            setattr(g, k, grid[k])
+        keep = None
+        if prim is not None and hasattr(prim, "is_cuda") and prim.is_cuda:
+            keep = prim.contiguous()
+            g.dtype = 1 if str(keep.dtype) == "torch.float32" else 0
+            g.location = 1
+            g.prim = keep.data_ptr()
+        else:
+            arr = grid["prim"] if prim is None else prim
+            keep = np.ascontiguousarray(arr)
+            if keep.dtype == np.float32:
+                g.dtype = 1
+            else:
+                keep = np.ascontiguousarray(keep, dtype=np.float64)
+                g.dtype = 0
+            g.location = 0
+            g.prim = keep.ctypes.data
+        self._check(lib().mc_set_grid(self._h, C.byref(g)))
+        self.nz = g.n1 * g.n2 * g.n3
+
+    def run(self, n_s: float, seed: int, shard: int = 0, n_shards: int = 1, stream=None) -> dict:
+        st = RunStats()
+        s = C.c_void_p(stream) if isinstance(stream, int) else C.c_void_p(getattr(stream, "cuda_stream", 0) or 0)
+        self._check(lib().mc_run(self._h, float(n_s), int(seed), int(shard), int(n_shards), s, C.byref(st)))
+        return st.as_dict()
+
+    def spectrum(self):
+        n = self.n_incl * self.n_bins
+        nuL, sig, cnt = np.zeros(n), np.zeros(n), np.zeros(n)
+        dp = C.POINTER(C.c_double)
+        self._check(lib().mc_get_spectrum(self._h, nuL.ctypes.data_as(dp), sig.ctypes.data_as(dp),
+                                          cnt.ctypes.data_as(dp), n))
+        sh = (self.n_incl, self.n_bins)
+        return nuL.reshape(sh), sig.reshape(sh), cnt.reshape(sh)
+
+    def spectrum_sums(self):
+        n = self.n_incl * self.n_bins * 3
+        out = np.zeros(n)
+        self._check(lib().mc_get_spectrum_sums(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n))
+        return out.reshape(self.n_incl, self.n_bins, 3)
+
+    def zone_counts(self):
+        out = np.zeros(self.nz, dtype=np.int64)
+        self._check(lib().mc_get_zone_counts(self._h, out.ctypes.data_as(C.POINTER(C.c_int64)), self.nz))
+        return out
+
+    def trace(self, n_s: float, seed: int, uids, cap: int | None = None, stream=None):
+        u = np.ascontiguousarray(uids, dtype=np.int64)
+        if cap is None:
+            cap = max(64, 64 * len(u))
+        out = np.zeros(cap, dtype=LOG_DTYPE)
+        n = C.c_size_t(0)
+        s = C.c_void_p(getattr(stream, "cuda_stream", 0) or 0) if stream is not None else C.c_void_p(0)
+        self._check(lib().mc_trace(self._h, float(n_s), int(seed), u.ctypes.data_as(C.POINTER(C.c_int64)), len(u),
+                                   out.ctypes.data, cap, C.byref(n), s))
+        return out[: n.value].copy()
+
+
+def fma_peak(device: int = 0, fp64: bool = True) -> float:
+    """FP64 (or FP32) FMA-chain throughput of the device in FLOP/s."""
+    f = C.c_double(0.0)
+    rc = lib().mc_fma_peak(device, 0 if fp64 else 1, C.byref(f))
+    if rc != MC_OK:
+        raise MCError(rc, lib().mc_last_error(None).decode())
+    return f.value
+
+
+def version() -> str:
+    return lib().mc_version().decode()

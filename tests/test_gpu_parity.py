@@ -1,0 +1,158 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded
+inputs.  Zone counts bit-exact; per-superphoton FP64 end states within 1e-9 relative
+(decision flips counted and bounded); spectra within max(1%, 3 Monte Carlo sigma)."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import compare_logs, flat_sphere, gpu_model, oracle_model, requires_gpu, spectra_agree
+from paper_2602_13198_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def cases():
+    out = {}
+    out["flat_thin"] = flat_sphere()
+    # Schwarzschild sphere of radius 10 GM/c^2 (n_e 1e13, Theta_e 10, B 10 G), full 1024 x 128 grid
+    out["ks_sphere"] = synth.sphere("ks")
+    # scattering sphere, tau_T = 0.1 (frequent scattering, bias clamps to 1)
+    out["ks_scatter"] = synth.scattering_sphere(0.1, n1=256, n2=64)
+    return out
+
+
+@pytest.fixture(scope="module")
+def case_data():
+    return cases()
+
+
+@pytest.mark.parametrize("name,n_s,seed", [("flat_thin", 3e4, 1), ("ks_sphere", 1e5, 1), ("ks_scatter", 2e4, 2)])
+def test_zone_counts_bit_exact(case_data, name, n_s, seed):
+    p, g = case_data[name]
+    gm = gpu_model(p, g)
+    st = gm.run(n_s, seed)
+    om = oracle_model(p, g)
+    tot = om.prepare(n_s, seed)
+    assert st["n_total"] == tot
+    assert np.array_equal(gm.zone_counts(), om.zones()["counts"])
+
+
+@pytest.mark.parametrize("name,n_s,seed,nsample", [("flat_thin", 3e4, 1, 400), ("ks_sphere", 1e5, 1, 400),
+                                                   ("ks_scatter", 2e4, 2, 600)])
+def test_superphoton_end_states_fp64(case_data, name, n_s, seed, nsample):
+    p, g = case_data[name]
+    gm = gpu_model(p, g)
+    om = oracle_model(p, g)
+    tot = om.prepare(n_s, seed)
+    rng = np.random.default_rng(seed)
+    uids = np.sort(rng.choice(tot, size=min(nsample, tot), replace=False))
+    lg = gm.trace(n_s, seed, uids)
+    lo = om.run(uids=uids, log=True)["log"]
+    r = compare_logs(lg, lo)
+    assert r["n"] >= 0.99 * len(lo)
+    assert len(r["flips"]) <= max(1, 0.002 * r["n"])
+    assert r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9
+    assert r["worst"]["w"] < 1e-7
+
+
+@pytest.mark.parametrize("name,n_s,seed", [("flat_thin", 2e4, 3), ("ks_scatter", 1e4, 4)])
+def test_spectrum_fp64(case_data, name, n_s, seed):
+    p, g = case_data[name]
+    gm = gpu_model(p, g)
+    stg = gm.run(n_s, seed)
+    om = oracle_model(p, g)
+    om.prepare(n_s, seed)
+    ro = om.run()
+    ok, bad = spectra_agree(gm.spectrum_sums(), ro["spec"])
+    assert ok, bad
+    so = ro["stats"]
+    for k in ("n_emit", "n_child", "n_rec", "n_capt"):
+        assert abs(stg[k] - so[k]) <= max(2, 2e-3 * so[k]), k
+
+
+@pytest.mark.parametrize("name,n_s,seed", [("flat_thin", 2e4, 5), ("ks_scatter", 1e4, 6)])
+def test_spectrum_mixed_precision(case_data, name, n_s, seed):
+    p, g = case_data[name]
+    gm = gpu_model(p, g, precision="mixed")
+    gm.run(n_s, seed)
+    om = oracle_model(p, g)
+    om.prepare(n_s, seed)
+    ro = om.run()
+    ok, bad = spectra_agree(gm.spectrum_sums(), ro["spec"])
+    assert ok, bad
+
+
+def test_shards_sum_to_whole(case_data):
+    p, g = case_data["ks_scatter"]
+    gm = gpu_model(p, g)
+    whole = gm.run(1e4, 9)
+    s_whole = gm.spectrum_sums().copy()
+    acc = np.zeros_like(s_whole)
+    n_emit = 0
+    for s in range(3):
+        st = gm.run(1e4, 9, shard=s, n_shards=3)
+        acc += gm.spectrum_sums()
+        n_emit += st["n_emit"]
+    assert n_emit == whole["n_emit"] == whole["n_total"]
+    assert np.array_equal(acc[..., 2], s_whole[..., 2])
+    assert np.allclose(acc[..., :2], s_whole[..., :2], rtol=1e-12, atol=0)
+
+
+def test_run_is_deterministic_and_seeded(case_data):
+    p, g = case_data["flat_thin"]
+    gm = gpu_model(p, g)
+    gm.run(5e3, 11)
+    a = gm.spectrum_sums().copy()
+    gm.run(5e3, 11)
+    b = gm.spectrum_sums().copy()
+    gm.run(5e3, 12)
+    c = gm.spectrum_sums().copy()
+    assert np.array_equal(a[..., 2], b[..., 2]) and np.allclose(a, b, rtol=1e-12, atol=0)
+    assert not np.array_equal(a[..., 2], c[..., 2])
+
+
+def test_edge_cases_and_errors():
+    from paper_2602_13198_gb300 import mc
+    p, g = flat_sphere(n1=2, n2=2)
+    m = mc.Model(p)
+    with pytest.raises(mc.MCError) as e:
+        m.run(10, 1)
+    assert e.value.code == -8          # STATE: no grid yet
+    m.set_grid(g)
+    st = m.run(0.01, 1)                # almost surely zero superphotons
+    assert st["n_total"] == st["n_emit"] <= 1
+    with pytest.raises(mc.MCError) as e:
+        m.run(-1.0, 1)
+    assert e.value.code == -1
+    bad = dict(p, n_nu=1)
+    with pytest.raises(mc.MCError):
+        mc.Model(bad)
+    g2 = dict(g)
+    pr = g["prim"].copy()
+    pr[0, 0] = np.nan
+    g2["prim"] = pr
+    with pytest.raises(mc.MCError) as e:
+        m.set_grid(g2)
+    assert e.value.code == -6          # NAN_INPUT
+
+
+def test_ragged_3d_float32_grid():
+    # 3-D grid with ragged sizes in FP32 storage (the layout of the 3-D snapshot workload)
+    p, g = synth.sphere("ks", n1=37, n2=19, R=10.0)
+    g3 = dict(g)
+    n3 = 5
+    pr = np.repeat(g["prim"].reshape(8, 37, 19, 1), n3, axis=3).reshape(8, -1)
+    rng = np.random.default_rng(3)
+    pr[0] *= np.exp(0.1 * rng.standard_normal(pr.shape[1]))
+    g3.update(n3=n3, dx3=2 * math.pi / n3, prim=pr.astype(np.float32))
+    go = dict(g3, prim=pr.astype(np.float32).astype(np.float64))
+    gm = gpu_model(p, g3)
+    st = gm.run(2e4, 5)
+    om = oracle_model(p, go)
+    tot = om.prepare(2e4, 5)
+    assert st["n_total"] == tot
+    assert np.array_equal(gm.zone_counts(), om.zones()["counts"])
+    uids = np.arange(0, tot, max(1, tot // 300))
+    r = compare_logs(gm.trace(2e4, 5, uids), om.run(uids=uids, log=True)["log"])
+    assert len(r["flips"]) <= 1 and r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9
