@@ -121,6 +121,7 @@ def oracle_rate(p, g, seed, budget_s, nthreads, first_n=None):
 
 
 def main():
+    global N_S, TAUS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
@@ -128,7 +129,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass (profiling runs)")
+    ap.add_argument("--n-s", type=float, default=N_S, help="N_s per run (smaller cases for profiling)")
+    ap.add_argument("--taus", default=",".join(str(t) for t in TAUS), help="comma-separated Thomson depths")
     args = ap.parse_args()
+    N_S = args.n_s
+    TAUS = tuple(float(t) for t in args.taus.split(","))
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -145,13 +151,13 @@ def main():
         oracle.build()
         models = [synth.scattering_sphere(t) for t in TAUS]
         for w in range(args.warmup):
-            p, g = models[w % 4]
+            p, g = models[w % len(models)]
             oracle_rate(p, g, 1, 2.0, cores, first_n=64)
         units, secs = 0, 0.0
         samples = []
         for k in range(args.steps):
-            p, g = models[k % 4]
-            seed = 1 + (k // 4) % 4
+            p, g = models[k % len(models)]
+            seed = 1 + (k // len(models)) % 4
             rate, u, dt, n = oracle_rate(p, g, seed, 12.0, cores)
             units += u
             secs += dt
@@ -188,9 +194,11 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    nt = len(TAUS)
+
     def one(k, ctx_seed_offset=0):
-        i = k % 4
-        seed = 1 + (k // 4) % 4 + 1000 * rank + ctx_seed_offset
+        i = k % nt
+        seed = 1 + (k // nt) % 4 + 1000 * rank + ctx_seed_offset
         return ctxs[i].run(N_S, seed, stream=stream)
 
     for w in range(args.warmup):
@@ -235,15 +243,15 @@ def main():
     for p, g in models:
         hp = torch.from_numpy(np.ascontiguousarray(g["prim"])).pin_memory()
         host_prims.append(hp)
-    e2e_units, t_e2e = 0, 0.0
+    e2e_units, t_e2e = 0, 1e-300
     torch.cuda.synchronize()
-    for k in range(args.steps):
-        i = k % 4
+    for k in range(0 if args.no_e2e else args.steps):
+        i = k % nt
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctxs[i].set_grid(models[i][1], prim=host_prims[i].numpy())
-        s = ctxs[i].run(N_S, 1 + (k // 4) % 4 + 1000 * rank, stream=stream)
+        s = ctxs[i].run(N_S, 1 + (k // nt) % 4 + 1000 * rank, stream=stream)
         spec = ctxs[i].spectrum()
         t_e2e += time.perf_counter() - t0
         e2e_units += s["n_emit"] + s["n_child"]
@@ -270,7 +278,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        p, g = models[2]
+        p, g = models[min(2, nt - 1)]
         rate, u, dt, n = oracle_rate(p, g, 1, 15.0, cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "first %d primaries (+ scattered descendants, %d superphotons) of the tau_T=1e-2 seed-1 job, "
@@ -283,8 +291,9 @@ def main():
                 "config": {"workload": WORKLOAD, "form": "plain FP64" if args.precision == "fp64" else "mixed FP64/FP32",
                            "n_s_per_run": N_S, "grid": [1024, 128, 1], "l2": "flushed (256 MiB write) between timed steps",
                            "parallelism": "replicas (independent jobs per rank)" if world > 1 else "single GPU"},
-                "clocks": clocks, "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                                          "d2h_bytes_per_step": d2h},
+                "clocks": clocks,
+                "e2e": None if args.no_e2e else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                                                  "d2h_bytes_per_step": d2h},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": int(launches + GEN_LAUNCHES * args.steps),
                 "detail": {"superphotons": units, "scattered": sum(s["n_child"] for s in stats),
