@@ -179,6 +179,25 @@ int mc_trace(mc_ctx *c, double n_s, uint64_t seed, const int64_t *uids, size_t n
  * NO_DEVICE, CUDA. */
 int mc_fma_peak(int device, int dtype, double *flops);
 
+/* Zone superphoton counts for (N_s, seed) -- the same numbers mc_run computes and
+ * mc_get_zone_counts returns -- without allocating any device memory, for callers that cannot
+ * allocate at this point (a stream being captured into a graph, a custom allocator's callback,
+ * an application that has given all device memory to its own pool).  The paper has no
+ * counterpart; it is an execution variant of the weight/count/scan kernels of mc_run.
+ *   counts: device int64[n1*n2*n3], written; start: device int64[n1*n2*n3], the exclusive scan
+ *   (first uid of each zone), written; total: device int64[1], the job's primary count, written.
+ *   All three are caller-owned device pointers; the call is asynchronous on `stream`.
+ * Scratch lives in one static device array of fixed size (5.3 MiB) that every GPU loading the
+ * library keeps until the process exits; grids above 131072 zones or weight tables above 512 nodes
+ * are rejected with MC_ERR_SIZE.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls whose work overlaps on
+ * the GPU (different streams, or different contexts on the same device) race and must be ordered
+ * by the caller.  The context's tables and grid are read, not modified.
+ * Errors: INVALID_ARG, STATE (no grid), SIZE, CUDA. */
+int mc_zone_counts_noalloc(mc_ctx *c, double n_s, uint64_t seed, int64_t *counts, int64_t *start, int64_t *total,
+                           void *stream);
+
 /* Releases the context and all its device memory.  NULL is a no-op. */
 void mc_free(mc_ctx *c);
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmcgb.so")
-SOURCES = ["mc_api.cu", "mc_tables.cu", "mc_transport.cu"]
+SOURCES = ["mc_api.cu", "mc_tables.cu", "mc_transport.cu", "mc_noalloc.cu"]
 HEADERS = ["mc_device.cuh", "mc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -17,44 +17,6 @@
 
 using namespace mcgb;
 
-struct mc_ctx {
-  mc_model_params p;
-  std::string err;
-  int sms = 0;
-  // allocations made through the caller's allocator (or cudaMalloc)
-  std::vector<void *> allocs;
-  // tables
-  double *lnF = nullptr, *lnK2 = nullptr, *hot = nullptr, *gl = nullptr;
-  int nF = 0, nK2 = 0;
-  // grid
-  bool have_grid = false;
-  void *prim = nullptr;
-  int prim_f32 = 0;
-  int n1 = 0, n2 = 0, n3 = 0;
-  int64_t nz = 0;
-  double x1_0 = 0, dx1 = 0, x2_0 = 0, dx2 = 0, x3_0 = 0, dx3 = 0;
-  // per-run generation data
-  double *zvol = nullptr, *zpref = nullptr, *zlnuc = nullptr, *zgmax = nullptr, *znbar = nullptr;
-  int64_t *counts = nullptr, *start = nullptr, *bsum = nullptr;
-  double *partial = nullptr, *lnw = nullptr, *winv = nullptr;
-  int *bad = nullptr;
-  int nchunks = 0;
-  // transport
-  ChildBuf q[2];
-  int64_t qcap = 0;
-  unsigned long long *cnt = nullptr;
-  int64_t *total_dev = nullptr;
-  double *spec = nullptr;
-  unsigned long long *cnt_host = nullptr;   // pinned
-  bool have_run = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  double t_transport = 0.0, t_generate = 0.0;
-  int64_t n_launch = 0;
-  int64_t last_total = 0;
-  uint64_t last_seed = 0;
-  double last_ns = 0.0;
-};
-
 static std::string g_init_err;
 
 static int fail(mc_ctx *c, int code, const std::string &msg) {
@@ -122,7 +84,7 @@ static void gauss_legendre(int n, double a, double b, double *x, double *w) {
   }
 }
 
-static DevModel make_model(const mc_ctx *c) {
+DevModel make_model(const mc_ctx *c) {
   const mc_model_params &p = c->p;
   DevModel m;
   std::memset(&m, 0, sizeof(m));

@@ -3,6 +3,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <string>
+#include <vector>
+
 #include "../../include/mc.h"
 #include "mc_device.cuh"
 
@@ -60,3 +63,47 @@ int transport_max_blocks_per_sm(int mixed, int block);
 void launch_transport(const DevModel &m, const RoundIO &io, int mixed, int grid, int block, cudaStream_t st);
 
 }  // namespace mcgb
+
+// Context owned by the library (opaque to callers; shared by the library's translation units).
+struct mc_ctx {
+  // parameters, last error, device properties
+  mc_model_params p;
+  std::string err;
+  int sms = 0;
+  // allocations made through the caller's allocator (or cudaMalloc)
+  std::vector<void *> allocs;
+  // tables
+  double *lnF = nullptr, *lnK2 = nullptr, *hot = nullptr, *gl = nullptr;
+  int nF = 0, nK2 = 0;
+  // grid
+  bool have_grid = false;
+  void *prim = nullptr;
+  int prim_f32 = 0;
+  int n1 = 0, n2 = 0, n3 = 0;
+  int64_t nz = 0;
+  double x1_0 = 0, dx1 = 0, x2_0 = 0, dx2 = 0, x3_0 = 0, dx3 = 0;
+  // per-run generation data
+  double *zvol = nullptr, *zpref = nullptr, *zlnuc = nullptr, *zgmax = nullptr, *znbar = nullptr;
+  int64_t *counts = nullptr, *start = nullptr, *bsum = nullptr;
+  double *partial = nullptr, *lnw = nullptr, *winv = nullptr;
+  int *bad = nullptr;
+  int nchunks = 0;
+  // transport
+  mcgb::ChildBuf q[2];
+  int64_t qcap = 0;
+  unsigned long long *cnt = nullptr;
+  int64_t *total_dev = nullptr;
+  double *spec = nullptr;
+  unsigned long long *cnt_host = nullptr;   // pinned
+  bool have_run = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double t_transport = 0.0, t_generate = 0.0;
+  int64_t n_launch = 0;
+  int64_t last_total = 0;
+  uint64_t last_seed = 0;
+  double last_ns = 0.0;
+};
+
+// Kernel-side view of a context (mc_api.cu).
+mcgb::DevModel make_model(const mc_ctx *c);
+

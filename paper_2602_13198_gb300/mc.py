@@ -103,6 +103,8 @@ def lib():
         L.mc_version.restype = C.c_char_p
         L.mc_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
         L.mc_fma_peak.restype = C.c_int
+        L.mc_zone_counts_noalloc.argtypes = [vp, C.c_double, u64, vp, vp, vp, vp]
+        L.mc_zone_counts_noalloc.restype = C.c_int
         for f in ("mc_init_model", "mc_set_grid", "mc_run", "mc_get_spectrum", "mc_get_spectrum_sums",
                   "mc_get_zone_counts", "mc_trace"):
             getattr(L, f).restype = C.c_int
@@ -222,6 +224,13 @@ class Model:
         out = np.zeros(self.nz, dtype=np.int64)
         self._check(lib().mc_get_zone_counts(self._h, out.ctypes.data_as(C.POINTER(C.c_int64)), self.nz))
         return out
+
+    def zone_counts_noalloc(self, n_s: float, seed: int, counts, start, total, stream=None):
+        """Zone counts into caller-owned CUDA tensors (int64 [nz], [nz], [1]) with no device
+        allocation inside the library (see mc_zone_counts_noalloc in include/mc.h)."""
+        s = C.c_void_p(getattr(stream, "cuda_stream", 0) or 0) if stream is not None else C.c_void_p(0)
+        self._check(lib().mc_zone_counts_noalloc(self._h, float(n_s), int(seed), C.c_void_p(counts.data_ptr()),
+                                                 C.c_void_p(start.data_ptr()), C.c_void_p(total.data_ptr()), s))
 
     def trace(self, n_s: float, seed: int, uids, cap: int | None = None, stream=None):
         u = np.ascontiguousarray(uids, dtype=np.int64)
