@@ -41,6 +41,7 @@ WORKLOAD = ("scattering synchrotron sphere, Schwarzschild a=0, R=10 GM/c^2, Thet
 # sigma_h lookup, optical depths, weight update), per predictor iteration (acceleration contraction
 # and convergence test), per emission and per scattering event.
 FLOP_STEP = 460.0
+FLOP_STEP_MIXED = 190.0   # mixed form: FP64 only in step size, position update and metric derivatives
 FLOP_ITER = 110.0
 FLOP_EMIT = 2000.0
 FLOP_EVENT = 1500.0
@@ -225,7 +226,8 @@ def main():
     units = sum(s["n_emit"] + s["n_child"] for s in stats)
     t_transport = sum(s["transport_ms"] for s in stats) / 1e3
     launches = sum(s["transport_launches"] for s in stats)
-    flops = sum(FLOP_STEP * s["n_steps"] + FLOP_ITER * s["n_iters"] + FLOP_EMIT * s["n_emit"] + FLOP_EVENT * s["n_events"]
+    fstep = FLOP_STEP if args.precision == "fp64" else FLOP_STEP_MIXED
+    flops = sum(fstep * s["n_steps"] + FLOP_ITER * s["n_iters"] + FLOP_EMIT * s["n_emit"] + FLOP_EVENT * s["n_events"]
                 for s in stats)
     if dist:
         t = torch.tensor([dev_s, float(units)], dtype=torch.float64, device="cuda")
@@ -270,7 +272,7 @@ def main():
     peak = fp64_peak / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None,
-                "kernel": "k_transport<fp64> (persistent, one launch per scattering generation)",
+                "kernel": "transport: k_init + k_push<in-grid> + k_push<free> (%s)" % args.precision,
                 "peak_source": "measured: project FP64 FMA-chain microbenchmark on this GPU (mc_fma_peak)",
                 "fp32_peak_tflops": fp32_peak / 1e12,
                 "algorithmic_flops": flops, "transport_s": t_transport}

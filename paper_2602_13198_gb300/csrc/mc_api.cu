@@ -233,7 +233,7 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
     mc_free(c);
     return fail(nullptr, MC_ERR_OOM, "device allocation failed");
   }
-  if (cudaMallocHost(&c->cnt_host, sizeof(unsigned long long) * (CNT_N + 8)) != cudaSuccess) {
+  if (cudaMallocHost(&c->cnt_host, sizeof(unsigned long long) * (2 * CNT_N + 8)) != cudaSuccess) {
     cudaGetLastError();
     c->cnt_host = nullptr;
     mc_free(c);
@@ -315,14 +315,23 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   return MC_OK;
 }
 
+static void free_childbuf(mc_ctx *c, ChildBuf &q) {
+  for (int k = 0; k < 4; ++k) { dev_free(c, q.X[k]); dev_free(c, q.K[k]); }
+  dev_free(c, q.w); dev_free(c, q.id); dev_free(c, q.ctr); dev_free(c, q.nsc);
+  std::memset(&q, 0, sizeof(q));
+}
+
+// Child queues (two generations, ping-pong), the superphoton pool and the two phase lists, all
+// sized for `cap` superphotons.
 static int ensure_queues(mc_ctx *c, int64_t cap) {
   if (cap <= c->qcap) return MC_OK;
-  for (int b = 0; b < 2; ++b) {
-    ChildBuf &q = c->q[b];
-    for (int k = 0; k < 4; ++k) { dev_free(c, q.X[k]); dev_free(c, q.K[k]); }
-    dev_free(c, q.w); dev_free(c, q.id); dev_free(c, q.ctr); dev_free(c, q.nsc);
-    std::memset(&q, 0, sizeof(q));
-  }
+  for (int b = 0; b < 2; ++b) free_childbuf(c, c->q[b]);
+  Pool &P = c->pool;
+  for (int k = 0; k < 4; ++k) { dev_free(c, P.X[k]); dev_free(c, P.K[k]); dev_free(c, P.A[k]); }
+  void *pv[] = {P.w, P.wb, P.ana, P.ans, P.acc, P.x1t, P.id, P.ctr, P.nev, P.nsc, P.nsteps, c->list_grid, c->list_free};
+  for (void *ptr : pv) dev_free(c, ptr);
+  std::memset(&P, 0, sizeof(P));
+  c->list_grid = c->list_free = nullptr;
   c->qcap = 0;
   for (int b = 0; b < 2; ++b) {
     ChildBuf &q = c->q[b];
@@ -337,6 +346,26 @@ static int ensure_queues(mc_ctx *c, int64_t cap) {
     q.nsc = (int32_t *)dev_alloc(c, 4 * cap);
     if (!q.w || !q.id || !q.ctr || !q.nsc) return fail(c, MC_ERR_OOM, "queue allocation failed");
   }
+  for (int k = 0; k < 4; ++k) {
+    P.X[k] = (double *)dev_alloc(c, 8 * cap);
+    P.K[k] = (double *)dev_alloc(c, 8 * cap);
+    P.A[k] = (double *)dev_alloc(c, 8 * cap);
+    if (!P.X[k] || !P.K[k] || !P.A[k]) return fail(c, MC_ERR_OOM, "pool allocation failed");
+  }
+  double **dv[] = {&P.w, &P.wb, &P.ana, &P.ans, &P.acc, &P.x1t};
+  for (double **d : dv) {
+    *d = (double *)dev_alloc(c, 8 * cap);
+    if (!*d) return fail(c, MC_ERR_OOM, "pool allocation failed");
+  }
+  P.id = (uint64_t *)dev_alloc(c, 8 * cap);
+  P.ctr = (uint32_t *)dev_alloc(c, 4 * cap);
+  P.nev = (uint32_t *)dev_alloc(c, 4 * cap);
+  P.nsc = (int32_t *)dev_alloc(c, 4 * cap);
+  P.nsteps = (int32_t *)dev_alloc(c, 4 * cap);
+  c->list_grid = (int32_t *)dev_alloc(c, 4 * cap);
+  c->list_free = (int32_t *)dev_alloc(c, 4 * cap);
+  if (!P.id || !P.ctr || !P.nev || !P.nsc || !P.nsteps || !c->list_grid || !c->list_free)
+    return fail(c, MC_ERR_OOM, "pool allocation failed");
   c->qcap = cap;
   return MC_OK;
 }
@@ -369,57 +398,116 @@ static int generate(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st) {
   return MC_OK;
 }
 
-// Transports primaries [u0, u1) (or the uid list) and all their descendants.
+// Launch helper: records the launch's device time between two events on the stream and reads the
+// counters back (the host needs the list lengths to size the next phase).
+#define TIMED_LAUNCH(launch_expr)                                                                         \
+  do {                                                                                                    \
+    CU(cudaEventRecord(c->ev[0], st));                                                                    \
+    launch_expr;                                                                                          \
+    CU(cudaGetLastError());                                                                               \
+    CU(cudaEventRecord(c->ev[1], st));                                                                    \
+    CU(cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st)); \
+    CU(cudaStreamSynchronize(st));                                                                        \
+    float ms_ = 0.0f;                                                                                     \
+    CU(cudaEventElapsedTime(&ms_, c->ev[0], c->ev[1]));                                                   \
+    c->t_transport += ms_;                                                                                \
+    c->n_launch++;                                                                                        \
+  } while (0)
+
+static int set_counter(mc_ctx *c, int idx, unsigned long long v, cudaStream_t st) {
+  unsigned long long *h = c->cnt_host + CNT_N + 2 + idx;   // pinned staging slot per counter
+  *h = v;
+  CU(cudaMemcpyAsync(c->cnt + idx, h, sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+  return MC_OK;
+}
+
+// Transports primaries [u0, u1) (or the uid list) and all their descendants: per batch and per
+// scattering generation, k_init fills the pool, then the in-grid and free push phases alternate
+// until no superphoton of the generation is left.
 static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_dev, int64_t n_list, mc_log_rec *log_dev,
                      int64_t log_cap, uint64_t seed, cudaStream_t st) {
   DevModel m = make_model(c);
   m.seed = seed;
-  int block = c->p.block ? c->p.block : 128;
-  int mixed = c->p.precision == MC_PREC_MIXED;
-  int occ = transport_max_blocks_per_sm(mixed, block);
-  if (occ < 1) occ = 1;
-  if (c->p.ctas_per_sm > 0) occ = std::min(occ, (int)c->p.ctas_per_sm);
+  const int block = c->p.block ? c->p.block : 128;
+  const int mixed = c->p.precision == MC_PREC_MIXED;
+  int occ[2];
+  for (int ph = 0; ph < 2; ++ph) {
+    occ[ph] = std::max(1, push_max_blocks_per_sm(mixed, ph, block));
+    if (c->p.ctas_per_sm > 0) occ[ph] = std::min(occ[ph], (int)c->p.ctas_per_sm);
+  }
   const int64_t n_prim = uid_list_dev ? n_list : (u1 - u0);
   const int64_t batch_max = 1 << 24;
   int64_t batch = std::min<int64_t>(std::max<int64_t>(n_prim, 1), batch_max);
   int rc = ensure_queues(c, std::max<int64_t>(1 << 20, 2 * batch));
   if (rc) return rc;
-  RoundIO io;
-  std::memset(&io, 0, sizeof(io));
-  io.spec = c->spec;
-  io.cnt = c->cnt;
-  io.log = log_dev;
-  io.log_cap = log_cap;
-  io.out_cap = c->qcap;
+  PushIO pio;
+  std::memset(&pio, 0, sizeof(pio));
+  pio.pool = c->pool;
+  pio.spec = c->spec;
+  pio.cnt = c->cnt;
+  pio.log = log_dev;
+  pio.log_cap = log_cap;
+  pio.out_cap = c->qcap;
+  InitIO iio;
+  std::memset(&iio, 0, sizeof(iio));
+  iio.pool = c->pool;
+  iio.list_grid = c->list_grid;
+  iio.list_free = c->list_free;
+  iio.cnt = c->cnt;
   for (int64_t b0 = 0; b0 < n_prim; b0 += batch) {
     int64_t nb = std::min(batch, n_prim - b0);
     int gen = 0;
     int64_t n_items = nb;
     while (n_items > 0) {
-      io.n_items = n_items;
+      if (n_items > c->qcap) return fail(c, MC_ERR_QUEUE_OVERFLOW, "generation larger than the superphoton pool");
+      iio.n_items = n_items;
       if (gen == 0) {
-        io.mode = uid_list_dev ? 1 : 0;
-        io.uid0 = u0 + b0;
-        io.uids = uid_list_dev ? uid_list_dev + b0 : nullptr;
+        iio.mode = uid_list_dev ? 1 : 0;
+        iio.uid0 = u0 + b0;
+        iio.uids = uid_list_dev ? uid_list_dev + b0 : nullptr;
       } else {
-        io.mode = 2;
-        io.in = c->q[(gen - 1) & 1];
+        iio.mode = 2;
+        iio.in = c->q[(gen - 1) & 1];
       }
-      io.out = c->q[gen & 1];
+      pio.out = c->q[gen & 1];
+      // cursor, children, phase-list counters start at zero for the generation
       CU(cudaMemsetAsync(c->cnt + CNT_NEXT, 0, 2 * sizeof(unsigned long long), st));
-      int64_t want = (n_items + block - 1) / block;
-      int grid = (int)std::min<int64_t>((int64_t)c->sms * occ, want);
-      CU(cudaEventRecord(c->ev[0], st));
-      launch_transport(m, io, mixed, grid, block, st);
-      CU(cudaGetLastError());
-      CU(cudaEventRecord(c->ev[1], st));
-      CU(cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
-      float ms = 0.0f;
-      CU(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-      c->t_transport += ms;
-      c->n_launch++;
-      if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
+      CU(cudaMemsetAsync(c->cnt + CNT_L0, 0, 2 * sizeof(unsigned long long), st));
+      int grid_init = (int)std::min<int64_t>((int64_t)c->sms * 4, (n_items + block - 1) / block);
+      TIMED_LAUNCH(launch_init(m, iio, mixed, grid_init, block, st));
+      int64_t n_grid = (int64_t)c->cnt_host[CNT_L0], n_free = (int64_t)c->cnt_host[CNT_L1];
+      while (n_grid > 0 || n_free > 0) {
+        if (n_grid > 0) {
+          rc = set_counter(c, CNT_NEXT, 0, st);
+          if (rc) return rc;
+          pio.list_in = c->list_grid;
+          pio.n_in = n_grid;
+          pio.list_out = c->list_free;
+          pio.out_counter = CNT_L1;   // continues after the n_free entries already listed
+          int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[0], (n_grid + block - 1) / block);
+          TIMED_LAUNCH(launch_push(m, pio, mixed, 0, grid, block, st));
+          if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
+          n_free = (int64_t)c->cnt_host[CNT_L1];
+          n_grid = 0;
+          rc = set_counter(c, CNT_L0, 0, st);
+          if (rc) return rc;
+        }
+        if (n_free > 0) {
+          rc = set_counter(c, CNT_NEXT, 0, st);
+          if (rc) return rc;
+          pio.list_in = c->list_free;
+          pio.n_in = n_free;
+          pio.list_out = c->list_grid;
+          pio.out_counter = CNT_L0;
+          int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[1], (n_free + block - 1) / block);
+          TIMED_LAUNCH(launch_push(m, pio, mixed, 1, grid, block, st));
+          if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
+          n_grid = (int64_t)c->cnt_host[CNT_L0];
+          n_free = 0;
+          rc = set_counter(c, CNT_L1, 0, st);
+          if (rc) return rc;
+        }
+      }
       n_items = (int64_t)c->cnt_host[CNT_OUT];
       ++gen;
     }

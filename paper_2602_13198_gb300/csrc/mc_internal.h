@@ -21,22 +21,50 @@ struct ChildBuf {
   int32_t *nsc;
 };
 
-// Counters written by the transport kernel (unsigned 64-bit for atomics).
+// Superphoton state between transport phases (structure of arrays, one slot per superphoton
+// of the current batch or generation).
+struct Pool {
+  double *X[4], *K[4], *A[4];
+  double *w, *wb, *ana, *ans, *acc, *x1t;
+  uint64_t *id;
+  uint32_t *ctr, *nev;
+  int32_t *nsc, *nsteps;
+};
+
+// Counters written by the transport kernels (unsigned 64-bit for atomics).
 enum {
   CNT_NEXT = 0,   // work-item cursor
   CNT_OUT,        // children appended
   CNT_LOG,        // log records appended
   CNT_ERR,        // error bits
+  CNT_L0,         // appends to the in-grid list
+  CNT_L1,         // appends to the free-streaming list
   CNT_EMIT, CNT_CHILD, CNT_REC, CNT_ABS, CNT_CAPT, CNT_MAXST,
   CNT_STEPS, CNT_ITERS, CNT_NONCONV, CNT_ROUL, CNT_REJCAP, CNT_EVENTS,
   CNT_N
 };
 
-struct RoundIO {
+// Emission (or loading of scattered children) and transport initialisation into the pool;
+// slots are appended to the in-grid list (CNT_L0) or the free list (CNT_L1).
+struct InitIO {
   int mode;                 // 0: primaries uid0 .. uid0+n_items; 1: uid list; 2: children
   int64_t uid0, n_items;
   const int64_t *uids;
-  ChildBuf in, out;
+  ChildBuf in;
+  Pool pool;
+  int32_t *list_grid, *list_free;
+  unsigned long long *cnt;
+};
+
+// One phase of transport over the listed pool slots; slots that change phase are appended to
+// list_out (counter out_counter).
+struct PushIO {
+  const int32_t *list_in;
+  int64_t n_in;
+  int32_t *list_out;
+  int out_counter;
+  Pool pool;
+  ChildBuf out;
   int64_t out_cap;
   double *spec;             // [n_incl][n_bins][3]
   unsigned long long *cnt;  // CNT_N counters
@@ -59,8 +87,10 @@ void launch_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, in
 // FMA-chain throughput of the FP64 or FP32 pipe in FLOP/s (mc_tables.cu)
 cudaError_t fma_peak(bool fp64, double *flops);
 // transport (mc_transport.cu)
-int transport_max_blocks_per_sm(int mixed, int block);
-void launch_transport(const DevModel &m, const RoundIO &io, int mixed, int grid, int block, cudaStream_t st);
+int push_max_blocks_per_sm(int mixed, int phase, int block);
+void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st);
+// phase 0: superphotons inside the radial extent of the grid; 1: outside it
+void launch_push(const DevModel &m, const PushIO &io, int mixed, int phase, int grid, int block, cudaStream_t st);
 
 }  // namespace mcgb
 
@@ -91,6 +121,9 @@ struct mc_ctx {
   // transport
   mcgb::ChildBuf q[2];
   int64_t qcap = 0;
+  mcgb::Pool pool;
+  int32_t *list_grid = nullptr, *list_free = nullptr;
+  int64_t pcap = 0;
   unsigned long long *cnt = nullptr;
   int64_t *total_dev = nullptr;
   double *spec = nullptr;

@@ -1,15 +1,20 @@
-// mc_transport.cu -- persistent superphoton transport kernel (sections 2.3-2.7, 3).
+// mc_transport.cu -- superphoton transport kernels (sections 2.3-2.7, 3).
 //
-// One launch processes one generation of superphotons: the primaries of a uid range (emitted
-// here: zone by binary search in the count scan, frequency and direction by rejection, wavevector
-// in the plasma tetrad) or the scattered children of the previous generation.  Each thread holds
-// one superphoton in registers and pushes it step by step; when a lane's superphoton finishes, the
-// warp refills its idle lanes from a global work cursor (one atomic per warp), so warps stay full
-// without separate compaction passes (the regeneration form of a wavefront).  Per step: iterated
-// velocity Verlet in FP64 (metric derivatives evaluated once per step at x_{n+1}, the predictor
-// loop reuses them), fluid interpolation and invariant coefficients (FP64, or FP32 in the mixed
-// precision variant), trapezoid optical depths, biased scattering with the event located within
-// the step, and recording into the spectrum at r >= r_record.
+// A batch of superphotons (the primaries of a uid range, or the scattered children of the
+// previous generation) goes through three kernels:
+//   * k_init: emission (zone by binary search in the count scan, frequency and direction by
+//     rejection, wavevector in the plasma tetrad) or loading of a child, then the transport
+//     initialisation; every lane does the same work, and the state goes to a pool in HBM;
+//   * k_push<phase 0>: superphotons inside the radial extent of the grid: iterated velocity Verlet
+//     in FP64 (metric derivatives evaluated once per step at x_{n+1}, reused by every predictor
+//     pass), fluid interpolation and invariant coefficients (FP64, or FP32 in the mixed variant),
+//     trapezoid optical depths, biased scattering with the event located within the step, Compton
+//     kinematics of the child, termination tests; a superphoton that leaves the grid is handed on;
+//   * k_push<phase 1>: superphotons outside the grid, where both trapezoid end points have no plasma
+//     and a step reduces to the geodesic and the termination tests (recording at r >= r_record);
+//     one that re-enters the grid is handed back.
+// Grouping superphotons by phase keeps the lanes of a warp on the same code path; the push kernels
+// are persistent and refill a lane from the phase's list as soon as its superphoton leaves.
 #include "mc_internal.h"
 
 namespace mcgb {
@@ -125,7 +130,7 @@ __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &ls) {
 
 // Compton event at Xe with pre-event wavevector Ke (section 2.7): child in the plasma frame of the
 // event point (radial lookup clamped to the grid), written to the next generation's queue.
-__device__ void scatter_child(const DevModel &m, const RoundIO &io, const double Xe[4], const double Ke[4], double wc,
+__device__ void scatter_child(const DevModel &m, const PushIO &io, const double Xe[4], const double Ke[4], double wc,
                               uint64_t cid, int nsc, LocalStats &ls) {
   Geo G;
   metric_eval<false>(m, Xe[1], Xe[2], G);
@@ -171,7 +176,11 @@ __device__ void scatter_child(const DevModel &m, const RoundIO &io, const double
   io.out.nsc[slot] = nsc;
 }
 
-__device__ void record(const DevModel &m, const RoundIO &io, const Geo &G, const Ph &p) {
+__device__ __forceinline__ bool in_grid(const DevModel &m, const double X[4]) {
+  return X[1] >= m.x1_0 && X[1] <= m.x1_hi;
+}
+
+__device__ void record(const DevModel &m, const PushIO &io, const Geo &G, const Ph &p) {
   double E = -(G.g00 * p.K[0] + G.g01 * p.K[1] + G.g03 * p.K[3]);
   if (!(E > 0.0)) return;
   double nu = E * (kME * kCL * kCL / kHPL);
@@ -188,7 +197,7 @@ __device__ void record(const DevModel &m, const RoundIO &io, const Geo &G, const
   atomicAdd(sp + 2, 1.0);
 }
 
-__device__ void write_log(const RoundIO &io, const Ph &p, int status) {
+__device__ void write_log(const PushIO &io, const Ph &p, int status) {
   if (!io.log) return;
   unsigned long long slot = atomicAdd(io.cnt + CNT_LOG, 1ull);
   if ((int64_t)slot >= io.log_cap) {
@@ -211,7 +220,7 @@ __device__ void write_log(const RoundIO &io, const Ph &p, int status) {
 
 // One geodesic step with absorption, scattering and the termination tests; false when finished.
 template <bool MIXED>
-__device__ bool step(const DevModel &m, const RoundIO &io, Ph &p, LocalStats &ls) {
+__device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
   const bool scat = m.scatter && p.nsc < m.n_sc_max;
   double dl = stepsize(m, p.X, p.K);
   double X0[4], K0[4], Kp[4], An[4];
@@ -323,17 +332,199 @@ __device__ bool step(const DevModel &m, const RoundIO &io, Ph &p, LocalStats &ls
   return true;
 }
 
+// Free-streaming step (both end points outside the grid: no plasma, so tau_a = tau_s = 0 and the
+// weight is unchanged): the same Verlet arithmetic and termination tests as step().  If the new
+// point lies inside the grid the step is discarded (state untouched) and 2 is returned, so the
+// in-grid phase redoes it with the coefficients.  Returns 0 to continue, 1 when finished.
+__device__ int step_free(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
+  double dl = stepsize(m, p.X, p.K);
+  double Xn[4], Kp[4], An[4], Kn[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Xn[q] = p.X[q] + p.K[q] * dl + 0.5 * p.A[q] * dl * dl;
+    Kp[q] = p.K[q] + p.A[q] * dl;
+  }
+  if (in_grid(m, Xn)) return 2;
+  Geo G;
+  metric_eval<true>(m, Xn[1], Xn[2], G);
+  int it = 0;
+  bool conv = false;
+  while (true) {
+    accel(G, Kp, An);
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Kn[q] = p.K[q] + 0.5 * (p.A[q] + An[q]) * dl;
+      num += fabs(Kn[q] - Kp[q]);
+      den += fabs(Kn[q]);
+    }
+    ++it;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
+    if (num < m.verlet_tol * den) {
+      conv = true;
+      break;
+    }
+    if (it >= m.verlet_maxit) break;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.X[q] = Xn[q];
+    p.K[q] = Kn[q];
+    p.A[q] = An[q];
+  }
+  ls.iters += it;
+  if (!conv) ls.nonconv++;
+  p.nsteps++;
+  ls.steps++;
+  p.ana = 0.0;
+  p.ans = 0.0;
+  const double r = G.r;
+  int status = 0;
+  if (r >= m.r_record) {
+    record(m, io, G, p);
+    status = 1;
+    ls.rec++;
+  } else if (r <= m.r_capture) {
+    status = 3;
+    ls.capt++;
+  } else if (!(p.w > 0.0)) {
+    status = 2;
+    ls.abs++;
+  } else {
+    if (p.w < m.roulette_w * p.wb) {
+      if (rng_u(p.s, m.seed) < m.roulette_p) {
+        p.w /= m.roulette_p;
+        ls.roul++;
+      } else {
+        status = 2;
+        ls.abs++;
+      }
+    }
+    if (status == 0 && p.nsteps >= m.max_steps) {
+      status = 4;
+      ls.maxst++;
+    }
+  }
+  if (status) {
+    write_log(io, p, status);
+    return 1;
+  }
+  return 0;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+__device__ __forceinline__ void flush_stats(const LocalStats &ls, unsigned long long *cnt) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long v[12] = {ls.emit, ls.child, ls.rec, ls.abs, ls.capt, ls.maxst,
+                              ls.steps, ls.iters, ls.nonconv, ls.roul, ls.rejcap, ls.events};
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    unsigned long long s = warp_sum(v[q]);
+    if (lane == 0 && s) atomicAdd(cnt + CNT_EMIT + q, s);
+  }
+}
+
+__device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const Ph &p) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    P.X[q][i] = p.X[q];
+    P.K[q][i] = p.K[q];
+    P.A[q][i] = p.A[q];
+  }
+  P.w[i] = p.w;
+  P.wb[i] = p.wb;
+  P.ana[i] = p.ana;
+  P.ans[i] = p.ans;
+  P.acc[i] = p.acc;
+  P.x1t[i] = p.x1t;
+  P.id[i] = p.s.id;
+  P.ctr[i] = p.s.n;
+  P.nev[i] = p.nev;
+  P.nsc[i] = p.nsc;
+  P.nsteps[i] = p.nsteps;
+}
+
+__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, Ph &p) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.X[q] = P.X[q][i];
+    p.K[q] = P.K[q][i];
+    p.A[q] = P.A[q][i];
+  }
+  p.w = P.w[i];
+  p.wb = P.wb[i];
+  p.ana = P.ana[i];
+  p.ans = P.ans[i];
+  p.acc = P.acc[i];
+  p.x1t = P.x1t[i];
+  rng_init(p.s, P.id[i], P.ctr[i]);
+  p.nev = P.nev[i];
+  p.nsc = P.nsc[i];
+  p.nsteps = P.nsteps[i];
+}
+
+// Emission or child loading + transport initialisation, one item per thread (grid-stride).
 template <bool MIXED>
-__global__ void __launch_bounds__(128) k_transport(DevModel m, RoundIO io) {
+__global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_round = (io.n_items + stride - 1) / stride * stride;   // warp-uniform trip count
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_round; idx += stride) {
+    const bool have = idx < io.n_items;
+    bool grid_phase = false;
+    if (have) {
+      Ph p;
+      if (io.mode == 2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          p.X[q] = io.in.X[q][idx];
+          p.K[q] = io.in.K[q][idx];
+        }
+        p.w = io.in.w[idx];
+        rng_init(p.s, io.in.id[idx], io.in.ctr[idx]);
+        p.nsc = io.in.nsc[idx];
+      } else {
+        int64_t uid = (io.mode == 1) ? io.uids[idx] : io.uid0 + idx;
+        emit(m, uid, p, ls);
+        ls.emit++;
+      }
+      init_transport<MIXED>(m, p);
+      save_ph(io.pool, idx, p);
+      grid_phase = in_grid(m, p.X);
+    }
+    // warp-aggregated appends to the two phase lists
+    const int lane = threadIdx.x & 31;
+    unsigned mg = __ballot_sync(0xffffffffu, have && grid_phase);
+    unsigned mf = __ballot_sync(0xffffffffu, have && !grid_phase);
+    unsigned long long bg = 0, bf = 0;
+    if (lane == 0) {
+      if (mg) bg = atomicAdd(io.cnt + CNT_L0, (unsigned long long)__popc(mg));
+      if (mf) bf = atomicAdd(io.cnt + CNT_L1, (unsigned long long)__popc(mf));
+    }
+    bg = __shfl_sync(0xffffffffu, bg, 0);
+    bf = __shfl_sync(0xffffffffu, bf, 0);
+    unsigned below = (1u << lane) - 1u;
+    if (have && grid_phase) io.list_grid[bg + __popc(mg & below)] = (int32_t)idx;
+    if (have && !grid_phase) io.list_free[bf + __popc(mf & below)] = (int32_t)idx;
+  }
+  flush_stats(ls, io.cnt);
+}
+
+// Persistent transport of one phase over io.list_in; PHASE 0 keeps superphotons while they are in
+// the grid, PHASE 1 while they are outside it.  A lane whose superphoton ends or changes phase is
+// refilled from the list (one atomic per warp).
+template <bool MIXED, int PHASE>
+__global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   Ph p;
+  int64_t slot = -1;
   bool live = false;
   bool exhausted = false;
   while (true) {
@@ -345,53 +536,64 @@ __global__ void __launch_bounds__(128) k_transport(DevModel m, RoundIO io) {
         unsigned long long base = 0;
         if (lane == leader) base = atomicAdd(io.cnt + CNT_NEXT, (unsigned long long)cnt);
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (base + cnt >= (unsigned long long)io.n_items) exhausted = true;
+        if (base + cnt >= (unsigned long long)io.n_in) exhausted = true;
         if (!live) {
-          unsigned long long idx = base + __popc(idle & ((1u << lane) - 1u));
-          if (idx < (unsigned long long)io.n_items) {
-            if (io.mode == 2) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                p.X[q] = io.in.X[q][idx];
-                p.K[q] = io.in.K[q][idx];
-              }
-              p.w = io.in.w[idx];
-              rng_init(p.s, io.in.id[idx], io.in.ctr[idx]);
-              p.nsc = io.in.nsc[idx];
-            } else {
-              int64_t uid = (io.mode == 1) ? io.uids[idx] : io.uid0 + (int64_t)idx;
-              emit(m, uid, p, ls);
-              ls.emit++;
-            }
-            init_transport<MIXED>(m, p);
+          unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
+          if (k < (unsigned long long)io.n_in) {
+            slot = io.list_in[k];
+            load_ph(io.pool, slot, p);
             live = true;
           }
         }
       }
     }
     if (!__any_sync(0xffffffffu, live)) break;
-    if (live) live = step<MIXED>(m, io, p, ls);
+    if (live) {
+      bool handoff;
+      if (PHASE == 0) {
+        live = step<MIXED>(m, io, p, ls);
+        handoff = live && !in_grid(m, p.X);
+      } else {
+        int r = step_free(m, io, p, ls);
+        live = (r != 1);
+        handoff = (r == 2);
+      }
+      if (handoff) {
+        save_ph(io.pool, slot, p);
+        unsigned long long o = atomicAdd(io.cnt + io.out_counter, 1ull);
+        io.list_out[o] = (int32_t)slot;
+        live = false;
+      }
+    }
   }
-  // flush counters: one atomic per warp per counter
-  unsigned long long v[12] = {ls.emit, ls.child, ls.rec, ls.abs, ls.capt, ls.maxst,
-                              ls.steps, ls.iters, ls.nonconv, ls.roul, ls.rejcap, ls.events};
-#pragma unroll
-  for (int q = 0; q < 12; ++q) {
-    unsigned long long s = warp_sum(v[q]);
-    if (lane == 0 && s) atomicAdd(io.cnt + CNT_EMIT + q, s);
-  }
+  flush_stats(ls, io.cnt);
 }
 
-int transport_max_blocks_per_sm(int mixed, int block) {
+int push_max_blocks_per_sm(int mixed, int phase, int block) {
   int n = 0;
-  if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<true>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<false>, block, 0);
+  if (mixed) {
+    if (phase == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<true, 0>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<true, 1>, block, 0);
+  } else {
+    if (phase == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<false, 0>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<false, 1>, block, 0);
+  }
   return n;
 }
 
-void launch_transport(const DevModel &m, const RoundIO &io, int mixed, int grid, int block, cudaStream_t st) {
-  if (mixed) k_transport<true><<<grid, block, 0, st>>>(m, io);
-  else k_transport<false><<<grid, block, 0, st>>>(m, io);
+void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st) {
+  if (mixed) k_init<true><<<grid, block, 0, st>>>(m, io);
+  else k_init<false><<<grid, block, 0, st>>>(m, io);
+}
+
+void launch_push(const DevModel &m, const PushIO &io, int mixed, int phase, int grid, int block, cudaStream_t st) {
+  if (mixed) {
+    if (phase == 0) k_push<true, 0><<<grid, block, 0, st>>>(m, io);
+    else k_push<true, 1><<<grid, block, 0, st>>>(m, io);
+  } else {
+    if (phase == 0) k_push<false, 0><<<grid, block, 0, st>>>(m, io);
+    else k_push<false, 1><<<grid, block, 0, st>>>(m, io);
+  }
 }
 
 }  // namespace mcgb
