@@ -36,12 +36,16 @@ WORKLOAD = ("scattering synchrotron sphere, Schwarzschild a=0, R=10 GM/c^2, Thet
             "tau_T in {1e-4,1e-3,1e-2,1e-1}, grid 1024x128, N_s=1e7 per run, seeds 1-4, 200 log bins 1e8-1e24 Hz")
 
 # Algorithmic FP64 operations (add/mul/div/sqrt = 1, FMA = 2, each transcendental = 1), hand-counted
-# from the formulas of the FP64 path: per geodesic step outside the Verlet predictor loop (step size,
-# position update, metric and its x1/x2 derivatives, fluid interpolation, plasma state, j_nu, B_nu,
-# sigma_h lookup, optical depths, weight update), per predictor iteration (acceleration contraction
-# and convergence test), per emission and per scattering event.
-FLOP_STEP = 460.0
-FLOP_STEP_MIXED = 190.0   # mixed form: FP64 only in step size, position update and metric derivatives
+# from the formulas of the FP64 path.  In-grid step outside the predictor loop: step size (8),
+# position update (28), metric and its x1/x2 derivatives (130), fluid interpolation (80), plasma
+# state (90), j_nu / B_nu / sigma_h (80), optical depths and weight update (20), termination (5);
+# free-streaming step: step size, position update, metric derivatives, termination (170); each
+# Verlet predictor pass (acceleration contraction + convergence test): 110; emission: 2000;
+# scattering event (kinematics + tetrad + child): 1500.  Mixed form: the in-grid coefficients run in
+# FP32, leaving 190 FP64 operations per in-grid step.
+FLOP_STEP_GRID = 460.0
+FLOP_STEP_GRID_MIXED = 190.0
+FLOP_STEP_FREE = 170.0
 FLOP_ITER = 110.0
 FLOP_EMIT = 2000.0
 FLOP_EVENT = 1500.0
@@ -226,9 +230,14 @@ def main():
     units = sum(s["n_emit"] + s["n_child"] for s in stats)
     t_transport = sum(s["transport_ms"] for s in stats) / 1e3
     launches = sum(s["transport_launches"] for s in stats)
-    fstep = FLOP_STEP if args.precision == "fp64" else FLOP_STEP_MIXED
-    flops = sum(fstep * s["n_steps"] + FLOP_ITER * s["n_iters"] + FLOP_EMIT * s["n_emit"] + FLOP_EVENT * s["n_events"]
-                for s in stats)
+    fgrid = FLOP_STEP_GRID if args.precision == "fp64" else FLOP_STEP_GRID_MIXED
+    flops_grid = sum(fgrid * s["n_steps_grid"] + FLOP_ITER * s["n_iters_grid"] + FLOP_EVENT * s["n_events"]
+                     for s in stats)
+    flops = flops_grid + sum(FLOP_STEP_FREE * (s["n_steps"] - s["n_steps_grid"])
+                             + FLOP_ITER * (s["n_iters"] - s["n_iters_grid"]) + FLOP_EMIT * s["n_emit"] for s in stats)
+    t_grid = sum(s["grid_ms"] for s in stats) / 1e3
+    t_free = sum(s["free_ms"] for s in stats) / 1e3
+    t_init = sum(s["init_ms"] for s in stats) / 1e3
     if dist:
         t = torch.tensor([dev_s, float(units)], dtype=torch.float64, device="cuda")
         tmax = t.clone()
@@ -268,14 +277,16 @@ def main():
     else:
         e2e_value = e2e_units / t_e2e
 
-    achieved = flops / t_transport / 1e12
+    achieved = flops_grid / t_grid / 1e12
     peak = fp64_peak / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None,
-                "kernel": "transport: k_init + k_push<in-grid> + k_push<free> (%s)" % args.precision,
+                "kernel": "k_push<in-grid> (%s): dominant kernel, %.0f%% of transport time"
+                          % (args.precision, 100 * t_grid / max(t_transport, 1e-30)),
                 "peak_source": "measured: project FP64 FMA-chain microbenchmark on this GPU (mc_fma_peak)",
                 "fp32_peak_tflops": fp32_peak / 1e12,
-                "algorithmic_flops": flops, "transport_s": t_transport}
+                "phase_s": {"init": t_init, "in_grid": t_grid, "free": t_free},
+                "transport_achieved_tflops": flops / t_transport / 1e12}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

@@ -119,6 +119,10 @@ typedef struct mc_run_stats {
   int64_t transport_launches;  /* transport kernel launches (one per generation and batch) */
   double transport_ms; /* summed device time of those launches (CUDA events on the launching stream) */
   double generate_ms;  /* device time of weights, counts and scan */
+  int64_t n_steps_grid;  /* steps taken inside the radial extent of the grid (the rest free-stream) */
+  int64_t n_iters_grid;  /* Verlet predictor passes of those steps */
+  double init_ms, grid_ms, free_ms;   /* transport device time by phase: emission/initialisation,
+                                         in-grid push, free-streaming push */
 } mc_run_stats;
 
 /* One finished superphoton, for per-photon parity checks (layout matches the test oracle's). */

@@ -400,7 +400,7 @@ static int generate(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st) {
 
 // Launch helper: records the launch's device time between two events on the stream and reads the
 // counters back (the host needs the list lengths to size the next phase).
-#define TIMED_LAUNCH(launch_expr)                                                                         \
+#define TIMED_LAUNCH(phase, launch_expr)                                                                  \
   do {                                                                                                    \
     CU(cudaEventRecord(c->ev[0], st));                                                                    \
     launch_expr;                                                                                          \
@@ -411,6 +411,7 @@ static int generate(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st) {
     float ms_ = 0.0f;                                                                                     \
     CU(cudaEventElapsedTime(&ms_, c->ev[0], c->ev[1]));                                                   \
     c->t_transport += ms_;                                                                                \
+    c->t_phase[phase] += ms_;                                                                             \
     c->n_launch++;                                                                                        \
   } while (0)
 
@@ -474,7 +475,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
       CU(cudaMemsetAsync(c->cnt + CNT_NEXT, 0, 2 * sizeof(unsigned long long), st));
       CU(cudaMemsetAsync(c->cnt + CNT_L0, 0, 2 * sizeof(unsigned long long), st));
       int grid_init = (int)std::min<int64_t>((int64_t)c->sms * 4, (n_items + block - 1) / block);
-      TIMED_LAUNCH(launch_init(m, iio, mixed, grid_init, block, st));
+      TIMED_LAUNCH(0, launch_init(m, iio, mixed, grid_init, block, st));
       int64_t n_grid = (int64_t)c->cnt_host[CNT_L0], n_free = (int64_t)c->cnt_host[CNT_L1];
       while (n_grid > 0 || n_free > 0) {
         if (n_grid > 0) {
@@ -485,7 +486,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
           pio.list_out = c->list_free;
           pio.out_counter = CNT_L1;   // continues after the n_free entries already listed
           int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[0], (n_grid + block - 1) / block);
-          TIMED_LAUNCH(launch_push(m, pio, mixed, 0, grid, block, st));
+          TIMED_LAUNCH(1, launch_push(m, pio, mixed, 0, grid, block, st));
           if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
           n_free = (int64_t)c->cnt_host[CNT_L1];
           n_grid = 0;
@@ -500,7 +501,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
           pio.list_out = c->list_grid;
           pio.out_counter = CNT_L0;
           int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[1], (n_free + block - 1) / block);
-          TIMED_LAUNCH(launch_push(m, pio, mixed, 1, grid, block, st));
+          TIMED_LAUNCH(2, launch_push(m, pio, mixed, 1, grid, block, st));
           if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
           n_grid = (int64_t)c->cnt_host[CNT_L0];
           n_free = 0;
@@ -525,6 +526,11 @@ static void fill_stats(mc_ctx *c, mc_run_stats *s) {
   s->transport_launches = c->n_launch;
   s->transport_ms = c->t_transport;
   s->generate_ms = c->t_generate;
+  s->n_steps_grid = h[CNT_GSTEPS];
+  s->n_iters_grid = h[CNT_GITERS];
+  s->init_ms = c->t_phase[0];
+  s->grid_ms = c->t_phase[1];
+  s->free_ms = c->t_phase[2];
 }
 
 int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards, void *stream, mc_run_stats *stats) {
@@ -541,6 +547,7 @@ int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards
   CU(cudaMemsetAsync(c->spec, 0, sizeof(double) * nspec, st));
   CU(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
   c->t_transport = 0.0;
+  c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0.0;
   c->n_launch = 0;
   rc = transport(c, u0, u1, nullptr, 0, nullptr, 0, seed, st);
   if (rc) return rc;

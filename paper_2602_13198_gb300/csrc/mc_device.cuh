@@ -160,7 +160,9 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
   else sincos(th, &s, &c);
   double s2 = s * s, c2 = c * c;
   double sig = r * r + a2 * c2;
-  double isig = 1.0 / sig;
+  // one division for 1/Sigma, 1/r and 1/sin^2
+  double q = 1.0 / (sig * r * s2);
+  double isig = q * r * s2, ir = q * sig * s2, is2 = q * sig * r;
   double f = 2.0 * M * r * isig;
   double opf = 1.0 + f;
   // Kerr-Schild components (t, r, theta, phi)
@@ -178,13 +180,13 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
   G.g33 = Gpp;
   // inverse: g^tt = -(1+f), g^tr = f, g^rr = (r^2 - 2Mr + a^2)/Sigma, g^rphi = a/Sigma,
   // g^thth = 1/Sigma, g^phph = 1/(Sigma sin^2); divided by the Jacobian factors
-  double ir = 1.0 / r, idth = 1.0 / dth;
+  double idth = (m.hslope == 1.0) ? (1.0 / kPI) : 1.0 / dth;
   G.G00 = -opf;
   G.G01 = f * ir;
   G.G11 = (r * r - 2.0 * M * r + a2) * isig * ir * ir;
   G.G13 = a * isig * ir;
   G.G22 = isig * idth * idth;
-  G.G33 = isig / s2;
+  G.G33 = isig * is2;
   if (!DERIV) return;
   // derivatives of the KS components with respect to r and theta
   double dfr = 2.0 * M * (sig - 2.0 * r * r) * isig * isig;
@@ -250,12 +252,11 @@ __device__ __forceinline__ void accel(const Geo &G, const double k[4], double A[
 // Step size (reading; the paper gives none): each internal coordinate moves at most eps_geo of
 // its scale (1 for ln r and phi, the distance to the nearer pole for x2).
 __device__ __forceinline__ double stepsize(const DevModel &m, const double X[4], const double K[4]) {
+  // 1 / (1/d1 + 1/d2 + 1/d3) with d1 = eps/(|k1|+S), d2 = eps x2n/(|k2|+S), d3 = eps/(|k3|+S)
   const double SMALL = 1e-40;
   double x2n = fmin(fabs(X[2]), fabs(1.0 - X[2]));
-  double d1 = m.eps_geo / (fabs(K[1]) + SMALL);
-  double d2 = m.eps_geo * x2n / (fabs(K[2]) + SMALL);
-  double d3 = m.eps_geo / (fabs(K[3]) + SMALL);
-  return 1.0 / (1.0 / d1 + 1.0 / d2 + 1.0 / d3);
+  double den = (fabs(K[1]) + SMALL) + (fabs(K[2]) + SMALL) / x2n + (fabs(K[3]) + SMALL);
+  return m.eps_geo / den;
 }
 
 // ---------------------------------------------------------------- tables
@@ -285,6 +286,11 @@ __device__ __forceinline__ double K2_of(const DevModel &m, double thetae) {
   return exp(cubic_table(m.lnK2, m.nK2, kK2LnT0, kK2Step, log(thetae)));
 }
 
+__device__ __forceinline__ double K2_of_ln(const DevModel &m, double thetae, double lt) {
+  if (m.k2_mode == 1) return 2.0 * thetae * thetae;
+  return exp(cubic_table(m.lnK2, m.nK2, kK2LnT0, kK2Step, lt));
+}
+
 __device__ __forceinline__ float K2_of_f(const DevModel &m, float thetae) {
   if (m.k2_mode == 1) return 2.0f * thetae * thetae;
   float f = (__logf(thetae) - (float)kK2LnT0) * (float)(1.0 / kK2Step);
@@ -294,8 +300,7 @@ __device__ __forceinline__ float K2_of_f(const DevModel &m, float thetae) {
   return __expf(l);
 }
 
-__device__ __forceinline__ double hot_lookup(const DevModel &m, double thetae, double eps) {
-  double lt = log(thetae), le = log(eps);
+__device__ __forceinline__ double hot_lookup_ln(const DevModel &m, double lt, double le) {
   double ft = (lt - kHotLT0) / (kHotLT1 - kHotLT0) * (kHotNT - 1);
   double fe = (le - kHotLE0) / (kHotLE1 - kHotLE0) * (kHotNE - 1);
   ft = fmin(fmax(ft, 0.0), (double)(kHotNT - 1));
@@ -307,6 +312,10 @@ __device__ __forceinline__ double hot_lookup(const DevModel &m, double thetae, d
   double v10 = h[(i + 1) * kHotNE + j], v11 = h[(i + 1) * kHotNE + j + 1];
   double l = (1 - a) * (1 - b) * v00 + (1 - a) * b * v01 + a * (1 - b) * v10 + a * b * v11;
   return kSIGT * exp(l);
+}
+
+__device__ __forceinline__ double hot_lookup(const DevModel &m, double thetae, double eps) {
+  return hot_lookup_ln(m, log(thetae), log(eps));
 }
 
 __device__ __forceinline__ float hot_lookup_f(const DevModel &m, float thetae, float eps) {
@@ -432,7 +441,7 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &
   T g00 = (T)G.g00, g01 = (T)G.g01, g03 = (T)G.g03, g11 = (T)G.g11, g13 = (T)G.g13, g22 = (T)G.g22, g33 = (T)G.g33;
   T rho = pr[0], uu = pr[1];
   T U1 = pr[5], U2 = pr[6], U3 = pr[7];
-  T alpha = (T)1 / sqrt(-(T)G.G00);
+  T alpha = rsqrt(-(T)G.G00);
   T q = g11 * U1 * U1 + g22 * U2 * U2 + g33 * U3 * U3 + (T)2 * g13 * U1 * U3;
   T gamma = sqrt((T)1 + q);
   T u0 = gamma / alpha;
@@ -443,7 +452,8 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &
   T uc2 = g22 * u2;
   T uc3 = g03 * u0 + g13 * u1 + g33 * u3;
   T b0 = pr[2] * uc1 + pr[3] * uc2 + pr[4] * uc3;
-  T b1 = (pr[2] + b0 * u1) / u0, b2 = (pr[3] + b0 * u2) / u0, b3 = (pr[4] + b0 * u3) / u0;
+  T iu0 = (T)1 / u0;
+  T b1 = (pr[2] + b0 * u1) * iu0, b2 = (pr[3] + b0 * u2) * iu0, b3 = (pr[4] + b0 * u3) * iu0;
   T bc0 = g00 * b0 + g01 * b1 + g03 * b3;
   T bc1 = g01 * b0 + g11 * b1 + g13 * b3;
   T bc2 = g22 * b2;
@@ -456,15 +466,16 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &
   P.ne = (rho > (T)0) ? rho * (T)m.Ne_unit : (T)0;
   P.B = sqrt(fmax(P.bsq, (T)0)) * (T)m.B_unit;
   if (rho > (T)0 && uu > (T)0) {
-    T trat;
+    // Theta_e = (m_p/m_e)(gam-1)(u/rho)/(1 + T_i/T_e), T_i/T_e = (R_high beta^2 + R_low)/(1 + beta^2)
+    T th;
     if (P.bsq > (T)0) {
-      T beta = uu * ((T)m.gam - (T)1) / ((T)0.5 * P.bsq);
+      T beta = (T)2 * uu * ((T)m.gam - (T)1) / P.bsq;
       T b2x = beta * beta;
-      trat = (T)m.R_high * b2x / ((T)1 + b2x) + (T)m.R_low / ((T)1 + b2x);
+      th = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu * ((T)1 + b2x) /
+           (rho * ((T)1 + (T)m.R_low + ((T)1 + (T)m.R_high) * b2x));
     } else {
-      trat = (T)m.R_high;
+      th = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu / (rho * ((T)1 + (T)m.R_high));
     }
-    T th = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu / rho / ((T)1 + trat);
     P.thetae = fmin(th, (T)m.thetae_max);
   } else {
     P.thetae = (T)0;
@@ -489,22 +500,25 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
   double eps = -(K[0] * P.ucov[0] + K[1] * P.ucov[1] + K[2] * P.ucov[2] + K[3] * P.ucov[3]);
   if (!(eps > 0.0)) return;
   double nu = eps * (kME * kCL * kCL / kHPL);
+  double lt = log(fmax(P.thetae, 1e-300));
   if (P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
     double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
-    double cth = fmin(1.0, fmax(-1.0, kb / (eps * sqrt(P.bsq))));
+    double cth = fmin(1.0, fmax(-1.0, kb * rsqrt(P.bsq) / eps));
     double s2 = 1.0 - cth * cth;
     if (s2 > 0.0) {
-      double sth = sqrt(s2);
-      double nus = (2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL)) * P.B * P.thetae * P.thetae * sth;
-      double j = 1.4142135623730951 * kPI * kEE * kEE * P.ne * nus / (3.0 * kCL * K2_of(m, P.thetae)) * Gsyn(nu / nus);
-      if (j > 0.0) {
-        // B_nu = 2 h nu^3 / c^2 / expm1(h nu / kT), kT = Theta_e m_e c^2 so h nu / kT = eps / Theta_e
-        double bnu = 2.0 * kHPL * nu * nu * nu / (kCL * kCL) / expm1(eps / P.thetae);
-        c.ana = nu * j / bnu;
+      double nus = (2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL)) * P.B * P.thetae * P.thetae * sqrt(s2);
+      double Xs = nu / nus;
+      double Gs = Gsyn(Xs);
+      if (Gs > 0.0) {
+        // nu alpha_nu = nu j_nu / B_nu with j_nu = sqrt2 pi e^2 n_e nu_s G / (3 c K2) and
+        // B_nu = 2 h nu^3 / (c^2 expm1(h nu / k T)), h nu / k T = eps / Theta_e:
+        // nu alpha_nu = (sqrt2 pi e^2 c / 6h) n_e G expm1(eps/Theta) / (K2 X nu), X = nu/nu_s
+        const double C1 = 1.4142135623730951 * kPI * kEE * kEE * kCL / (6.0 * kHPL);
+        c.ana = C1 * P.ne * Gs * expm1(eps / P.thetae) / (K2_of_ln(m, P.thetae, lt) * Xs * nu);
       }
     }
   }
-  if (want_s) c.ans = nu * P.ne * hot_lookup(m, fmax(P.thetae, 1e-300), eps);
+  if (want_s) c.ans = nu * P.ne * hot_lookup_ln(m, lt, log(eps));
 }
 
 // Mixed precision: the same quantities with FP32 plasma state and coefficient arithmetic.

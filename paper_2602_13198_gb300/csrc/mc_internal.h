@@ -41,6 +41,7 @@ enum {
   CNT_L1,         // appends to the free-streaming list
   CNT_EMIT, CNT_CHILD, CNT_REC, CNT_ABS, CNT_CAPT, CNT_MAXST,
   CNT_STEPS, CNT_ITERS, CNT_NONCONV, CNT_ROUL, CNT_REJCAP, CNT_EVENTS,
+  CNT_GSTEPS, CNT_GITERS,   // steps and predictor passes taken by the in-grid phase
   CNT_N
 };
 
@@ -130,7 +131,7 @@ struct mc_ctx {
   unsigned long long *cnt_host = nullptr;   // pinned
   bool have_run = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  double t_transport = 0.0, t_generate = 0.0;
+  double t_transport = 0.0, t_generate = 0.0, t_phase[3] = {0.0, 0.0, 0.0};
   int64_t n_launch = 0;
   int64_t last_total = 0;
   uint64_t last_seed = 0;

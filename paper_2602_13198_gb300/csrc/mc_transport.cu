@@ -29,7 +29,7 @@ struct Ph {
 };
 
 struct LocalStats {
-  unsigned long long emit, child, rec, abs, capt, maxst, steps, iters, nonconv, roul, rejcap, events;
+  unsigned long long emit, child, rec, abs, capt, maxst, steps, iters, nonconv, roul, rejcap, events, gsteps, giters;
 };
 
 template <bool MIXED>
@@ -260,6 +260,8 @@ __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls)
     p.A[q] = An[q];
   }
   ls.iters += it;
+  ls.giters += it;
+  ls.gsteps++;
   if (!conv) ls.nonconv++;
   p.nsteps++;
   ls.steps++;
@@ -421,10 +423,10 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 
 __device__ __forceinline__ void flush_stats(const LocalStats &ls, unsigned long long *cnt) {
   const int lane = threadIdx.x & 31;
-  unsigned long long v[12] = {ls.emit, ls.child, ls.rec, ls.abs, ls.capt, ls.maxst,
-                              ls.steps, ls.iters, ls.nonconv, ls.roul, ls.rejcap, ls.events};
+  unsigned long long v[14] = {ls.emit, ls.child, ls.rec, ls.abs, ls.capt, ls.maxst,
+                              ls.steps, ls.iters, ls.nonconv, ls.roul, ls.rejcap, ls.events, ls.gsteps, ls.giters};
 #pragma unroll
-  for (int q = 0; q < 12; ++q) {
+  for (int q = 0; q < 14; ++q) {
     unsigned long long s = warp_sum(v[q]);
     if (lane == 0 && s) atomicAdd(cnt + CNT_EMIT + q, s);
   }
@@ -472,7 +474,7 @@ __device__ __forceinline__ void load_ph(const Pool &P, int64_t i, Ph &p) {
 // Emission or child loading + transport initialisation, one item per thread (grid-stride).
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t n_round = (io.n_items + stride - 1) / stride * stride;   // warp-uniform trip count
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_round; idx += stride) {
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
 template <bool MIXED, int PHASE>
 __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
   const int lane = threadIdx.x & 31;
-  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   Ph p;
   int64_t slot = -1;
   bool live = false;

@@ -58,18 +58,20 @@ class GridDesc(C.Structure):
     ]
 
 
-STAT_NAMES = ("n_emit", "n_child", "n_rec", "n_abs", "n_capt", "n_maxst", "n_steps", "n_iters",
-              "n_nonconv", "n_roul_surv", "n_rej_cap", "n_events", "n_total", "err_flags",
-              "transport_launches", "transport_ms", "generate_ms")
+INT_STATS = ("n_emit", "n_child", "n_rec", "n_abs", "n_capt", "n_maxst", "n_steps", "n_iters",
+             "n_nonconv", "n_roul_surv", "n_rej_cap", "n_events", "n_total", "err_flags", "transport_launches")
 
 
 class RunStats(C.Structure):
-    _fields_ = [(n, C.c_int64) for n in STAT_NAMES[:-2]] + [("transport_ms", C.c_double), ("generate_ms", C.c_double)]
+    _fields_ = ([(n, C.c_int64) for n in INT_STATS] + [("transport_ms", C.c_double), ("generate_ms", C.c_double)] +
+                [("n_steps_grid", C.c_int64), ("n_iters_grid", C.c_int64)] +
+                [("init_ms", C.c_double), ("grid_ms", C.c_double), ("free_ms", C.c_double)])
 
     def as_dict(self):
-        d = {n: int(getattr(self, n)) for n in STAT_NAMES[:-2]}
-        d["transport_ms"] = float(self.transport_ms)
-        d["generate_ms"] = float(self.generate_ms)
+        d = {}
+        for n, t in self._fields_:
+            v = getattr(self, n)
+            d[n] = float(v) if t is C.c_double else int(v)
         return d
 
 

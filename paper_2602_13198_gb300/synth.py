@@ -140,3 +140,173 @@ def scattering_sphere(tau_t: float, *, R: float = 10.0, thetae: float = 4.0, **o
     kw = dict(scatter=1, bias_mode=0, bias_p0=bias, n_sc_max=4)
     kw.update(over)
     return sphere("ks", R=R, ne=ne, thetae=thetae, **kw)
+
+
+# ----------------------------------------------------------------------------- tori (section 4.3 stand-ins)
+def _ks_mks_metric(r, th, dth, a):
+    """Covariant Kerr-Schild metric (M = 1) in MKS internal coordinates, as [..., 4, 4] (set-up use)."""
+    s2, c2 = np.sin(th) ** 2, np.cos(th) ** 2
+    sig = r * r + a * a * c2
+    f = 2.0 * r / sig
+    g = np.zeros(r.shape + (4, 4))
+    g[..., 0, 0] = -(1 - f)
+    g[..., 0, 1] = g[..., 1, 0] = f * r
+    g[..., 0, 3] = g[..., 3, 0] = -a * f * s2
+    g[..., 1, 1] = (1 + f) * r * r
+    g[..., 1, 3] = g[..., 3, 1] = -a * s2 * (1 + f) * r
+    g[..., 2, 2] = sig * dth * dth
+    g[..., 3, 3] = s2 * (sig + a * a * s2 * (1 + f))
+    return g
+
+
+def _fm_torus(r, th, a, r_in, r_max, gam):
+    """Fishbone-Moncrief torus (constant l = u^t u_phi): density (max 1), internal energy and the
+    Boyer-Lindquist angular velocity.  With l constant the relativistic Euler equation integrates to
+    ln h = -ln(-u_t) - l Omega + ln(1 + l Omega) + const; Omega solves
+    l g_pp Omega^2 + (2 l g_tp + g_pp) Omega + l g_tt + g_tp = 0 (the BL t-phi block)."""
+    def blk(rr, tt):
+        s2 = np.sin(tt) ** 2
+        sig = rr * rr + a * a * np.cos(tt) ** 2
+        gtt = -(1 - 2 * rr / sig)
+        gtp = -2 * a * rr * s2 / sig
+        gpp = (rr * rr + a * a + 2 * rr * a * a * s2 / sig) * s2
+        return gtt, gtp, gpp
+
+    # l of the circular geodesic (Keplerian) at r_max in the equator: Omega_K = 1/(r^1.5 + a)
+    gtt, gtp, gpp = blk(np.array(r_max), np.array(np.pi / 2))
+    om_k = 1.0 / (r_max ** 1.5 + a)
+    ut = 1.0 / np.sqrt(-(gtt + 2 * gtp * om_k + gpp * om_k ** 2))
+    l = float(ut * ut * (gtp + gpp * om_k))
+
+    def lnh_raw(rr, tt):
+        gtt, gtp, gpp = blk(rr, tt)
+        A, B, C = l * gpp, 2 * l * gtp + gpp, l * gtt + gtp
+        disc = np.sqrt(np.maximum(B * B - 4 * A * C, 0.0))
+        om = (-B + disc) / (2 * A)
+        norm = -(gtt + 2 * gtp * om + gpp * om * om)
+        ok = norm > 0
+        ut = 1.0 / np.sqrt(np.where(ok, norm, 1.0))
+        u_t = ut * (gtt + gtp * om)
+        val = -np.log(np.where(ok & (u_t < 0), -u_t, 1.0)) - l * om + np.log(np.abs(1 + l * om))
+        return np.where(ok & (u_t < 0), val, -np.inf), om, ut
+
+    ref, _, _ = lnh_raw(np.array(r_in), np.array(np.pi / 2))
+    lnh, om, ut = lnh_raw(r, th)
+    lnh = lnh - ref
+    inside = (lnh > 0) & (r >= r_in)
+    h = np.exp(np.where(inside, lnh, 0.0))
+    # polytrope p = kappa rho^gam: p/rho = (h - 1)(gam - 1)/gam; density normalised to max 1
+    rho = np.where(inside, ((h - 1) * (gam - 1) / gam) ** (1 / (gam - 1)), 0.0)
+    rho = rho / rho.max()
+    u = np.where(inside, (h - 1) / gam * rho, 0.0)   # u = p / (gam - 1)
+    return rho, u, np.where(inside, om, 0.0), np.where(inside, ut, 0.0), inside
+
+
+def torus(*, a=0.9375, n1=256, n2=128, n3=1, r_out=40.0, hslope=0.3, r_in=6.0, r_max=12.0, beta_min=100.0,
+          pert=0.1, seed=1, m_bh_msun=4.14e6, M_unit=1e18, R_high=20.0, R_low=1.0, dtype=np.float64,
+          turb_sigma=0.0, turb_slope=-11.0 / 3.0, **over):
+    """Synthetic GRMHD-like snapshot: Fishbone-Moncrief torus (r_in, r_max) around a Kerr hole in
+    modified Kerr-Schild coordinates, r from the horizon to r_out, with a single poloidal field loop
+    (A_phi ~ max(rho - 0.2, 0)) normalised to min beta = beta_min, atmosphere floors rho = 1e-5 r^-1.5,
+    u = 1e-7 r^-2.5, and seeded lognormal perturbations of rho and u (exp(pert N(0,1) - pert^2/2) per
+    zone).  With turb_sigma > 0 (3-D grids) a Gaussian random field with power spectrum
+    P(k) ~ k^turb_slope (k^-11/3: the 3-D form of a k^-5/3 spectrum) and standard deviation turb_sigma
+    multiplies rho and u as exp(delta - sigma^2/2)."""
+    gam = GAM
+    rh = 1.0 + math.sqrt(1.0 - a * a)
+    g = _grid(n1, n2, n3, math.log(rh), math.log(r_out))
+    X1, X2, X3 = _zone_centres(g)
+    r = np.exp(X1)
+    th = math.pi * X2 + 0.5 * (1 - hslope) * np.sin(2 * math.pi * X2)
+    dth = math.pi * (1 + (1 - hslope) * np.cos(2 * math.pi * X2))
+    rho, uu, om, ut, inside = _fm_torus(r, th, a, r_in, r_max, gam)
+    rng = np.random.default_rng(seed)
+    # velocities: torus u^t (1, 0, 0, Omega) (BL = KS components when u^r = 0); normal-observer
+    # velocity U^i = u^i - u^t g^{ti}/g^{tt}; KS g^{tr}/g^{tt} = -2r/(Sigma + 2r), g^{tphi} = 0
+    sig = r * r + a * a * np.cos(th) ** 2
+    U1 = np.where(inside, ut * 2 * r / (sig + 2 * r) / r, 0.0)
+    U3 = np.where(inside, ut * om, 0.0)
+    # atmosphere at rest with respect to normal observers
+    rho_fl, u_fl = 1e-5 * r ** -1.5, 1e-7 * r ** -2.5
+    rho = np.maximum(rho, rho_fl)
+    uu = np.maximum(uu, u_fl)
+    # field from A_phi (zone centres, centred differences in x1, x2): B^1 = -d2 A / sqrt(-g), B^2 = d1 A / sqrt(-g)
+    shape = (n1, n2, n3)
+    Aphi = np.maximum(rho.reshape(shape) - 0.2, 0.0)
+    dA1 = np.gradient(Aphi, g["dx1"], axis=0)
+    dA2 = np.gradient(Aphi, g["dx2"], axis=1)
+    sqrtg = (sig * np.sin(th) * r * dth).reshape(shape)
+    B1 = (-dA2 / sqrtg).ravel()
+    B2 = (dA1 / sqrtg).ravel()
+    B3 = np.zeros_like(B1)
+    # fluid-frame b^2 for the normalisation
+    G = _ks_mks_metric(r, th, dth, a)
+    Gi = np.linalg.inv(G)
+    alpha = 1 / np.sqrt(-Gi[:, 0, 0])
+    Ut = np.stack([np.zeros_like(r), U1, np.zeros_like(r), U3], axis=1)
+    qq = np.einsum("ni,nij,nj->n", Ut[:, 1:], G[:, 1:, 1:], Ut[:, 1:])
+    gamma = np.sqrt(1 + qq)
+    ucon = np.stack([gamma / alpha, U1 - gamma * alpha * Gi[:, 0, 1], np.zeros_like(r), U3 - gamma * alpha * Gi[:, 0, 3]], 1)
+    ucov = np.einsum("nij,nj->ni", G, ucon)
+    Bv = np.stack([np.zeros_like(r), B1, B2, B3], 1)
+    bt = np.einsum("ni,ni->n", Bv, ucov)
+    bcon = (Bv + bt[:, None] * ucon) / ucon[:, :1]
+    bcon[:, 0] = bt
+    bsq = np.einsum("ni,nij,nj->n", bcon, G, bcon)
+    beta = np.where(bsq > 0, (gam - 1) * uu / (0.5 * np.maximum(bsq, 1e-300)), np.inf)
+    sel = inside & (rho > 0.2)
+    norm = math.sqrt(beta[sel].min() / beta_min) if sel.any() else 1.0
+    B1 *= norm
+    B2 *= norm
+    # perturbations
+    fac = np.exp(pert * rng.standard_normal(r.size) - 0.5 * pert * pert)
+    rho = rho * fac
+    uu = uu * np.exp(pert * rng.standard_normal(r.size) - 0.5 * pert * pert)
+    if turb_sigma > 0 and n3 > 1:
+        kx = np.fft.fftfreq(n1)[:, None, None]
+        ky = np.fft.fftfreq(n2)[None, :, None]
+        kz = np.fft.fftfreq(n3)[None, None, :]
+        k = np.sqrt(kx * kx + ky * ky + kz * kz)
+        amp = np.where(k > 0, np.where(k > 0, k, 1.0) ** (turb_slope / 2.0), 0.0)
+        noise = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        delta = np.real(np.fft.ifftn(noise * amp))
+        delta *= turb_sigma / delta.std()
+        d = delta.ravel()
+        rho = rho * np.exp(d - 0.5 * turb_sigma ** 2)
+        uu = uu * np.exp(d - 0.5 * turb_sigma ** 2)
+    prim = np.stack([rho, uu, B1, B2, B3, U1, np.zeros_like(r), U3]).astype(dtype)
+    g["prim"] = prim
+    params = base_params(a=a, mass=1.0, hslope=hslope, L_unit=length_unit(m_bh_msun), M_unit=M_unit,
+                         R_high=R_high, R_low=R_low, w_min=1e20, scatter=1, bias_mode=2, bias_p0=96e4,
+                         n_sc_max=3, dh=0.05)
+    params.update(over)
+    return params, g
+
+
+def torus3d(**over):
+    """3-D snapshot stand-in: a = 0.5, 288 x 128 x 128, FP32 fields, torus x lognormal turbulence
+    (sigma 0.1, P(k) ~ k^-11/3), 6 inclination bins, mixed precision intended."""
+    kw = dict(a=0.5, n1=288, n2=128, n3=128, dtype=np.float32, turb_sigma=0.1, n_incl=6)
+    kw.update(over)
+    return torus(**kw)
+
+
+def survey(n_models=64, seed=1):
+    """Batched parameter survey: models drawn (seeded) from spin {-0.94,-0.5,0,0.5,0.94} x
+    R_high {1,10,40,160} x accretion-rate scale {0.5,1,2,4} (M_unit x scale), grids 128x64, 192x96 or
+    256x128, N_s log-uniform in [1e5, 1e7].  Returns a list of (params, grid, N_s)."""
+    rng = np.random.default_rng(seed)
+    spins = [-0.94, -0.5, 0.0, 0.5, 0.94]
+    rhs = [1.0, 10.0, 40.0, 160.0]
+    scales = [0.5, 1.0, 2.0, 4.0]
+    grids = [(128, 64), (192, 96), (256, 128)]
+    out = []
+    for i in range(n_models):
+        a = spins[rng.integers(len(spins))]
+        rh = rhs[rng.integers(len(rhs))]
+        sc = scales[rng.integers(len(scales))]
+        n1, n2 = grids[rng.integers(len(grids))]
+        ns = float(10 ** rng.uniform(5, 7))
+        p, g = torus(a=a, n1=n1, n2=n2, R_high=rh, M_unit=1e18 * sc, seed=seed * 1000 + i)
+        out.append((p, g, ns))
+    return out

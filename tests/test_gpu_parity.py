@@ -156,3 +156,68 @@ def test_ragged_3d_float32_grid():
     uids = np.arange(0, tot, max(1, tot // 300))
     r = compare_logs(gm.trace(2e4, 5, uids), om.run(uids=uids, log=True)["log"])
     assert len(r["flips"]) <= 1 and r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9
+
+
+# ------------------------------------------------------------------ GRMHD-like stand-ins (section 4.3)
+@pytest.fixture(scope="module")
+def tori():
+    out = {}
+    out["torus_small"] = synth.torus(n1=64, n2=32)
+    out["torus3d_small"] = synth.torus3d(n1=48, n2=24, n3=16)
+    return out
+
+
+@pytest.mark.parametrize("name,n_s,seed", [("torus_small", 2e4, 1), ("torus3d_small", 2e4, 2)])
+def test_torus_counts_end_states_and_spectrum(tori, name, n_s, seed):
+    p, g = tori[name]
+    go = dict(g, prim=np.asarray(g["prim"], dtype=np.float64))   # oracle reads the same (rounded) values
+    gm = gpu_model(p, g)
+    st = gm.run(n_s, seed)
+    om = oracle_model(p, go)
+    tot = om.prepare(n_s, seed)
+    assert st["n_total"] == tot
+    assert np.array_equal(gm.zone_counts(), om.zones()["counts"])
+    ro = om.run(log=True)
+    ok, bad = spectra_agree(gm.spectrum_sums(), ro["spec"])
+    assert ok, bad
+    uids = np.arange(0, tot, max(1, tot // 500))
+    r = compare_logs(gm.trace(n_s, seed, uids), om.run(uids=uids, log=True)["log"])
+    assert r["n"] >= 0.99 * len(uids)
+    assert len(r["flips"]) <= max(1, 0.002 * r["n"])
+    assert r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9 and r["worst"]["w"] < 1e-7
+    assert st["n_child"] > 0
+
+
+def test_torus_full_size_sampled():
+    # the 2-D GRMHD-like workload at its full size (256 x 128, N_s = 1e7): bit-exact counts, and
+    # per-superphoton parity on a sample of uids the oracle can trace one by one
+    p, g = synth.torus()
+    gm = gpu_model(p, g)
+    st = gm.run(1e7, 1)
+    om = oracle_model(p, g)
+    tot = om.prepare(1e7, 1)
+    assert st["n_total"] == tot
+    assert np.array_equal(gm.zone_counts(), om.zones()["counts"])
+    rng = np.random.default_rng(7)
+    uids = np.sort(rng.choice(tot, size=400, replace=False))
+    r = compare_logs(gm.trace(1e7, 1, uids), om.run(uids=uids, log=True)["log"])
+    assert r["n"] >= 0.99 * len(uids)
+    assert len(r["flips"]) <= 2
+    assert r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9
+
+
+def test_scattering_sphere_full_size_sampled():
+    # the benchmark workload at full size (1024 x 128, N_s = 1e7), per-superphoton parity on samples
+    p, g = synth.scattering_sphere(1e-1)
+    gm = gpu_model(p, g)
+    st = gm.run(1e7, 3)
+    om = oracle_model(p, g)
+    tot = om.prepare(1e7, 3)
+    assert st["n_total"] == tot
+    assert np.array_equal(gm.zone_counts(), om.zones()["counts"])
+    rng = np.random.default_rng(8)
+    uids = np.sort(rng.choice(tot, size=600, replace=False))
+    r = compare_logs(gm.trace(1e7, 3, uids), om.run(uids=uids, log=True)["log"])
+    assert r["n"] >= 0.99 * len(uids)
+    assert len(r["flips"]) <= 2
+    assert r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9
