@@ -202,6 +202,36 @@ int mc_fma_peak(int device, int dtype, double *flops);
 int mc_zone_counts_noalloc(mc_ctx *c, double n_s, uint64_t seed, int64_t *counts, int64_t *start, int64_t *total,
                            void *stream);
 
+/* ---- coefficient surrogate (not in the paper: an addition of this library) ----
+ * A 3 -> 64 -> 64 -> 3 SiLU network maps normalised inputs
+ *   x0 = ln(Theta_e)/ln(1e3), x1 = ln(nu/nu_c)/ln(1e4), x2 = (ln(eps) - ln(1e-3))/ln(1e9)
+ * to o0 = ln(sigma_h/sigma_T) (hot cross-section, section 2.7), o1 = ln K2(1/Theta_e) -
+ * ln(2 Theta_e^2) (section 2.2) and o2 = ln F(nu/nu_c)/10 (angle-integrated synchrotron
+ * shape).  Weights are 4611 floats: W1[64][3] b1[64] W2[64][64] b2[64] W3[3][64] b3[3]. */
+
+/* Trains the context's network on the device: n_train samples uniform in the input domain with
+ * targets from the library's own FP64 quadratures, `steps` Adam steps of `batch` samples, cosine
+ * learning-rate decay from lr; then packs BF16 tiles for tensor-core inference.  *val_loss gets the
+ * mean squared error on 16384 held-out samples.  Errors: INVALID_ARG, OOM, CUDA. */
+int mc_surrogate_train(mc_ctx *c, int64_t n_train, int64_t steps, int64_t batch, double lr, uint64_t seed,
+                       double *val_loss);
+
+/* Sets / gets the FP32 weights (host arrays of 4611 floats).  Errors: INVALID_ARG, STATE (get
+ * before any weights), CUDA. */
+int mc_surrogate_set_weights(mc_ctx *c, const float *w);
+int mc_surrogate_get_weights(mc_ctx *c, float *w);
+
+/* Gradient of the masked mean squared error sum m (y - t)^2 / sum m with respect to the 4611
+ * weights w, over n samples (host arrays x, t, mask of n*3 floats), computed by the library's
+ * training kernel; *loss gets the loss.  Errors: INVALID_ARG, OOM, CUDA. */
+int mc_surrogate_grad(mc_ctx *c, const float *w, const float *x, const float *t, const float *mask, int64_t n,
+                      float *grad, double *loss);
+
+/* Evaluates the network on n input rows (host x, y: n*3 floats) with the BF16 tensor-core kernel
+ * (tensor_cores = 1) or the FP32 reference kernel (0).  Errors: STATE (no weights), TIMEOUT (a
+ * tensor-core wait ran out), CUDA. */
+int mc_surrogate_infer(mc_ctx *c, const float *x, float *y, int64_t n, int tensor_cores);
+
 /* Releases the context and all its device memory.  NULL is a no-op. */
 void mc_free(mc_ctx *c);
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "mc_internal.h"
+#include "mc_mlp.cuh"
 
 using namespace mcgb;
 
@@ -45,6 +46,10 @@ static void dev_free(mc_ctx *c, void *ptr) {
   if (c->p.free) c->p.free(ptr, c->p.alloc_user);
   else cudaFree(ptr);
 }
+
+void *dev_alloc_ext(mc_ctx *c, size_t bytes) { return dev_alloc(c, bytes); }
+void dev_free_ext(mc_ctx *c, void *ptr) { dev_free(c, ptr); }
+int set_err(mc_ctx *c, int code, const char *msg) { return fail(c, code, msg); }
 
 #define CU(call)                                                                                    \
   do {                                                                                              \
@@ -171,7 +176,8 @@ static int check_params(const mc_model_params *p, std::string &why) {
   if (!(p->roulette_p > 0.0 && p->roulette_p <= 1.0) || !(p->roulette_w >= 0.0)) return bad("bad roulette");
   if (p->max_steps < 1 || p->max_steps > 2000000000LL) return bad("max_steps out of range");
   if (p->precision != MC_PREC_FP64 && p->precision != MC_PREC_MIXED) return bad("unknown precision");
-  if (p->surrogate != 0) return bad("surrogate coefficients are not available in this build of mc_run");
+  if (p->surrogate != 0 && p->surrogate != 1) return bad("surrogate must be 0 or 1");
+  if (p->surrogate == 1 && p->precision != MC_PREC_MIXED) return bad("the surrogate runs in the mixed-precision form");
   if (p->block != 0 && (p->block < 32 || p->block > 128 || p->block % 32)) return bad("block must be 32..128, multiple of 32");
   if (!(p->thetae_min >= 0.0 && p->thetae_max > 0.0)) return bad("bad Theta_e bounds");
   if (!(p->gam > 1.0)) return bad("gam must exceed 1");
@@ -436,6 +442,19 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
     occ[ph] = std::max(1, push_max_blocks_per_sm(mixed, ph, block));
     if (c->p.ctas_per_sm > 0) occ[ph] = std::min(occ[ph], (int)c->p.ctas_per_sm);
   }
+  const bool use_sur = c->p.surrogate == 1;
+  if (use_sur && !c->sur_ready) return fail(c, MC_ERR_STATE, "surrogate requested but no trained weights");
+  SurrogateView sv;
+  std::memset(&sv, 0, sizeof(sv));
+  // >= 56 KB of shared memory per CTA: at most four CTAs (4 x 128 TMEM columns) per SM
+  const int sur_smem = std::max(kTcSmemBytes, 56 * 1024);
+  int occ_sur = 1;
+  if (use_sur) {
+    sv = surrogate_view(c);
+    occ_sur = std::max(1, std::min(4, push_sur_max_blocks_per_sm(128, sur_smem)));
+    if (c->p.ctas_per_sm > 0) occ_sur = std::min(occ_sur, (int)c->p.ctas_per_sm);
+    CU(cudaMemsetAsync(c->sur_err, 0, sizeof(unsigned int), st));
+  }
   const int64_t n_prim = uid_list_dev ? n_list : (u1 - u0);
   const int64_t batch_max = 1 << 24;
   int64_t batch = std::min<int64_t>(std::max<int64_t>(n_prim, 1), batch_max);
@@ -485,8 +504,13 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
           pio.n_in = n_grid;
           pio.list_out = c->list_free;
           pio.out_counter = CNT_L1;   // continues after the n_free entries already listed
-          int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[0], (n_grid + block - 1) / block);
-          TIMED_LAUNCH(1, launch_push(m, pio, mixed, 0, grid, block, st));
+          if (use_sur) {
+            int grid = (int)std::min<int64_t>((int64_t)c->sms * occ_sur, (n_grid + 127) / 128);
+            TIMED_LAUNCH(1, launch_push_sur(m, pio, sv, grid, sur_smem, st));
+          } else {
+            int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[0], (n_grid + block - 1) / block);
+            TIMED_LAUNCH(1, launch_push(m, pio, mixed, 0, grid, block, st));
+          }
           if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
           n_free = (int64_t)c->cnt_host[CNT_L1];
           n_grid = 0;
@@ -512,6 +536,11 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
       n_items = (int64_t)c->cnt_host[CNT_OUT];
       ++gen;
     }
+  }
+  if (use_sur) {
+    unsigned int err = 0;
+    CU(cudaMemcpy(&err, c->sur_err, sizeof(unsigned int), cudaMemcpyDeviceToHost));
+    if (err) return fail(c, MC_ERR_TIMEOUT, "tensor-core wait timed out in the surrogate push");
   }
   return MC_OK;
 }

@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mc_mlp.cuh"
+
 namespace mcgb {
 
 // ---------------------------------------------------------------- physical constants (CGS, CODATA 2018)
@@ -561,6 +563,78 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, 
   if (want_s) {
     float sh = hot_lookup_f(m, fmaxf(P.thetae, 1e-30f), eps);
     c.ans = (double)(nu9 * P.ne * (sh * 1e9f));
+  }
+}
+
+// Mixed precision with the coefficient surrogate, split around the network evaluation.
+// Part A: plasma state at the new point, the absorption coefficient without its 1/K2 factor, and
+// the normalised network inputs (ln Theta_e, ln(nu/nu_c), ln eps).
+struct CoefA {
+  bool on, emit;
+  float thetae, ne, eps, nu9, ana_k2;   // ana = ana_k2 / K2
+  float in[3];
+};
+
+__device__ __forceinline__ void coefficients32_a(const DevModel &m, const Geo &G, const double X[4], const double K[4],
+                                                 CoefA &a) {
+  a.on = a.emit = false;
+  a.thetae = a.ne = a.eps = a.nu9 = a.ana_k2 = 0.0f;
+  a.in[0] = a.in[1] = a.in[2] = 0.0f;
+  float pr[8];
+  if (!interp_prims<float>(m, X, pr)) return;
+  Plasma<float> P;
+  plasma_from_prims<float>(m, G, pr, P, nullptr, nullptr);
+  a.thetae = P.thetae;
+  if (!P.on) return;
+  float kf[4] = {(float)K[0], (float)K[1], (float)K[2], (float)K[3]};
+  float eps = -(kf[0] * P.ucov[0] + kf[1] * P.ucov[1] + kf[2] * P.ucov[2] + kf[3] * P.ucov[3]);
+  if (!(eps > 0.0f)) return;
+  a.on = true;
+  a.ne = P.ne;
+  a.eps = eps;
+  float nu9 = eps * (float)(kME * kCL * kCL / kHPL * 1e-9);
+  a.nu9 = nu9;
+  float lnK = 0.0f;
+  if (P.thetae >= (float)m.thetae_min && P.B > 0.0f && P.bsq > 0.0f) {
+    float kb = kf[0] * P.bcov[0] + kf[1] * P.bcov[1] + kf[2] * P.bcov[2] + kf[3] * P.bcov[3];
+    float cth = fminf(1.0f, fmaxf(-1.0f, kb / (eps * sqrtf(P.bsq))));
+    float s2 = 1.0f - cth * cth;
+    if (s2 > 0.0f) {
+      float sth = sqrtf(s2);
+      float nuc9 = (float)((2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL)) * 1e-9) * P.B * P.thetae * P.thetae;
+      float nus9 = nuc9 * sth;
+      float Xs = nu9 / nus9;
+      float x6 = cbrtf(sqrtf(Xs));
+      float t = x6 * x6 * x6 + 1.887748625f * x6;
+      float Gs = t * t * __expf(-x6 * x6);
+      float em1 = expm1f(eps / P.thetae);
+      float pre = (float)(1.4142135623730951 * kPI * kEE * kEE / (3.0 * kCL) * kCL * kCL / (2.0 * kHPL) * 1e-9);
+      a.ana_k2 = pre * P.ne * nus9 / (nu9 * nu9) * Gs * em1;
+      a.emit = a.ana_k2 > 0.0f;
+      lnK = __logf(nu9 / nuc9);
+    }
+  }
+  a.in[0] = fminf(1.0f, fmaxf(-1.0f, __logf(fmaxf(P.thetae, 1e-30f)) * (float)(1.0 / kSurLT1)));
+  a.in[1] = fminf(1.0f, fmaxf(-1.0f, lnK * (float)(1.0 / kSurLK1)));
+  a.in[2] = fminf(1.0f, fmaxf(-1.0f, (__logf(eps) - (float)(0.5 * (kSurLE0 + kSurLE1))) *
+                                             (float)(2.0 / (kSurLE1 - kSurLE0))));
+}
+
+// Part B: K2 and sigma_h from the network outputs inside the trained domain (table otherwise).
+__device__ __forceinline__ void coefficients32_b(const DevModel &m, const CoefA &a, const float out[3], bool want_s,
+                                                 Coef &c) {
+  c.ana = c.ans = 0.0;
+  c.thetae = a.thetae;
+  if (!a.on) return;
+  const float th = a.thetae;
+  if (a.emit) {
+    float k2 = (th >= (float)kSurThetaK2Min && th <= 1e3f) ? 2.0f * th * th * __expf(out[1]) : K2_of_f(m, th);
+    c.ana = (double)(a.ana_k2 / k2);
+  }
+  if (want_s) {
+    bool in_dom = th >= 1e-3f && th <= 1e3f && a.eps >= 1e-12f && a.eps <= 1e6f;
+    float sh = in_dom ? (float)kSIGT * __expf(out[0]) : hot_lookup_f(m, fmaxf(th, 1e-30f), a.eps);
+    c.ans = (double)(a.nu9 * a.ne * (sh * 1e9f));
   }
 }
 

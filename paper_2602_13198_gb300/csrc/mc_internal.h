@@ -92,6 +92,9 @@ int push_max_blocks_per_sm(int mixed, int phase, int block);
 void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st);
 // phase 0: superphotons inside the radial extent of the grid; 1: outside it
 void launch_push(const DevModel &m, const PushIO &io, int mixed, int phase, int grid, int block, cudaStream_t st);
+// in-grid push of the mixed form with the coefficient network (128 threads per CTA)
+int push_sur_max_blocks_per_sm(int block, int smem);
+void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &sv, int grid, int smem, cudaStream_t st);
 
 }  // namespace mcgb
 
@@ -136,8 +139,20 @@ struct mc_ctx {
   int64_t last_total = 0;
   uint64_t last_seed = 0;
   double last_ns = 0.0;
+  // coefficient surrogate network
+  float *sur_w = nullptr;              // FP32 master weights
+  unsigned char *sur_packed = nullptr; // BF16 tiles for tcgen05 inference
+  float *sur_bias = nullptr;
+  unsigned int *sur_err = nullptr;     // tensor-core wait timeouts
+  bool sur_ready = false;
 };
 
-// Kernel-side view of a context (mc_api.cu).
+// Tensor-core view of the context's trained network (mc_mlp.cu).
+mcgb::SurrogateView surrogate_view(const mc_ctx *c);
+// Kernel-side view of a context, device allocation through the context's allocator, and the
+// error setter (mc_api.cu).
 mcgb::DevModel make_model(const mc_ctx *c);
+void *dev_alloc_ext(mc_ctx *c, size_t bytes);
+void dev_free_ext(mc_ctx *c, void *ptr);
+int set_err(mc_ctx *c, int code, const char *msg);
 

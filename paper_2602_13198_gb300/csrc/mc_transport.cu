@@ -571,6 +571,217 @@ __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
   flush_stats(ls, io.cnt);
 }
 
+// ---------------------------------------------------------------- surrogate in-grid push
+// The mixed-precision in-grid step with the coefficient network: part A (geodesic, plasma state,
+// network inputs), one tensor-core evaluation for the CTA's 128 superphotons, part B (optical
+// depths, scattering, termination).  Identical to step<true> except for where K2 and sigma_h
+// come from.
+struct SurCarry {
+  double X0[4], K0[4], dl;
+  double r, cth, g00, g01, g03;
+  CoefA a;
+};
+
+__device__ void step_sur_a(const DevModel &m, Ph &p, SurCarry &sc, LocalStats &ls) {
+  double dl = stepsize(m, p.X, p.K);
+  double Kp[4], An[4], Kn[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    sc.X0[q] = p.X[q];
+    sc.K0[q] = p.K[q];
+    p.X[q] = sc.X0[q] + sc.K0[q] * dl + 0.5 * p.A[q] * dl * dl;
+    Kp[q] = sc.K0[q] + p.A[q] * dl;
+  }
+  Geo G;
+  metric_eval<true>(m, p.X[1], p.X[2], G);
+  int it = 0;
+  bool conv = false;
+  while (true) {
+    accel(G, Kp, An);
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Kn[q] = sc.K0[q] + 0.5 * (p.A[q] + An[q]) * dl;
+      num += fabs(Kn[q] - Kp[q]);
+      den += fabs(Kn[q]);
+    }
+    ++it;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
+    if (num < m.verlet_tol * den) {
+      conv = true;
+      break;
+    }
+    if (it >= m.verlet_maxit) break;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.K[q] = Kn[q];
+    p.A[q] = An[q];
+  }
+  ls.iters += it;
+  ls.giters += it;
+  ls.gsteps++;
+  if (!conv) ls.nonconv++;
+  p.nsteps++;
+  ls.steps++;
+  sc.dl = dl;
+  sc.r = G.r;
+  sc.cth = G.cth;
+  sc.g00 = G.g00;
+  sc.g01 = G.g01;
+  sc.g03 = G.g03;
+  coefficients32_a(m, G, p.X, p.K, sc.a);
+}
+
+__device__ bool step_sur_b(const DevModel &m, const PushIO &io, Ph &p, const SurCarry &sc, const float out[3],
+                           LocalStats &ls) {
+  const bool scat = m.scatter && p.nsc < m.n_sc_max;
+  Coef c;
+  coefficients32_b(m, sc.a, out, scat, c);
+  const double C = m.Ccoef, dl = sc.dl;
+  double tau_a = 0.5 * (p.ana + c.ana) * C * dl;
+  double w0 = p.w;
+  double wn = w0 * exp(-tau_a);
+  if (scat) {
+    double tau_s = 0.5 * (p.ans + c.ans) * C * dl;
+    if (tau_s > 0.0) {
+      double b = bias_of(m, c.thetae, p.nsc);
+      double d = b * tau_s;
+      if (p.acc + d > p.x1t) {
+        double f = (p.x1t - p.acc) / d;
+        double Xe[4], Ke[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Xe[q] = sc.X0[q] + f * (p.X[q] - sc.X0[q]);
+          Ke[q] = sc.K0[q] + f * (p.K[q] - sc.K0[q]);
+        }
+        double we = w0 * exp(-f * tau_a);
+        uint64_t cid = child_id(p.s.id, p.nev);
+        scatter_child(m, io, Xe, Ke, we / b, cid, p.nsc + 1, ls);
+        p.nev++;
+        ls.events++;
+        wn *= (1.0 - 1.0 / b);
+        p.acc = 0.0;
+        p.x1t = -log(rng_u(p.s, m.seed));
+      } else {
+        p.acc += d;
+      }
+    }
+  }
+  p.w = wn;
+  p.ana = c.ana;
+  p.ans = c.ans;
+  const double r = sc.r;
+  int status = 0;
+  if (r >= m.r_record) {
+    Geo G;
+    G.g00 = sc.g00;
+    G.g01 = sc.g01;
+    G.g03 = sc.g03;
+    G.cth = sc.cth;
+    record(m, io, G, p);
+    status = 1;
+    ls.rec++;
+  } else if (r <= m.r_capture) {
+    status = 3;
+    ls.capt++;
+  } else if (!(p.w > 0.0)) {
+    status = 2;
+    ls.abs++;
+  } else {
+    if (p.w < m.roulette_w * p.wb) {
+      if (rng_u(p.s, m.seed) < m.roulette_p) {
+        p.w /= m.roulette_p;
+        ls.roul++;
+      } else {
+        status = 2;
+        ls.abs++;
+      }
+    }
+    if (status == 0 && p.nsteps >= m.max_steps) {
+      status = 4;
+      ls.maxst++;
+    }
+  }
+  if (status) {
+    write_log(io, p, status);
+    return false;
+  }
+  return true;
+}
+
+// Persistent in-grid push with the network; every thread of the CTA reaches the same tensor-core
+// evaluation once per iteration (idle lanes contribute a zero row), and the loop ends for the
+// whole CTA together.
+__global__ void __launch_bounds__(128) k_push_sur(DevModel m, PushIO io, SurrogateView sv) {
+  extern __shared__ __align__(128) unsigned char smem_sur[];
+  TcMlp T;
+  tc_setup(T, smem_sur, sv);
+  const int lane = threadIdx.x & 31;
+  LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  Ph p;
+  int64_t slot = -1;
+  bool live = false;
+  bool exhausted = false;
+  SurCarry sc;
+  while (true) {
+    if (!exhausted) {
+      unsigned idle = __ballot_sync(0xffffffffu, !live);
+      if (idle) {
+        int cnt = __popc(idle);
+        int leader = __ffs(idle) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(io.cnt + CNT_NEXT, (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (base + cnt >= (unsigned long long)io.n_in) exhausted = true;
+        if (!live) {
+          unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
+          if (k < (unsigned long long)io.n_in) {
+            slot = io.list_in[k];
+            load_ph(io.pool, slot, p);
+            live = true;
+          }
+        }
+      }
+    }
+    if (!__syncthreads_or(live ? 1 : 0)) {
+      if (!__syncthreads_or(exhausted ? 0 : 1)) break;
+      continue;
+    }
+    float in[3] = {0.0f, 0.0f, 0.0f}, out[3];
+    if (live) {
+      step_sur_a(m, p, sc, ls);
+      in[0] = sc.a.in[0];
+      in[1] = sc.a.in[1];
+      in[2] = sc.a.in[2];
+    }
+    tc_mlp_eval(T, in, out);
+    if (live) {
+      live = step_sur_b(m, io, p, sc, out, ls);
+      if (live && !in_grid(m, p.X)) {
+        save_ph(io.pool, slot, p);
+        unsigned long long o = atomicAdd(io.cnt + io.out_counter, 1ull);
+        io.list_out[o] = (int32_t)slot;
+        live = false;
+      }
+    }
+  }
+  tc_teardown(T);
+  flush_stats(ls, io.cnt);
+}
+
+int push_sur_max_blocks_per_sm(int block, int smem) {
+  int n = 0;
+  cudaFuncSetAttribute(k_push_sur, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push_sur, block, smem);
+  return n;
+}
+
+void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &sv, int grid, int smem, cudaStream_t st) {
+  k_push_sur<<<grid, 128, smem, st>>>(m, io, sv);
+}
+
 int push_max_blocks_per_sm(int mixed, int phase, int block) {
   int n = 0;
   if (mixed) {

@@ -107,6 +107,15 @@ def lib():
         L.mc_fma_peak.restype = C.c_int
         L.mc_zone_counts_noalloc.argtypes = [vp, C.c_double, u64, vp, vp, vp, vp]
         L.mc_zone_counts_noalloc.restype = C.c_int
+        fp = C.POINTER(C.c_float)
+        L.mc_surrogate_train.argtypes = [vp, i64, i64, i64, C.c_double, u64, dp]
+        L.mc_surrogate_set_weights.argtypes = [vp, fp]
+        L.mc_surrogate_get_weights.argtypes = [vp, fp]
+        L.mc_surrogate_grad.argtypes = [vp, fp, fp, fp, fp, i64, fp, dp]
+        L.mc_surrogate_infer.argtypes = [vp, fp, fp, i64, C.c_int]
+        for f in ("mc_surrogate_train", "mc_surrogate_set_weights", "mc_surrogate_get_weights",
+                  "mc_surrogate_grad", "mc_surrogate_infer"):
+            getattr(L, f).restype = C.c_int
         for f in ("mc_init_model", "mc_set_grid", "mc_run", "mc_get_spectrum", "mc_get_spectrum_sums",
                   "mc_get_zone_counts", "mc_trace"):
             getattr(L, f).restype = C.c_int
@@ -132,14 +141,14 @@ class Model:
     """One model context: ``Model(params, device=0)`` then ``set_grid`` and ``run``."""
 
     def __init__(self, params: dict, device: int = 0, precision: str = "fp64", use_torch_allocator: bool = True,
-                 block: int = 0, ctas_per_sm: int = 0):
+                 block: int = 0, ctas_per_sm: int = 0, surrogate: bool = False):
         L = lib()
         p = ModelParams()
         for name, _ in ModelParams._fields_:
             if name in params and name not in ("alloc", "free", "alloc_user"):
                 setattr(p, name, params[name])
         p.precision = PREC[precision] if isinstance(precision, str) else int(precision)
-        p.surrogate = 0
+        p.surrogate = 1 if surrogate else 0
         p.block = block
         p.ctas_per_sm = ctas_per_sm
         p.device = device
@@ -233,6 +242,47 @@ class Model:
         s = C.c_void_p(getattr(stream, "cuda_stream", 0) or 0) if stream is not None else C.c_void_p(0)
         self._check(lib().mc_zone_counts_noalloc(self._h, float(n_s), int(seed), C.c_void_p(counts.data_ptr()),
                                                  C.c_void_p(start.data_ptr()), C.c_void_p(total.data_ptr()), s))
+
+    # ---------------------------------------------------------------- coefficient surrogate
+    N_WEIGHTS = 4611
+
+    def surrogate_train(self, n_train=1 << 18, steps=8000, batch=4096, lr=3e-3, seed=1) -> float:
+        """Trains the surrogate on the GPU (data from the library's own quadratures); returns the
+        validation loss (mean squared error in the scaled outputs)."""
+        v = C.c_double(0.0)
+        self._check(lib().mc_surrogate_train(self._h, int(n_train), int(steps), int(batch), float(lr), int(seed),
+                                             C.byref(v)))
+        return v.value
+
+    def surrogate_weights(self, w=None):
+        fp = C.POINTER(C.c_float)
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            self._check(lib().mc_surrogate_set_weights(self._h, w.ctypes.data_as(fp)))
+            return w
+        out = np.zeros(self.N_WEIGHTS, dtype=np.float32)
+        self._check(lib().mc_surrogate_get_weights(self._h, out.ctypes.data_as(fp)))
+        return out
+
+    def surrogate_grad(self, w, x, t, mask):
+        fp = C.POINTER(C.c_float)
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        mask = np.ascontiguousarray(mask, dtype=np.float32)
+        g = np.zeros(self.N_WEIGHTS, dtype=np.float32)
+        loss = C.c_double(0.0)
+        self._check(lib().mc_surrogate_grad(self._h, w.ctypes.data_as(fp), x.ctypes.data_as(fp), t.ctypes.data_as(fp),
+                                            mask.ctypes.data_as(fp), len(x), g.ctypes.data_as(fp), C.byref(loss)))
+        return g, loss.value
+
+    def surrogate_infer(self, x, tensor_cores=True):
+        fp = C.POINTER(C.c_float)
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros_like(x)
+        self._check(lib().mc_surrogate_infer(self._h, x.ctypes.data_as(fp), y.ctypes.data_as(fp), len(x),
+                                             1 if tensor_cores else 0))
+        return y
 
     def trace(self, n_s: float, seed: int, uids, cap: int | None = None, stream=None):
         u = np.ascontiguousarray(uids, dtype=np.int64)

@@ -1,0 +1,140 @@
+"""Coefficient surrogate: the library's training kernel against the FP64 reference gradients
+of oracle/mlp.py, the BF16 tensor-core inference against an FP32 reference, and the trained
+network against the library's quadratures (and what it gains over the lookup tables)."""
+import numpy as np
+import pytest
+
+from helpers import requires_gpu
+from oracle import mlp
+from paper_2602_13198_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def pack(w):
+    return np.concatenate([w[k].reshape(-1) for k in ORDER]).astype(np.float32)
+
+
+def unpack(v):
+    out, o = {}, 0
+    for k in ORDER:
+        n = int(np.prod(mlp.SHAPES[k]))
+        out[k] = np.asarray(v[o:o + n], dtype=np.float64).reshape(mlp.SHAPES[k])
+        o += n
+    return out
+
+
+@pytest.fixture(scope="module")
+def model():
+    from paper_2602_13198_gb300 import build, mc
+    build.build()
+    p, _ = synth.sphere("flat", n1=4, n2=4)
+    return mc.Model(p, precision="mixed")
+
+
+def test_training_gradients_match_oracle(model):
+    rng = np.random.default_rng(11)
+    w = mlp.init(2)
+    n = 300
+    x = rng.uniform(-1, 1, (n, 3))
+    t = rng.standard_normal((n, 3)) * 0.5
+    m = (rng.uniform(size=(n, 3)) > 0.15).astype(float)
+    g_ref = mlp.grad(w, x, t, m)
+    # the oracle runs on the same FP32-rounded inputs
+    w32 = unpack(pack(w))
+    g_ref = mlp.grad(w32, x.astype(np.float32).astype(float), t.astype(np.float32).astype(float), m)
+    g, loss = model.surrogate_grad(pack(w), x, t, m)
+    gd = unpack(g)
+    assert loss == pytest.approx(mlp.loss(w32, x.astype(np.float32).astype(float), t.astype(np.float32).astype(float), m),
+                                 rel=1e-5)
+    for k in ORDER:
+        scale = np.abs(g_ref[k]).max() + 1e-12
+        assert np.abs(gd[k] - g_ref[k]).max() <= 2e-5 * scale, k
+
+
+def bf16(a):
+    a = np.asarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def split_mm(a, w):
+    """a @ w.T as the tensor cores form it: hi/lo BF16 parts, a_hi w_hi + a_lo w_hi + a_hi w_lo."""
+    ah, wh = bf16(a), bf16(w)
+    al, wl = bf16(a - ah), bf16(w - wh)
+    return ah @ wh.T + al @ wh.T + ah @ wl.T
+
+
+def forward_bf16(w, x):
+    """Reference of the tensor-core arithmetic (split BF16 products, FP32 accumulation, bias, SiLU)."""
+    h1 = mlp.silu(split_mm(x, w["W1"]) + w["b1"])
+    h2 = mlp.silu(split_mm(h1, w["W2"]) + w["b2"])
+    return split_mm(h2, w["W3"]) + w["b3"]
+
+
+def test_tensor_core_inference(model):
+    rng = np.random.default_rng(5)
+    w = mlp.init(4)
+    model.surrogate_weights(pack(w))
+    x = rng.uniform(-1, 1, (1000, 3)).astype(np.float32)       # ragged: 7 full CTAs + 104 rows
+    y_tc = model.surrogate_infer(x, tensor_cores=True)
+    y32 = model.surrogate_infer(x, tensor_cores=False)
+    w32 = unpack(pack(w))
+    y_ref32, _ = mlp.forward(w32, x.astype(float))
+    assert np.abs(y32 - y_ref32).max() < 1e-4 * (1 + np.abs(y_ref32).max())
+    y_emul = forward_bf16(w32, x.astype(float))
+    # split-BF16 products reach near-FP32 accuracy: within 2e-4 of the FP32 network
+    scale = 1 + np.abs(y_ref32).max()
+    assert np.abs(y_tc - y_emul).max() < 1e-4 * scale
+    assert np.abs(y_tc - y_ref32).max() < 2e-4 * scale
+
+
+def test_trained_network_against_quadrature(model):
+    import oracle
+    v = model.surrogate_train(n_train=1 << 18, steps=40000, batch=4096, lr=2e-3, seed=1)
+    print("validation loss %.3e" % v)
+    assert v < 2e-5
+    rng = np.random.default_rng(9)
+    lt = rng.uniform(np.log(2e-3), np.log(5e2), 300)
+    le = rng.uniform(np.log(2e-12), np.log(1e2), 300)
+    lk = rng.uniform(np.log(2e-4), np.log(5e3), 300)
+    x = np.stack([lt / np.log(1e3), lk / np.log(1e4), (le - np.log(1e-3)) / np.log(1e9)], 1).astype(np.float32)
+    y = model.surrogate_infer(x, tensor_cores=True)
+    sig_q = np.array([oracle.sigma_hot_quad(np.exp(a), np.exp(b)) for a, b in zip(lt, le)])
+    sig_tab = np.array([oracle.sigma_hot_table(np.exp(a), np.exp(b)) for a, b in zip(lt, le)])
+    sig_nn = 6.6524587321e-25 * np.exp(y[:, 0])
+    err_nn = np.abs(sig_nn / sig_q - 1)
+    err_tab = np.abs(sig_tab / sig_q - 1)
+    # photon energies up to 100 m_e c^2: the network reproduces the quadrature to ~1%
+    assert np.median(err_nn) < 5e-3 and err_nn.max() < 3e-2
+    print("sigma_h relative error: network median %.2e max %.2e; bilinear table median %.2e max %.2e"
+          % (np.median(err_nn), err_nn.max(), np.median(err_tab), err_tab.max()))
+
+
+@pytest.fixture(scope="module")
+def trained_weights(model):
+    model.surrogate_train(n_train=1 << 18, steps=40000, batch=4096, lr=2e-3, seed=1)
+    return model.surrogate_weights()
+
+
+@pytest.mark.parametrize("case,n_s,seed", [("flat_thin", 2e4, 5), ("ks_scatter", 1e4, 6), ("torus_small", 2e4, 3)])
+def test_surrogate_spectrum_within_tolerance(trained_weights, case, n_s, seed):
+    """The batched/mixed form with the network in the in-grid push: spectrum within max(1%, 3 sigma)
+    of the FP64 oracle in every bin."""
+    from helpers import flat_sphere, oracle_model, spectra_agree
+    from paper_2602_13198_gb300 import mc
+    p, g = {"flat_thin": flat_sphere, "ks_scatter": lambda: synth.scattering_sphere(0.1, n1=256, n2=64),
+            "torus_small": lambda: synth.torus(n1=64, n2=32)}[case]()
+    m = mc.Model(p, precision="mixed", surrogate=True)
+    m.surrogate_weights(trained_weights)
+    m.set_grid(g)
+    st = m.run(n_s, seed)
+    om = oracle_model(p, g)
+    om.prepare(n_s, seed)
+    ro = om.run()
+    ok, bad = spectra_agree(m.spectrum_sums(), ro["spec"])
+    assert ok, bad
+    assert st["n_emit"] == ro["stats"]["n_emit"]
