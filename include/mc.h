@@ -71,6 +71,7 @@ typedef struct mc_model_params {
   double bias_p0;      /* bias parameter; see bias_mode */
   double lnu_lo, lnu_hi;   /* spectrum range, log10(nu/Hz) */
   double roulette_w, roulette_p;  /* Russian roulette when w < roulette_w * w_birth, survival roulette_p */
+  double bias_max;     /* upper bound on the bias b (any b >= 1 leaves the estimate unbiased) */
   int64_t max_steps;   /* drop a superphoton after this many steps */
   int32_t n_nu;        /* weight-table nodes in ln nu (>= 2) */
   int32_t verlet_maxit;/* cap on Verlet predictor iterations */
@@ -123,6 +124,10 @@ typedef struct mc_run_stats {
   int64_t n_iters_grid;  /* Verlet predictor passes of those steps */
   double init_ms, grid_ms, free_ms;   /* transport device time by phase: emission/initialisation,
                                          in-grid push, free-streaming push */
+  int32_t batch_min_blocks;  /* mc_run_batch: register-cap variant (minimum resident CTAs per SM) */
+  int32_t batch_ctas;        /* mc_run_batch: persistent grid size in CTAs */
+  int32_t batch_graph;       /* mc_run_batch: 1 if the run replayed a captured CUDA graph */
+  int32_t pad0;
 } mc_run_stats;
 
 /* One finished superphoton, for per-photon parity checks (layout matches the test oracle's). */
@@ -231,6 +236,22 @@ int mc_surrogate_grad(mc_ctx *c, const float *w, const float *x, const float *t,
  * (tensor_cores = 1) or the FP32 reference kernel (0).  Errors: STATE (no weights), TIMEOUT (a
  * tensor-core wait ran out), CUDA. */
 int mc_surrogate_infer(mc_ctx *c, const float *x, float *y, int64_t n, int tensor_cores);
+
+/* Batched survey (section 1's parameter surveys): runs n <= 64 models (contexts with grids, same
+ * device, precision and surrogate mode) together, each with its own N_s (n_s[i]) and seed.  Per
+ * model the weights/counts/scan run as in mc_run; then ONE cooperative persistent kernel
+ * transports every superphoton of every model through all scattering generations.  flags: bit 0
+ * (MC_BATCH_AUTOTUNE): before the first batched run of this leading context, time 5%-size
+ * calibration runs over the register-cap variants and resident CTAs per SM and keep the fastest;
+ * bit 1 (MC_BATCH_GRAPH): capture the whole sequence into a CUDA graph (re-captured when models,
+ * N_s, seeds or the launch configuration change) and replay it.  Each model's spectrum is read
+ * with mc_get_spectrum on its own context; `stats` (may be NULL) gets the totals and the launch
+ * configuration.  State (queues, graph, tuning) is kept by ctxs[0].  Errors: INVALID_ARG, SIZE
+ * (more than 64 models), STATE, QUEUE_OVERFLOW, TIMEOUT (grid barrier), OOM, CUDA. */
+#define MC_BATCH_AUTOTUNE 1
+#define MC_BATCH_GRAPH 2
+int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint64_t *seeds, int flags, void *stream,
+                 mc_run_stats *stats);
 
 /* Releases the context and all its device memory.  NULL is a no-op. */
 void mc_free(mc_ctx *c);

@@ -146,6 +146,7 @@ struct or_params {
   double bias_p0;              // bias parameter (meaning set by bias_mode)
   double lnu_lo, lnu_hi;       // spectrum range, log10(nu / Hz)
   double roulette_w, roulette_p;
+  double bias_max;             // upper bound on b (reading: any b >= 1 keeps the estimate unbiased)
   int64_t max_steps;
   int32_t n_nu;                // weight-table nodes
   int32_t verlet_maxit;
@@ -879,7 +880,7 @@ double bias_of(const or_params &P, double thetae, int nsc) {
   if (P.bias_mode == 1) b = P.bias_p0 * (nsc + 1.0) * (nsc + 1.0);
   else if (P.bias_mode == 2) b = P.bias_p0 * thetae * thetae;
   else b = P.bias_p0;
-  return std::max(1.0, b);
+  return std::max(1.0, std::min(b, P.bias_max));
 }
 
 // ---------------------------------------------------------------- transport (sections 2.4-2.7, 3)

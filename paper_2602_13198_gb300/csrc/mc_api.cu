@@ -119,6 +119,7 @@ DevModel make_model(const mc_ctx *c) {
   m.r_capture = (p.mass > 0.0) ? m.r_h * (1.0 + p.dh) : -1.0;
   m.bias_mode = p.bias_mode;
   m.bias_p0 = p.bias_p0;
+  m.bias_max = p.bias_max;
   m.n_sc_max = p.n_sc_max;
   m.scatter = p.scatter;
   m.k2_mode = p.k2_mode;
@@ -154,6 +155,7 @@ DevModel make_model(const mc_ctx *c) {
   m.zgmax = c->zgmax;
   m.lnw = c->lnw;
   m.winv = c->winv;
+  m.spec = c->spec;
   return m;
 }
 
@@ -172,6 +174,7 @@ static int check_params(const mc_model_params *p, std::string &why) {
   if (p->n_bins < 1 || p->n_incl < 1 || !(p->lnu_hi > p->lnu_lo)) return bad("bad spectrum bins");
   if (p->n_incl * (int64_t)p->n_bins > (1 << 24)) return bad("too many spectrum bins");
   if (p->bias_mode < 0 || p->bias_mode > 2) return bad("bias_mode must be 0, 1 or 2");
+  if (!(p->bias_max >= 1.0)) return bad("bias_max must be >= 1");
   if (p->n_sc_max < 0 || p->n_sc_max > 1000) return bad("n_sc_max out of range");
   if (!(p->roulette_p > 0.0 && p->roulette_p <= 1.0) || !(p->roulette_w >= 0.0)) return bad("bad roulette");
   if (p->max_steps < 1 || p->max_steps > 2000000000LL) return bad("max_steps out of range");
@@ -194,6 +197,7 @@ void mc_free(mc_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->p.device);
   cudaDeviceSynchronize();
+  mc_batch_release(c);
   std::vector<void *> a = c->allocs;
   for (void *ptr : a) dev_free(c, ptr);
   if (c->cnt_host) cudaFreeHost(c->cnt_host);
@@ -318,6 +322,7 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   if (staging) dev_free(c, staging);
   if (bad) return fail(c, MC_ERR_NAN_INPUT, "grid primitives contain non-finite values");
   c->have_grid = true;
+  c->grid_epoch++;
   return MC_OK;
 }
 
@@ -328,7 +333,8 @@ static void free_childbuf(mc_ctx *c, ChildBuf &q) {
 }
 
 // Child queues (two generations, ping-pong), the superphoton pool and the two phase lists, all
-// sized for `cap` superphotons.
+// sized for `cap` superphotons: 2 x 88 B of queue, 168 B of pool and 8 B of lists per slot.
+static const double kQueueSlotBytes = 352.0;
 static int ensure_queues(mc_ctx *c, int64_t cap) {
   if (cap <= c->qcap) return MC_OK;
   for (int b = 0; b < 2; ++b) free_childbuf(c, c->q[b]);
@@ -376,19 +382,26 @@ static int ensure_queues(mc_ctx *c, int64_t cap) {
   return MC_OK;
 }
 
-// Weights, counts and scan for (N_s, seed); leaves the job's primary total in c->last_total.
-static int generate(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st) {
+// Enqueues weights, zone counts and scan for (N_s, seed) on st without any host synchronisation
+// (usable under stream capture); the job's primary total ends up in c->total_dev.
+int generate_async(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st) {
   DevModel m = make_model(c);
   m.seed = seed;
-  CU(cudaEventRecord(c->ev[2], st));
-  CU(cudaMemsetAsync(c->bad, 0, sizeof(int), st));
+  cudaError_t e = cudaMemsetAsync(c->bad, 0, sizeof(int), st);
+  if (e != cudaSuccess) return (int)e;
   launch_zone_prep(m, c->zvol, c->zpref, c->zlnuc, c->bad, st);
   launch_weights(m, c->zvol, c->zpref, c->zlnuc, c->partial, c->nchunks, n_s, c->p.w_min, c->lnw, c->winv, st);
-  m = make_model(c);
-  m.seed = seed;
   launch_counts(m, c->zvol, c->zpref, c->zlnuc, c->zgmax, c->znbar, c->counts, st);
   launch_scan(c->counts, c->start, c->bsum, c->nz, c->total_dev, st);
-  CU(cudaGetLastError());
+  c->last_seed = seed;
+  c->last_ns = n_s;
+  return (int)cudaGetLastError();
+}
+
+// Weights, counts and scan for (N_s, seed); leaves the job's primary total in c->last_total.
+static int generate(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st) {
+  CU(cudaEventRecord(c->ev[2], st));
+  CU((cudaError_t)generate_async(c, n_s, seed, st));
   CU(cudaEventRecord(c->ev[3], st));
   CU(cudaMemcpyAsync(c->cnt_host + CNT_N, c->total_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CU(cudaMemcpyAsync(c->cnt_host + CNT_N + 1, c->bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -573,13 +586,28 @@ int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards
   int64_t T = c->last_total;
   int64_t u0 = (int64_t)((__int128)T * shard / n_shards), u1 = (int64_t)((__int128)T * (shard + 1) / n_shards);
   size_t nspec = (size_t)c->p.n_incl * c->p.n_bins * 3;
-  CU(cudaMemsetAsync(c->spec, 0, sizeof(double) * nspec, st));
-  CU(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
-  c->t_transport = 0.0;
-  c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0.0;
-  c->n_launch = 0;
-  rc = transport(c, u0, u1, nullptr, 0, nullptr, 0, seed, st);
+  // A scattered generation that outgrows the queues is rerun from the start with larger queues:
+  // every superphoton draws from its own counter-based stream, so the rerun gives the same result.
+  for (int attempt = 0;; ++attempt) {
+    CU(cudaMemsetAsync(c->spec, 0, sizeof(double) * nspec, st));
+    CU(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * CNT_N, st));
+    c->t_transport = 0.0;
+    c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0.0;
+    c->n_launch = 0;
+    rc = transport(c, u0, u1, nullptr, 0, nullptr, 0, seed, st);
+    if (rc != MC_ERR_QUEUE_OVERFLOW || attempt == 3) break;
+    int64_t need = (int64_t)c->cnt_host[CNT_OUT];   // slots the overflowing generation asked for
+    int64_t want = std::max<int64_t>(need + need / 2, 2 * c->qcap);
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    if ((double)want * kQueueSlotBytes > 0.9 * ((double)free_b + (double)c->qcap * kQueueSlotBytes)) break;
+    rc = ensure_queues(c, want);
+    if (rc) return rc;
+  }
   if (rc) return rc;
+  // final counters (also when the shard had no superphoton and nothing was launched)
+  CU(cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
   c->have_run = true;
   fill_stats(c, stats);
   return MC_OK;

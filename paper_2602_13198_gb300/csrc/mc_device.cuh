@@ -45,7 +45,7 @@ struct DevModel {
   // transport
   double eps_geo, verlet_tol, r_record, r_capture;
   int verlet_maxit, bias_mode, n_sc_max, scatter, k2_mode;
-  double bias_p0, roulette_w, roulette_p;
+  double bias_p0, bias_max, roulette_w, roulette_p;
   int64_t max_steps;
   // record
   double lnu_lo, dlog_bin;
@@ -70,6 +70,7 @@ struct DevModel {
   const double *lnw;      // ln w_j (n_nu)
   const double *winv;     // 1 / w_j (n_nu)
   uint64_t seed;
+  double *spec;           // spectrum sums [n_incl][n_bins][3] of this model
 };
 
 // ---------------------------------------------------------------- Philox4x32-10 (Salmon et al. 2011)
@@ -644,7 +645,7 @@ __device__ __forceinline__ double bias_of(const DevModel &m, double thetae, int 
   if (m.bias_mode == 1) b = m.bias_p0 * (nsc + 1.0) * (nsc + 1.0);
   else if (m.bias_mode == 2) b = m.bias_p0 * thetae * thetae;
   else b = m.bias_p0;
-  return fmax(1.0, b);
+  return fmax(1.0, fmin(b, m.bias_max));
 }
 
 // ---------------------------------------------------------------- tetrads (sections 2.1, 2.7)

@@ -19,6 +19,7 @@ struct ChildBuf {
   uint64_t *id;
   uint32_t *ctr;
   int32_t *nsc;
+  int16_t *model;   // model index (batched runs only; NULL otherwise)
 };
 
 // Superphoton state between transport phases (structure of arrays, one slot per superphoton
@@ -29,6 +30,7 @@ struct Pool {
   uint64_t *id;
   uint32_t *ctr, *nev;
   int32_t *nsc, *nsteps;
+  int16_t *model;   // model index (batched runs only; NULL otherwise)
 };
 
 // Counters written by the transport kernels (unsigned 64-bit for atomics).
@@ -111,6 +113,7 @@ struct mc_ctx {
   int nF = 0, nK2 = 0;
   // grid
   bool have_grid = false;
+  uint64_t grid_epoch = 0;   // bumped by every mc_set_grid (captured batch graphs hold grid pointers)
   void *prim = nullptr;
   int prim_f32 = 0;
   int n1 = 0, n2 = 0, n3 = 0;
@@ -145,6 +148,8 @@ struct mc_ctx {
   float *sur_bias = nullptr;
   unsigned int *sur_err = nullptr;     // tensor-core wait timeouts
   bool sur_ready = false;
+  // batched runs led by this context (mc_batch.cu)
+  void *batch = nullptr;
 };
 
 // Tensor-core view of the context's trained network (mc_mlp.cu).
@@ -155,4 +160,6 @@ mcgb::DevModel make_model(const mc_ctx *c);
 void *dev_alloc_ext(mc_ctx *c, size_t bytes);
 void dev_free_ext(mc_ctx *c, void *ptr);
 int set_err(mc_ctx *c, int code, const char *msg);
+extern "C" int generate_async(mc_ctx *c, double n_s, uint64_t seed, cudaStream_t st);
+void mc_batch_release(mc_ctx *c);
 

@@ -1,0 +1,607 @@
+// mc_push.cuh -- per-superphoton transport arithmetic shared by the transport kernels
+// (mc_transport.cu) and the batched persistent kernel (mc_batch.cu): state, emission (section 2.3),
+// initialisation, the in-grid step (sections 2.4-2.7), the free-streaming step, recording and the
+// Compton child (section 2.7), and the surrogate-split in-grid step.
+#pragma once
+#include "mc_internal.h"
+
+namespace mcgb {
+
+
+struct Ph {
+  double X[4], K[4], A[4];
+  double w, wb, ana, ans, acc, x1t;
+  Rng s;
+  int nsc;
+  uint32_t nev;
+  int nsteps;
+  int model;   // index of the superphoton's model in a batched run (0 otherwise)
+};
+
+struct LocalStats {
+  unsigned long long emit, child, rec, abs, capt, maxst, steps, iters, nonconv, roul, rejcap, events, gsteps, giters;
+};
+
+template <bool MIXED>
+__device__ __forceinline__ void coefs(const DevModel &m, const Geo &G, const double X[4], const double K[4], bool ws,
+                                      Coef &c) {
+  if (MIXED) coefficients32(m, G, X, K, ws, c);
+  else coefficients64(m, G, X, K, ws, c);
+}
+
+template <bool MIXED>
+static __device__ void init_transport(const DevModel &m, Ph &p) {
+  p.x1t = -log(rng_u(p.s, m.seed));
+  p.acc = 0.0;
+  bool scat = m.scatter && p.nsc < m.n_sc_max;
+  Geo G;
+  metric_eval<true>(m, p.X[1], p.X[2], G);
+  Coef c;
+  coefs<MIXED>(m, G, p.X, p.K, scat, c);
+  p.ana = c.ana;
+  p.ans = c.ans;
+  accel(G, p.K, p.A);
+  p.nsteps = 0;
+  p.nev = 0;
+  p.wb = p.w;
+}
+
+// Emission of primary uid (section 2.3) at the centre of its zone.
+static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &ls) {
+  int64_t lo = 0, hi = m.nz - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(m.start + mid) <= uid) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t z = lo;
+  rng_init(p.s, (uint64_t)uid, 0u);
+  const double pref = m.zpref[z], lnuc = m.zlnuc[z], gm = m.zgmax[z];
+  double lnu = m.lnu_min;
+  int it;
+  for (it = 0; it < 100000; ++it) {
+    double r1 = rng_u(p.s, m.seed);
+    lnu = m.lnu_min + r1 * m.dlntot;
+    double fj = (lnu - m.lnu_min) / m.dlnu;
+    int j = min(max((int)floor(fj), 0), m.n_nu - 2);
+    double fr = fj - j;
+    double g0 = pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc) * m.winv[j];
+    double g1 = pref * F_of_lnK(m, m.lnu_min + (j + 1) * m.dlnu - lnuc) * m.winv[j + 1];
+    double gv = (1.0 - fr) * g0 + fr * g1;
+    double r2 = rng_u(p.s, m.seed);
+    if (r2 * gm < gv) break;
+  }
+  if (it == 100000) ls.rejcap++;
+  // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
+  double K0 = exp(lnu - lnuc);
+  double jmax = Gsyn(K0);
+  double cth = 0.0;
+  for (it = 0; it < 100000; ++it) {
+    double r3 = rng_u(p.s, m.seed);
+    cth = 2.0 * r3 - 1.0;
+    double r4 = rng_u(p.s, m.seed);
+    double sth = sqrt(1.0 - cth * cth);
+    if (r4 * jmax < sth * Gsyn(K0 / sth)) break;
+  }
+  if (it == 100000) ls.rejcap++;
+  double phi = 2.0 * rng_u(p.s, m.seed);   // units of pi
+  double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+  double eps = exp(lnu) * (kHPL / (kME * kCL * kCL));
+  // plasma at the zone centre
+  int64_t iz = z / ((int64_t)m.n2 * m.n3), jz = (z / m.n3) % m.n2, kz = z % m.n3;
+  double X[4] = {0.0, m.x1_0 + (iz + 0.5) * m.dx1, m.x2_0 + (jz + 0.5) * m.dx2, m.x3_0 + (kz + 0.5) * m.dx3};
+  Geo G;
+  metric_eval<false>(m, X[1], X[2], G);
+  double pr[8];
+  if (m.prim_f32) {
+    for (int f = 0; f < 8; ++f) pr[f] = (double)m.prim32[z * 8 + f];
+  } else {
+    for (int f = 0; f < 8; ++f) pr[f] = m.prim64[z * 8 + f];
+  }
+  Plasma<double> P;
+  double ucon[4], bcon[4];
+  plasma_from_prims<double>(m, G, pr, P, ucon, bcon);
+  double e[4][4];
+  tetrad_emission(G, ucon, bcon, P.bsq, e);
+  double sp, cp;
+  sincospi(phi, &sp, &cp);
+  double kf[4] = {eps, eps * sth * cp, eps * sth * sp, eps * cth};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.X[q] = X[q];
+    p.K[q] = kf[0] * e[0][q] + kf[1] * e[1][q] + kf[2] * e[2][q] + kf[3] * e[3][q];
+  }
+  double fj = (lnu - m.lnu_min) / m.dlnu;
+  int j = min(max((int)floor(fj), 0), m.n_nu - 2);
+  double fr = fj - j;
+  p.w = exp((1.0 - fr) * m.lnw[j] + fr * m.lnw[j + 1]);
+  p.nsc = 0;
+}
+
+// Compton event at Xe with pre-event wavevector Ke (section 2.7): child in the plasma frame of the
+// event point (radial lookup clamped to the grid), written to the next generation's queue.
+static __device__ void scatter_child(const DevModel &m, const PushIO &io, const double Xe[4], const double Ke[4], double wc,
+                              uint64_t cid, int nsc, int model, LocalStats &ls) {
+  Geo G;
+  metric_eval<false>(m, Xe[1], Xe[2], G);
+  double Xc[4] = {Xe[0], fmin(fmax(Xe[1], m.x1_0), m.x1_hi), Xe[2], Xe[3]};
+  double pr[8];
+  interp_prims<double>(m, Xc, pr);
+  Plasma<double> P;
+  double ucon[4];
+  plasma_from_prims<double>(m, G, pr, P, ucon, nullptr);
+  double e[4][4];
+  tetrad_scatter(G, ucon, e);
+  double kc[4];
+  lower(G, Ke, kc);
+  double kf[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    double d = e[a][0] * kc[0] + e[a][1] * kc[1] + e[a][2] * kc[2] + e[a][3] * kc[3];
+    kf[a] = (a == 0) ? -d : d;
+  }
+  double eps = kf[0];
+  double il = 1.0 / sqrt(kf[1] * kf[1] + kf[2] * kf[2] + kf[3] * kf[3]);
+  double n[3] = {kf[1] * il, kf[2] * il, kf[3] * il};
+  Rng s;
+  rng_init(s, cid, 0u);
+  double eo, dir[3];
+  int rej = 0;
+  compton_fluid(fmax(P.thetae, 1e-8), eps, n, s, m.seed, eo, dir, rej);
+  ls.rejcap += rej;
+  unsigned long long slot = atomicAdd(io.cnt + CNT_OUT, 1ull);
+  ls.child++;
+  if ((int64_t)slot >= io.out_cap) {
+    atomicOr(io.cnt + CNT_ERR, 1ull);
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    io.out.X[q][slot] = Xe[q];
+    io.out.K[q][slot] = eo * e[0][q] + dir[0] * e[1][q] + dir[1] * e[2][q] + dir[2] * e[3][q];
+  }
+  io.out.w[slot] = wc;
+  io.out.id[slot] = cid;
+  io.out.ctr[slot] = s.n;
+  io.out.nsc[slot] = nsc;
+  if (io.out.model) io.out.model[slot] = (int16_t)model;
+}
+
+__device__ __forceinline__ bool in_grid(const DevModel &m, const double X[4]) {
+  return X[1] >= m.x1_0 && X[1] <= m.x1_hi;
+}
+
+static __device__ void record(const DevModel &m, const PushIO &io, const Geo &G, const Ph &p) {
+  double E = -(G.g00 * p.K[0] + G.g01 * p.K[1] + G.g03 * p.K[3]);
+  if (!(E > 0.0)) return;
+  double nu = E * (kME * kCL * kCL / kHPL);
+  double l = log10(nu);
+  int ib = (int)floor((l - m.lnu_lo) / m.dlog_bin);
+  if (ib < 0 || ib >= m.n_bins) return;
+  double thf = acos(fabs(G.cth));
+  int ii = (int)floor(thf / (0.5 * kPI) * m.n_incl);
+  ii = min(max(ii, 0), m.n_incl - 1);
+  double we = p.w * E;
+  double *sp = m.spec + ((int64_t)ii * m.n_bins + ib) * 3;
+  atomicAdd(sp, we);
+  atomicAdd(sp + 1, we * we);
+  atomicAdd(sp + 2, 1.0);
+}
+
+static __device__ void write_log(const PushIO &io, const Ph &p, int status) {
+  if (!io.log) return;
+  unsigned long long slot = atomicAdd(io.cnt + CNT_LOG, 1ull);
+  if ((int64_t)slot >= io.log_cap) {
+    atomicOr(io.cnt + CNT_ERR, 2ull);
+    return;
+  }
+  mc_log_rec &L = io.log[slot];
+  L.id = p.s.id;
+  L.gen = p.nsc;
+  L.status = status;
+  for (int q = 0; q < 4; ++q) {
+    L.X[q] = p.X[q];
+    L.K[q] = p.K[q];
+  }
+  L.w = p.w;
+  L.nsteps = p.nsteps;
+  L.nev = (int32_t)p.nev;
+  L.pad = 0;
+}
+
+// One geodesic step with absorption, scattering and the termination tests; false when finished.
+template <bool MIXED>
+static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
+  const bool scat = m.scatter && p.nsc < m.n_sc_max;
+  double dl = stepsize(m, p.X, p.K);
+  double X0[4], K0[4], Kp[4], An[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    X0[q] = p.X[q];
+    K0[q] = p.K[q];
+    p.X[q] = X0[q] + K0[q] * dl + 0.5 * p.A[q] * dl * dl;
+    Kp[q] = K0[q] + p.A[q] * dl;
+  }
+  Geo G;
+  metric_eval<true>(m, p.X[1], p.X[2], G);
+  int it = 0;
+  bool conv = false;
+  double Kn[4];
+  while (true) {
+    accel(G, Kp, An);
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Kn[q] = K0[q] + 0.5 * (p.A[q] + An[q]) * dl;
+      num += fabs(Kn[q] - Kp[q]);
+      den += fabs(Kn[q]);
+    }
+    ++it;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
+    if (num < m.verlet_tol * den) {
+      conv = true;
+      break;
+    }
+    if (it >= m.verlet_maxit) break;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.K[q] = Kn[q];
+    p.A[q] = An[q];
+  }
+  ls.iters += it;
+  ls.giters += it;
+  ls.gsteps++;
+  if (!conv) ls.nonconv++;
+  p.nsteps++;
+  ls.steps++;
+  Coef c;
+  coefs<MIXED>(m, G, p.X, p.K, scat, c);
+  const double C = m.Ccoef;
+  double tau_a = 0.5 * (p.ana + c.ana) * C * dl;
+  double w0 = p.w;
+  double wn = w0 * exp(-tau_a);
+  if (scat) {
+    double tau_s = 0.5 * (p.ans + c.ans) * C * dl;
+    if (tau_s > 0.0) {
+      double b = bias_of(m, c.thetae, p.nsc);
+      double d = b * tau_s;
+      if (p.acc + d > p.x1t) {
+        double f = (p.x1t - p.acc) / d;
+        double Xe[4], Ke[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Xe[q] = X0[q] + f * (p.X[q] - X0[q]);
+          Ke[q] = K0[q] + f * (p.K[q] - K0[q]);
+        }
+        double we = w0 * exp(-f * tau_a);
+        uint64_t cid = child_id(p.s.id, p.nev);
+        scatter_child(m, io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
+        p.nev++;
+        ls.events++;
+        wn *= (1.0 - 1.0 / b);
+        p.acc = 0.0;
+        p.x1t = -log(rng_u(p.s, m.seed));
+      } else {
+        p.acc += d;
+      }
+    }
+  }
+  p.w = wn;
+  p.ana = c.ana;
+  p.ans = c.ans;
+  const double r = G.r;
+  int status = 0;
+  if (r >= m.r_record) {
+    record(m, io, G, p);
+    status = 1;
+    ls.rec++;
+  } else if (r <= m.r_capture) {
+    status = 3;
+    ls.capt++;
+  } else if (!(p.w > 0.0)) {
+    status = 2;
+    ls.abs++;
+  } else {
+    if (p.w < m.roulette_w * p.wb) {
+      if (rng_u(p.s, m.seed) < m.roulette_p) {
+        p.w /= m.roulette_p;
+        ls.roul++;
+      } else {
+        status = 2;
+        ls.abs++;
+      }
+    }
+    if (status == 0 && p.nsteps >= m.max_steps) {
+      status = 4;
+      ls.maxst++;
+    }
+  }
+  if (status) {
+    write_log(io, p, status);
+    return false;
+  }
+  return true;
+}
+
+// Free-streaming step (both end points outside the grid: no plasma, so tau_a = tau_s = 0 and the
+// weight is unchanged): the same Verlet arithmetic and termination tests as step().  If the new
+// point lies inside the grid the step is discarded (state untouched) and 2 is returned, so the
+// in-grid phase redoes it with the coefficients.  Returns 0 to continue, 1 when finished.
+static __device__ int step_free(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
+  double dl = stepsize(m, p.X, p.K);
+  double Xn[4], Kp[4], An[4], Kn[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Xn[q] = p.X[q] + p.K[q] * dl + 0.5 * p.A[q] * dl * dl;
+    Kp[q] = p.K[q] + p.A[q] * dl;
+  }
+  if (in_grid(m, Xn)) return 2;
+  Geo G;
+  metric_eval<true>(m, Xn[1], Xn[2], G);
+  int it = 0;
+  bool conv = false;
+  while (true) {
+    accel(G, Kp, An);
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Kn[q] = p.K[q] + 0.5 * (p.A[q] + An[q]) * dl;
+      num += fabs(Kn[q] - Kp[q]);
+      den += fabs(Kn[q]);
+    }
+    ++it;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
+    if (num < m.verlet_tol * den) {
+      conv = true;
+      break;
+    }
+    if (it >= m.verlet_maxit) break;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.X[q] = Xn[q];
+    p.K[q] = Kn[q];
+    p.A[q] = An[q];
+  }
+  ls.iters += it;
+  if (!conv) ls.nonconv++;
+  p.nsteps++;
+  ls.steps++;
+  p.ana = 0.0;
+  p.ans = 0.0;
+  const double r = G.r;
+  int status = 0;
+  if (r >= m.r_record) {
+    record(m, io, G, p);
+    status = 1;
+    ls.rec++;
+  } else if (r <= m.r_capture) {
+    status = 3;
+    ls.capt++;
+  } else if (!(p.w > 0.0)) {
+    status = 2;
+    ls.abs++;
+  } else {
+    if (p.w < m.roulette_w * p.wb) {
+      if (rng_u(p.s, m.seed) < m.roulette_p) {
+        p.w /= m.roulette_p;
+        ls.roul++;
+      } else {
+        status = 2;
+        ls.abs++;
+      }
+    }
+    if (status == 0 && p.nsteps >= m.max_steps) {
+      status = 4;
+      ls.maxst++;
+    }
+  }
+  if (status) {
+    write_log(io, p, status);
+    return 1;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void flush_stats(const LocalStats &ls, unsigned long long *cnt) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long v[14] = {ls.emit, ls.child, ls.rec, ls.abs, ls.capt, ls.maxst,
+                              ls.steps, ls.iters, ls.nonconv, ls.roul, ls.rejcap, ls.events, ls.gsteps, ls.giters};
+#pragma unroll
+  for (int q = 0; q < 14; ++q) {
+    unsigned long long s = warp_sum(v[q]);
+    if (lane == 0 && s) atomicAdd(cnt + CNT_EMIT + q, s);
+  }
+}
+
+__device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const Ph &p) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    P.X[q][i] = p.X[q];
+    P.K[q][i] = p.K[q];
+    P.A[q][i] = p.A[q];
+  }
+  P.w[i] = p.w;
+  P.wb[i] = p.wb;
+  P.ana[i] = p.ana;
+  P.ans[i] = p.ans;
+  P.acc[i] = p.acc;
+  P.x1t[i] = p.x1t;
+  P.id[i] = p.s.id;
+  P.ctr[i] = p.s.n;
+  P.nev[i] = p.nev;
+  P.nsc[i] = p.nsc;
+  P.nsteps[i] = p.nsteps;
+  if (P.model) P.model[i] = (int16_t)p.model;
+}
+
+__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, Ph &p) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.X[q] = P.X[q][i];
+    p.K[q] = P.K[q][i];
+    p.A[q] = P.A[q][i];
+  }
+  p.w = P.w[i];
+  p.wb = P.wb[i];
+  p.ana = P.ana[i];
+  p.ans = P.ans[i];
+  p.acc = P.acc[i];
+  p.x1t = P.x1t[i];
+  rng_init(p.s, P.id[i], P.ctr[i]);
+  p.nev = P.nev[i];
+  p.nsc = P.nsc[i];
+  p.nsteps = P.nsteps[i];
+  p.model = P.model ? (int)P.model[i] : 0;
+}
+
+// ---------------------------------------------------------------- surrogate in-grid push
+// The mixed-precision in-grid step with the coefficient network: part A (geodesic, plasma state,
+// network inputs), one tensor-core evaluation for the CTA's 128 superphotons, part B (optical
+// depths, scattering, termination).  Identical to step<true> except for where K2 and sigma_h
+// come from.
+struct SurCarry {
+  double X0[4], K0[4], dl;
+  double r, cth, g00, g01, g03;
+  CoefA a;
+};
+
+static __device__ void step_sur_a(const DevModel &m, Ph &p, SurCarry &sc, LocalStats &ls) {
+  double dl = stepsize(m, p.X, p.K);
+  double Kp[4], An[4], Kn[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    sc.X0[q] = p.X[q];
+    sc.K0[q] = p.K[q];
+    p.X[q] = sc.X0[q] + sc.K0[q] * dl + 0.5 * p.A[q] * dl * dl;
+    Kp[q] = sc.K0[q] + p.A[q] * dl;
+  }
+  Geo G;
+  metric_eval<true>(m, p.X[1], p.X[2], G);
+  int it = 0;
+  bool conv = false;
+  while (true) {
+    accel(G, Kp, An);
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      Kn[q] = sc.K0[q] + 0.5 * (p.A[q] + An[q]) * dl;
+      num += fabs(Kn[q] - Kp[q]);
+      den += fabs(Kn[q]);
+    }
+    ++it;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
+    if (num < m.verlet_tol * den) {
+      conv = true;
+      break;
+    }
+    if (it >= m.verlet_maxit) break;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p.K[q] = Kn[q];
+    p.A[q] = An[q];
+  }
+  ls.iters += it;
+  ls.giters += it;
+  ls.gsteps++;
+  if (!conv) ls.nonconv++;
+  p.nsteps++;
+  ls.steps++;
+  sc.dl = dl;
+  sc.r = G.r;
+  sc.cth = G.cth;
+  sc.g00 = G.g00;
+  sc.g01 = G.g01;
+  sc.g03 = G.g03;
+  coefficients32_a(m, G, p.X, p.K, sc.a);
+}
+
+static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, Ph &p, const SurCarry &sc, const float out[3],
+                           LocalStats &ls) {
+  const bool scat = m.scatter && p.nsc < m.n_sc_max;
+  Coef c;
+  coefficients32_b(m, sc.a, out, scat, c);
+  const double C = m.Ccoef, dl = sc.dl;
+  double tau_a = 0.5 * (p.ana + c.ana) * C * dl;
+  double w0 = p.w;
+  double wn = w0 * exp(-tau_a);
+  if (scat) {
+    double tau_s = 0.5 * (p.ans + c.ans) * C * dl;
+    if (tau_s > 0.0) {
+      double b = bias_of(m, c.thetae, p.nsc);
+      double d = b * tau_s;
+      if (p.acc + d > p.x1t) {
+        double f = (p.x1t - p.acc) / d;
+        double Xe[4], Ke[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Xe[q] = sc.X0[q] + f * (p.X[q] - sc.X0[q]);
+          Ke[q] = sc.K0[q] + f * (p.K[q] - sc.K0[q]);
+        }
+        double we = w0 * exp(-f * tau_a);
+        uint64_t cid = child_id(p.s.id, p.nev);
+        scatter_child(m, io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
+        p.nev++;
+        ls.events++;
+        wn *= (1.0 - 1.0 / b);
+        p.acc = 0.0;
+        p.x1t = -log(rng_u(p.s, m.seed));
+      } else {
+        p.acc += d;
+      }
+    }
+  }
+  p.w = wn;
+  p.ana = c.ana;
+  p.ans = c.ans;
+  const double r = sc.r;
+  int status = 0;
+  if (r >= m.r_record) {
+    Geo G;
+    G.g00 = sc.g00;
+    G.g01 = sc.g01;
+    G.g03 = sc.g03;
+    G.cth = sc.cth;
+    record(m, io, G, p);
+    status = 1;
+    ls.rec++;
+  } else if (r <= m.r_capture) {
+    status = 3;
+    ls.capt++;
+  } else if (!(p.w > 0.0)) {
+    status = 2;
+    ls.abs++;
+  } else {
+    if (p.w < m.roulette_w * p.wb) {
+      if (rng_u(p.s, m.seed) < m.roulette_p) {
+        p.w /= m.roulette_p;
+        ls.roul++;
+      } else {
+        status = 2;
+        ls.abs++;
+      }
+    }
+    if (status == 0 && p.nsteps >= m.max_steps) {
+      status = 4;
+      ls.maxst++;
+    }
+  }
+  if (status) {
+    write_log(io, p, status);
+    return false;
+  }
+  return true;
+}
+
+}  // namespace mcgb

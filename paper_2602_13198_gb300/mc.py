@@ -39,7 +39,7 @@ class ModelParams(C.Structure):
         ("nu_min", C.c_double), ("nu_max", C.c_double), ("w_min", C.c_double), ("n_s", C.c_double),
         ("eps_geo", C.c_double), ("verlet_tol", C.c_double), ("r_record", C.c_double), ("dh", C.c_double),
         ("bias_p0", C.c_double), ("lnu_lo", C.c_double), ("lnu_hi", C.c_double),
-        ("roulette_w", C.c_double), ("roulette_p", C.c_double),
+        ("roulette_w", C.c_double), ("roulette_p", C.c_double), ("bias_max", C.c_double),
         ("max_steps", C.c_int64),
         ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32), ("n_sc_max", C.c_int32),
         ("n_bins", C.c_int32), ("n_incl", C.c_int32), ("k2_mode", C.c_int32), ("scatter", C.c_int32),
@@ -65,13 +65,16 @@ INT_STATS = ("n_emit", "n_child", "n_rec", "n_abs", "n_capt", "n_maxst", "n_step
 class RunStats(C.Structure):
     _fields_ = ([(n, C.c_int64) for n in INT_STATS] + [("transport_ms", C.c_double), ("generate_ms", C.c_double)] +
                 [("n_steps_grid", C.c_int64), ("n_iters_grid", C.c_int64)] +
-                [("init_ms", C.c_double), ("grid_ms", C.c_double), ("free_ms", C.c_double)])
+                [("init_ms", C.c_double), ("grid_ms", C.c_double), ("free_ms", C.c_double)] +
+                [("batch_min_blocks", C.c_int32), ("batch_ctas", C.c_int32), ("batch_graph", C.c_int32),
+                 ("pad0", C.c_int32)])
 
     def as_dict(self):
         d = {}
         for n, t in self._fields_:
             v = getattr(self, n)
-            d[n] = float(v) if t is C.c_double else int(v)
+            if n != "pad0":
+                d[n] = float(v) if t is C.c_double else int(v)
         return d
 
 
@@ -105,6 +108,8 @@ def lib():
         L.mc_version.restype = C.c_char_p
         L.mc_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
         L.mc_fma_peak.restype = C.c_int
+        L.mc_run_batch.argtypes = [C.POINTER(vp), C.c_int, dp, C.POINTER(u64), C.c_int, vp, C.POINTER(RunStats)]
+        L.mc_run_batch.restype = C.c_int
         L.mc_zone_counts_noalloc.argtypes = [vp, C.c_double, u64, vp, vp, vp, vp]
         L.mc_zone_counts_noalloc.restype = C.c_int
         fp = C.POINTER(C.c_float)
@@ -294,6 +299,21 @@ class Model:
         self._check(lib().mc_trace(self._h, float(n_s), int(seed), u.ctypes.data_as(C.POINTER(C.c_int64)), len(u),
                                    out.ctypes.data, cap, C.byref(n), s))
         return out[: n.value].copy()
+
+
+def run_batch(models, n_s, seeds, autotune=True, graph=True, stream=None) -> dict:
+    """Runs several models in one persistent launch (mc_run_batch); spectra are read per model."""
+    n = len(models)
+    hs = (C.c_void_p * n)(*[m._h.value for m in models])
+    ns = (C.c_double * n)(*[float(x) for x in n_s])
+    sd = (C.c_uint64 * n)(*[int(x) for x in seeds])
+    flags = (1 if autotune else 0) | (2 if graph else 0)
+    st = RunStats()
+    s = C.c_void_p(getattr(stream, "cuda_stream", 0) or 0) if stream is not None else C.c_void_p(0)
+    rc = lib().mc_run_batch(hs, n, ns, sd, flags, s, C.byref(st))
+    if rc != MC_OK:
+        raise MCError(rc, lib().mc_last_error(models[0]._h).decode())
+    return st.as_dict()
 
 
 def fma_peak(device: int = 0, fp64: bool = True) -> float:

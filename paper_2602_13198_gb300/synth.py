@@ -43,7 +43,7 @@ def base_params(**over) -> dict:
         eps_geo=0.04, verlet_tol=1e-3,
         r_record=1000.0, dh=0.05, bias_p0=1.0,
         lnu_lo=8.0, lnu_hi=24.0,
-        roulette_w=1e-12, roulette_p=0.1,
+        roulette_w=1e-12, roulette_p=0.1, bias_max=1e300,
         max_steps=20000,
         n_nu=200, verlet_maxit=16, bias_mode=0, n_sc_max=4,
         n_bins=200, n_incl=1, k2_mode=0, scatter=0,
@@ -197,12 +197,22 @@ def _fm_torus(r, th, a, r_in, r_max, gam):
     h = np.exp(np.where(inside, lnh, 0.0))
     # polytrope p = kappa rho^gam: p/rho = (h - 1)(gam - 1)/gam; density normalised to max 1
     rho = np.where(inside, ((h - 1) * (gam - 1) / gam) ** (1 / (gam - 1)), 0.0)
+    if not rho.max() > 0:
+        raise ValueError("no Fishbone-Moncrief torus for a=%g, r_in=%g, r_max=%g on this grid" % (a, r_in, r_max))
     rho = rho / rho.max()
     u = np.where(inside, (h - 1) / gam * rho, 0.0)   # u = p / (gam - 1)
     return rho, u, np.where(inside, om, 0.0), np.where(inside, ut, 0.0), inside
 
 
-def torus(*, a=0.9375, n1=256, n2=128, n3=1, r_out=40.0, hslope=0.3, r_in=6.0, r_max=12.0, beta_min=100.0,
+def r_isco(a):
+    """Innermost stable circular orbit (Bardeen, Press & Teukolsky 1972), prograde for a > 0,
+    retrograde for a < 0 (M = 1)."""
+    z1 = 1 + (1 - a * a) ** (1 / 3) * ((1 + a) ** (1 / 3) + (1 - a) ** (1 / 3))
+    z2 = math.sqrt(3 * a * a + z1 * z1)
+    return 3 + z2 - math.copysign(math.sqrt((3 - z1) * (3 + z1 + 2 * z2)), a if a != 0 else 1.0)
+
+
+def torus(*, a=0.9375, n1=256, n2=128, n3=1, r_out=40.0, hslope=0.3, r_in=None, r_max=None, beta_min=100.0,
           pert=0.1, seed=1, m_bh_msun=4.14e6, M_unit=1e18, R_high=20.0, R_low=1.0, dtype=np.float64,
           turb_sigma=0.0, turb_slope=-11.0 / 3.0, **over):
     """Synthetic GRMHD-like snapshot: Fishbone-Moncrief torus (r_in, r_max) around a Kerr hole in
@@ -213,6 +223,10 @@ def torus(*, a=0.9375, n1=256, n2=128, n3=1, r_out=40.0, hslope=0.3, r_in=6.0, r
     P(k) ~ k^turb_slope (k^-11/3: the 3-D form of a k^-5/3 spectrum) and standard deviation turb_sigma
     multiplies rho and u as exp(delta - sigma^2/2)."""
     gam = GAM
+    if r_in is None:   # r_in = 6, r_max = 12 (section 4.3 stand-in) moved outside the ISCO when needed
+        r_in = max(6.0, math.ceil(r_isco(a)) + 1.0)
+    if r_max is None:
+        r_max = max(12.0, 2.0 * r_in)
     rh = 1.0 + math.sqrt(1.0 - a * a)
     g = _grid(n1, n2, n3, math.log(rh), math.log(r_out))
     X1, X2, X3 = _zone_centres(g)
@@ -278,7 +292,7 @@ def torus(*, a=0.9375, n1=256, n2=128, n3=1, r_out=40.0, hslope=0.3, r_in=6.0, r
     g["prim"] = prim
     params = base_params(a=a, mass=1.0, hslope=hslope, L_unit=length_unit(m_bh_msun), M_unit=M_unit,
                          R_high=R_high, R_low=R_low, w_min=1e20, scatter=1, bias_mode=2, bias_p0=96e4,
-                         n_sc_max=3, dh=0.05)
+                         bias_max=1e5, n_sc_max=3, dh=0.05)
     params.update(over)
     return params, g
 
@@ -293,12 +307,12 @@ def torus3d(**over):
 
 def survey(n_models=64, seed=1):
     """Batched parameter survey: models drawn (seeded) from spin {-0.94,-0.5,0,0.5,0.94} x
-    R_high {1,10,40,160} x accretion-rate scale {0.5,1,2,4} (M_unit x scale), grids 128x64, 192x96 or
+    R_high {1,10,40,160} x accretion-rate scale {0.25,0.5,1,2} (M_unit x scale), grids 128x64, 192x96 or
     256x128, N_s log-uniform in [1e5, 1e7].  Returns a list of (params, grid, N_s)."""
     rng = np.random.default_rng(seed)
     spins = [-0.94, -0.5, 0.0, 0.5, 0.94]
     rhs = [1.0, 10.0, 40.0, 160.0]
-    scales = [0.5, 1.0, 2.0, 4.0]
+    scales = [0.25, 0.5, 1.0, 2.0]
     grids = [(128, 64), (192, 96), (256, 128)]
     out = []
     for i in range(n_models):

@@ -137,6 +137,22 @@ def test_edge_cases_and_errors():
     assert e.value.code == -6          # NAN_INPUT
 
 
+def test_queue_grows_when_a_generation_overflows():
+    # optically thick torus (~30 scattered children per primary): the first scattered generation
+    # outgrows the initial 2^20-slot queue, the run is redone with larger queues, and the result
+    # equals a second run on the already-grown context (streams are keyed per superphoton)
+    p, g = synth.torus(a=0.9375, n1=64, n2=32, R_high=20.0, M_unit=4e18, seed=104)
+    gm = gpu_model(p, g)
+    st1 = gm.run(5e5, 1)
+    s1 = gm.spectrum_sums().copy()
+    assert st1["n_child"] > (1 << 20)
+    st2 = gm.run(5e5, 1)
+    s2 = gm.spectrum_sums().copy()
+    for k in ("n_total", "n_emit", "n_child", "n_rec", "n_abs", "n_capt", "n_steps", "n_events"):
+        assert st1[k] == st2[k], k
+    assert np.array_equal(s1[..., 2], s2[..., 2]) and np.allclose(s1, s2, rtol=1e-10, atol=0)
+
+
 def test_ragged_3d_float32_grid():
     # 3-D grid with ragged sizes in FP32 storage (the layout of the 3-D snapshot workload)
     p, g = synth.sphere("ks", n1=37, n2=19, R=10.0)
