@@ -50,6 +50,10 @@ FLOP_ITER = 110.0
 FLOP_EMIT = 2000.0
 FLOP_EVENT = 1500.0
 GEN_LAUNCHES = 7          # zone prep, weight partials, weight final, counts, 3 scan kernels
+# DRAM bytes (read + write) per superphoton of the first in-grid launch of a job, from one ncu capture
+# of k_push<in-grid> (FP64) at N_s = 1e6, tau_T = 1e-2: 227.2 MB for ~787k superphotons.  Traffic grows
+# in proportion to the superphotons a launch carries.  Must be re-taken whenever that kernel changes.
+TRAFFIC_B_PER_PH_FP64 = 289.0
 
 
 def log(*a):
@@ -125,6 +129,116 @@ def oracle_rate(p, g, seed, budget_s, nthreads, first_n=None):
     return units / dt, units, dt, min(n, tot)
 
 
+SURVEY = ("batched parameter survey: 64 synthetic 2-D Fishbone-Moncrief tori drawn (seed 1) from spin "
+          "{-0.94,-0.5,0,0.5,0.94} x R_high {1,10,40,160} x accretion scale {0.5,1,2,4} (M_unit = 5e17 g x scale), "
+          "grids 128x64 / 192x96 / 256x128, N_s log-uniform in [1e5, 1e7] per model, bias 96e4 Theta_e^2 (<= 1e5)")
+FLOP_SUR_EVAL = 2.0 * (3 * 64 + 64 * 64 + 64 * 3)   # one 3-64-64-3 network evaluation (algorithmic)
+
+
+def spectrum_error(s_new, s_ref, min_count=16):
+    """Error of one spectrum against the plain FP64 spectrum of the same model and seed: relative
+    error of the total luminosity, and the fraction of bins (>= min_count superphotons on both
+    sides) within max(1 %, 3 combined Monte Carlo sigma)."""
+    import numpy as np
+    a, b = s_new[..., 0], s_ref[..., 0]
+    tot = float(b.sum())
+    lum = abs(float(a.sum()) - tot) / tot if tot > 0 else 0.0
+    sig = np.sqrt(s_new[..., 1] + s_ref[..., 1])
+    sel = (s_new[..., 2] >= min_count) & (s_ref[..., 2] >= min_count)
+    ok = np.abs(a - b) <= np.maximum(0.01 * np.abs(b), 3.0 * sig)
+    return lum, int(sel.sum()), int((sel & ok).sum())
+
+
+def survey_forms(args, dev, stream, flush, fp64_peak, bf16_peak):
+    """The metric's second form on the survey workload: the same 64 models and seeds run (1) as plain
+    FP64, one mc_run per model, and (2) batched into one persistent launch (autotuned, replayed from
+    a captured CUDA graph) in mixed precision, with and without the coefficient surrogate.  Each
+    timed pass is preceded by an L2 flush and timed with CUDA events on the launching stream."""
+    import numpy as np
+    import torch
+    from paper_2602_13198_gb300 import mc, synth
+    specs = synth.survey(64, 1)
+    ns = [n * args.survey_scale for (_, _, n) in specs]
+    seeds = [1 + i for i in range(len(specs))]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": SURVEY, "n_s_scale": args.survey_scale, "n_s_total": sum(ns), "models": len(specs)}
+
+    # (1) plain FP64, one model after another
+    ref, units, ms, launches, events = [], 0, 0.0, 0, 0
+    for (p, g, _), n_s, sd in zip(specs, ns, seeds):
+        m = mc.Model(p, device=dev, precision="fp64")
+        m.set_grid(g)
+        m.run(min(n_s, 1e4), sd, stream=stream)       # warm-up (queues, tables)
+        flush.zero_()
+        e0.record(stream)
+        st = m.run(n_s, sd, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        units += st["n_emit"] + st["n_child"]
+        events += st["n_events"]
+        launches += st["transport_launches"] + GEN_LAUNCHES
+        ref.append(m.spectrum_sums().copy())
+        del m
+    torch.cuda.empty_cache()
+    out["plain_fp64"] = {"value": units / (ms / 1e3), "unit": UNIT, "superphotons": units, "ms": ms,
+                         "scatterings_per_s": events / (ms / 1e3), "gpu_launches": launches}
+
+    # the surrogate network, trained on the GPU by the library's own kernels (untimed set-up)
+    trainer = mc.Model(specs[0][0], device=dev, precision="mixed")
+    vloss = trainer.surrogate_train(n_train=1 << 18, steps=40000, batch=4096, lr=2e-3, seed=1)
+    weights = trainer.surrogate_weights()
+    del trainer
+
+    for form, sur in (("batched_mixed", False), ("batched_mixed_surrogate", True)):
+        ctxs = []
+        for (p, g, _) in specs:
+            m = mc.Model(p, device=dev, precision="mixed", surrogate=sur)
+            if sur:
+                m.surrogate_weights(weights)
+            m.set_grid(g)
+            ctxs.append(m)
+        t0 = time.perf_counter()
+        mc.run_batch(ctxs, ns, seeds, autotune=True, graph=True, stream=stream)   # tune + capture
+        t_setup = time.perf_counter() - t0
+        flush.zero_()
+        e0.record(stream)
+        st = mc.run_batch(ctxs, ns, seeds, autotune=True, graph=True, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1)
+        u = st["n_emit"] + st["n_child"]
+        errs = [spectrum_error(c.spectrum_sums(), r) for c, r in zip(ctxs, ref)]
+        lum = [e[0] for e in errs]
+        nb, nok = sum(e[1] for e in errs), sum(e[2] for e in errs)
+        fp64_flops = (FLOP_STEP_GRID_MIXED * st["n_steps_grid"] + FLOP_ITER * st["n_iters"]
+                      + FLOP_STEP_FREE * (st["n_steps"] - st["n_steps_grid"]) + FLOP_EVENT * st["n_events"]
+                      + FLOP_EMIT * st["n_emit"])
+        kern_s = st["transport_ms"] / 1e3
+        r = {"value": u / (bms / 1e3), "unit": UNIT, "superphotons": u, "ms": bms,
+             "speedup_vs_plain_fp64": (u / (bms / 1e3)) / out["plain_fp64"]["value"],
+             "scatterings_per_s": st["n_events"] / (bms / 1e3),
+             "spectrum_error": {"total_luminosity_rel_max": max(lum), "total_luminosity_rel_median": float(np.median(lum)),
+                                "bins_within_max_1pct_3sigma": nok / max(nb, 1), "bins_compared": nb,
+                                "within_1pct": bool(max(lum) <= 0.01)},
+             "autotune": {"min_blocks_per_sm": st["batch_min_blocks"], "ctas": st["batch_ctas"],
+                          "graph": bool(st["batch_graph"]), "tune_and_capture_s": t_setup},
+             "gpu_launches": 1 + GEN_LAUNCHES * len(specs) + 1,
+             "roofline": {"bound": "alu", "kernel": "k_batch (whole batched transport, one cooperative launch)",
+                          "achieved": fp64_flops / kern_s / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                          "frac": fp64_flops / kern_s / fp64_peak,
+                          "peak_source": "measured FP64 FMA-chain (mc_fma_peak); FP64 share of the mixed path only"}}
+        if sur:
+            tf = FLOP_SUR_EVAL * st["n_steps_grid"] / kern_s / 1e12
+            r["surrogate"] = {"validation_loss": vloss, "tensor_achieved_tflops": tf, "bf16_peak_tflops": bf16_peak,
+                              "tensor_frac": tf / bf16_peak if bf16_peak else None,
+                              "evals": st["n_steps_grid"]}
+        out[form] = r
+        del ctxs
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     global N_S, TAUS
     ap = argparse.ArgumentParser()
@@ -137,6 +251,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass (profiling runs)")
     ap.add_argument("--n-s", type=float, default=N_S, help="N_s per run (smaller cases for profiling)")
     ap.add_argument("--taus", default=",".join(str(t) for t in TAUS), help="comma-separated Thomson depths")
+    ap.add_argument("--no-survey", action="store_true", help="skip the batched-survey form")
+    ap.add_argument("--survey-scale", type=float, default=1.0, help="N_s multiplier of the survey form")
     args = ap.parse_args()
     N_S = args.n_s
     TAUS = tuple(float(t) for t in args.taus.split(","))
@@ -279,8 +395,11 @@ def main():
 
     achieved = flops_grid / t_grid / 1e12
     peak = fp64_peak / 1e12
+    per_run = units / max(args.steps, 1)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": TRAFFIC_B_PER_PH_FP64 * per_run if args.precision == "fp64" else None,
+                "traffic_note": "bytes of the first in-grid launch of a run (it carries every primary): ncu DRAM "
+                                "read+write per superphoton at N_s=1e6 x superphotons per run",
                 "kernel": "k_push<in-grid> (%s): dominant kernel, %.0f%% of transport time"
                           % (args.precision, 100 * t_grid / max(t_transport, 1e-30)),
                 "peak_source": "measured: project FP64 FMA-chain microbenchmark on this GPU (mc_fma_peak)",
@@ -296,6 +415,15 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "first %d primaries (+ scattered descendants, %d superphotons) of the tau_T=1e-2 seed-1 job, "
                          "%.1f s" % (n, u, dt)}
+    survey = None
+    if world == 1 and not args.no_survey:
+        bf16 = None
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16 = json.load(f).get("bf16_tflops")
+        except Exception:
+            bf16 = None
+        survey = survey_forms(args, dev, stream, flush, fp64_peak, bf16)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
@@ -307,7 +435,7 @@ def main():
                 "clocks": clocks,
                 "e2e": None if args.no_e2e else {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                                                   "d2h_bytes_per_step": d2h},
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "cpu_baseline": cpu, "survey": survey,
                 "gpu_launches": int(launches + GEN_LAUNCHES * args.steps),
                 "detail": {"superphotons": units, "scattered": sum(s["n_child"] for s in stats),
                            "steps_per_superphoton": sum(s["n_steps"] for s in stats) / max(units, 1),

@@ -156,8 +156,10 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g);
  * generation by generation (section 3).  The spectrum sums are reset at the start of the
  * call.  `stream` is a cudaStream_t (NULL: default stream); the call returns after the
  * work on `stream` is complete (it reads the counters back).  stats may be NULL.
- * Errors: STATE (no grid), INVALID_ARG, QUEUE_OVERFLOW (scattered superphotons exceeded
- * the queue; results invalid), OOM, CUDA. */
+ * A scattered generation that exceeds the queues makes the call grow them and start again
+ * (same result: every superphoton has its own counter-based stream), up to three times while
+ * device memory allows.  Errors: STATE (no grid), INVALID_ARG, QUEUE_OVERFLOW (the queues could
+ * not grow enough; results invalid), OOM, CUDA. */
 int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards, void *stream,
            mc_run_stats *stats);
 
@@ -241,13 +243,16 @@ int mc_surrogate_infer(mc_ctx *c, const float *x, float *y, int64_t n, int tenso
  * device, precision and surrogate mode) together, each with its own N_s (n_s[i]) and seed.  Per
  * model the weights/counts/scan run as in mc_run; then ONE cooperative persistent kernel
  * transports every superphoton of every model through all scattering generations.  flags: bit 0
- * (MC_BATCH_AUTOTUNE): before the first batched run of this leading context, time 5%-size
- * calibration runs over the register-cap variants and resident CTAs per SM and keep the fastest;
+ * (MC_BATCH_AUTOTUNE): before the first batched run of this leading context, time calibration runs
+ * (every model at the same fraction of its N_s, >= 5% and >= ~5e6 superphotons in all, at most the
+ * whole batch) over the register-cap variants and resident CTAs per SM and keep the fastest;
  * bit 1 (MC_BATCH_GRAPH): capture the whole sequence into a CUDA graph (re-captured when models,
  * N_s, seeds or the launch configuration change) and replay it.  Each model's spectrum is read
  * with mc_get_spectrum on its own context; `stats` (may be NULL) gets the totals and the launch
- * configuration.  State (queues, graph, tuning) is kept by ctxs[0].  Errors: INVALID_ARG, SIZE
- * (more than 64 models), STATE, QUEUE_OVERFLOW, TIMEOUT (grid barrier), OOM, CUDA. */
+ * configuration.  State (queues, graph, tuning) is kept by ctxs[0].  A scattered generation larger
+ * than the pool makes the batch run again with a pool twice as large (same result; up to two times).
+ * Errors: INVALID_ARG, SIZE (more than 64 models, or more transport phases than one launch holds),
+ * STATE, QUEUE_OVERFLOW (the pool cannot grow further), TIMEOUT (grid barrier), OOM, CUDA. */
 #define MC_BATCH_AUTOTUNE 1
 #define MC_BATCH_GRAPH 2
 int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint64_t *seeds, int flags, void *stream,

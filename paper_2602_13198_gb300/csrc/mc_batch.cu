@@ -510,18 +510,21 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
       return set_err(c0, MC_ERR_OOM, "pinned host allocation failed");
     }
   }
-  // capacity: every generation of the batch must fit the pool (primaries ~ N_s per model; the
-  // scattered generations of the survey stay below three times that)
+  // capacity: every generation of the batch must fit the pool (primaries ~ N_s per model; a larger
+  // scattered generation makes the run repeat with a pool twice as large, below)
   double ns_tot = 0.0;
   for (int i = 0; i < n; ++i) ns_tot += n_s[i];
-  int64_t cap = std::max<int64_t>((int64_t)(3.0 * ns_tot) + (1 << 20), bs->cap);
+  int64_t cap = std::max<int64_t>((int64_t)(1.5 * ns_tot) + (1 << 20), bs->cap);
   if (cap > (int64_t)2000000000) return set_err(c0, MC_ERR_SIZE, "batch too large for one launch");
   int rc = batch_alloc(c0, bs, n, cap);
   if (rc) return rc;
-  // ---- autotuner: register cap x resident CTAs per SM, timed on a 5% calibration run
+  // ---- autotuner: register cap x resident CTAs per SM, timed on a calibration run of every model at
+  // a fraction of its N_s.  The fraction keeps >= ~5e6 superphotons in the calibration batch: with
+  // less, the tails of the phases (a few long paths between grid barriers) hide the throughput.
   if ((flags & 1) && !bs->tuned) {
     std::vector<double> ns_small(n);
-    for (int i = 0; i < n; ++i) ns_small[i] = std::max(1.0, 0.05 * n_s[i]);
+    const double frac = std::min(1.0, std::max(0.05, 5e6 / ns_tot));
+    for (int i = 0; i < n; ++i) ns_small[i] = std::max(1.0, frac * n_s[i]);
     double best = 1e300;
     const int minbs[2] = {1, (c0->p.surrogate == 1) ? 2 : 3};
     for (int mb : minbs) {

@@ -327,3 +327,54 @@ def fma_peak(device: int = 0, fp64: bool = True) -> float:
 
 def version() -> str:
     return lib().mc_version().decode()
+
+
+# ------------------------------------------------------------- multi-rank jobs (one process per GPU)
+# Superphotons are independent once the weights and zone counts are fixed (section 2.3), so a job
+# shards by contiguous uid ranges of its primaries; scattered children stay with their parent's
+# rank.  Every rank computes the same weights and counts; the only exchange is one sum-allreduce
+# of the spectrum accumulators (and of the counters) at the end.
+SUMMED_STATS = ("n_emit", "n_child", "n_rec", "n_abs", "n_capt", "n_maxst", "n_steps", "n_iters", "n_nonconv",
+                "n_roul_surv", "n_rej_cap", "n_events", "n_steps_grid", "n_iters_grid")
+
+
+def shard_bounds(total: int, shard: int, n_shards: int):
+    """uid range [u0, u1) of shard `shard` of `n_shards` over `total` primaries: the contiguous
+    split mc_run applies (u0 = floor(total * shard / n_shards))."""
+    if n_shards < 1 or not 0 <= shard < n_shards:
+        raise ValueError("bad shard")
+    return (total * shard) // n_shards, (total * (shard + 1)) // n_shards
+
+
+def _allreduce(arr, dtype, group):
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(np.ascontiguousarray(arr, dtype=dtype).copy())
+    if dist.get_backend(group) == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t.cpu().numpy()
+
+
+def allreduce_spectrum(sums, group=None):
+    """Sum over the ranks of `group` of spectrum accumulators (sum wE, sum (wE)^2, count) in FP64
+    (host tensors under gloo, device tensors under NCCL)."""
+    return _allreduce(sums, np.float64, group)
+
+
+def allreduce_stats(stats: dict, group=None) -> dict:
+    """Counters of a sharded job: event counts summed over ranks; n_total (the job's primary
+    count, the same on every rank) kept."""
+    v = _allreduce([int(stats[k]) for k in SUMMED_STATS], np.int64, group)
+    out = dict(stats)
+    out.update({k: int(x) for k, x in zip(SUMMED_STATS, v)})
+    return out
+
+
+def run_sharded(model: "Model", n_s: float, seed: int, group=None, stream=None):
+    """Runs this rank's shard of the job (N_s, seed) on its GPU and returns the job's summed
+    counters and spectrum accumulators [n_incl][n_bins][3] on every rank."""
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    st = model.run(n_s, seed, shard=rank, n_shards=world, stream=stream)
+    return allreduce_stats(st, group), allreduce_spectrum(model.spectrum_sums(), group)

@@ -307,12 +307,12 @@ def torus3d(**over):
 
 def survey(n_models=64, seed=1):
     """Batched parameter survey: models drawn (seeded) from spin {-0.94,-0.5,0,0.5,0.94} x
-    R_high {1,10,40,160} x accretion-rate scale {0.25,0.5,1,2} (M_unit x scale), grids 128x64, 192x96 or
-    256x128, N_s log-uniform in [1e5, 1e7].  Returns a list of (params, grid, N_s)."""
+    R_high {1,10,40,160} x accretion-rate scale {0.5,1,2,4} (M_unit = 5e17 g x scale), grids 128x64,
+    192x96 or 256x128, N_s log-uniform in [1e5, 1e7].  Returns a list of (params, grid, N_s)."""
     rng = np.random.default_rng(seed)
     spins = [-0.94, -0.5, 0.0, 0.5, 0.94]
     rhs = [1.0, 10.0, 40.0, 160.0]
-    scales = [0.25, 0.5, 1.0, 2.0]
+    scales = [0.5, 1.0, 2.0, 4.0]
     grids = [(128, 64), (192, 96), (256, 128)]
     out = []
     for i in range(n_models):
@@ -321,6 +321,6 @@ def survey(n_models=64, seed=1):
         sc = scales[rng.integers(len(scales))]
         n1, n2 = grids[rng.integers(len(grids))]
         ns = float(10 ** rng.uniform(5, 7))
-        p, g = torus(a=a, n1=n1, n2=n2, R_high=rh, M_unit=1e18 * sc, seed=seed * 1000 + i)
+        p, g = torus(a=a, n1=n1, n2=n2, R_high=rh, M_unit=5e17 * sc, seed=seed * 1000 + i)
         out.append((p, g, ns))
     return out
