@@ -51,9 +51,9 @@ FLOP_EMIT = 2000.0
 FLOP_EVENT = 1500.0
 GEN_LAUNCHES = 7          # zone prep, weight partials, weight final, counts, 3 scan kernels
 # DRAM bytes (read + write) per superphoton of the first in-grid launch of a job, from one ncu capture
-# of k_push<in-grid> (FP64) at N_s = 1e6, tau_T = 1e-2: 227.2 MB for ~787k superphotons.  Traffic grows
-# in proportion to the superphotons a launch carries.  Must be re-taken whenever that kernel changes.
-TRAFFIC_B_PER_PH_FP64 = 289.0
+# of k_push<in-grid> (FP64) at N_s = 1e6, tau_T = 1e-2; traffic grows in proportion to the superphotons
+# a launch carries.  None until re-taken after a change of that kernel.
+TRAFFIC_B_PER_PH_FP64 = None
 
 
 def log(*a):
@@ -397,7 +397,8 @@ def main():
     peak = fp64_peak / 1e12
     per_run = units / max(args.steps, 1)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_B_PER_PH_FP64 * per_run if args.precision == "fp64" else None,
+                "traffic": (TRAFFIC_B_PER_PH_FP64 * per_run
+                            if args.precision == "fp64" and TRAFFIC_B_PER_PH_FP64 else None),
                 "traffic_note": "bytes of the first in-grid launch of a run (it carries every primary): ncu DRAM "
                                 "read+write per superphoton at N_s=1e6 x superphotons per run",
                 "kernel": "k_push<in-grid> (%s): dominant kernel, %.0f%% of transport time"

@@ -142,6 +142,9 @@ DevModel make_model(const mc_ctx *c) {
   m.x3_0 = c->x3_0;
   m.dx3 = c->dx3;
   m.x1_hi = c->x1_0 + c->n1 * c->dx1;
+  m.idx1 = 1.0 / c->dx1;
+  m.idx2 = 1.0 / c->dx2;
+  m.idx3 = 1.0 / c->dx3;
   m.prim64 = c->prim_f32 ? nullptr : (const double *)c->prim;
   m.prim32 = c->prim_f32 ? (const float *)c->prim : nullptr;
   m.lnF = c->lnF;

@@ -54,6 +54,7 @@ struct DevModel {
   int n1, n2, n3, prim_f32;
   int64_t nz;
   double x1_0, dx1, x2_0, dx2, x3_0, dx3, x1_hi;
+  double idx1, idx2, idx3;   // 1 / dx_i
   const double *prim64;
   const float *prim32;
   // tables
@@ -152,20 +153,49 @@ __device__ __forceinline__ void theta_map(double h, double x2, double &th, doubl
   d2th = -2.0 * kPI * kPI * (1.0 - h) * s2;
 }
 
+// sin and cos of |d| < 1/2 by their Taylor series (truncation below 1e-20 relative).
+__device__ __forceinline__ void sincos_small(double d, double &s, double &c) {
+  constexpr double s3 = -1.0 / 6.0, s5 = 1.0 / 120.0, s7 = -1.0 / 5040.0, s9 = 1.0 / 362880.0,
+                   s11 = -1.0 / 39916800.0, s13 = 1.0 / 6227020800.0, s15 = -1.0 / 1307674368000.0;
+  constexpr double c2 = -0.5, c4 = 1.0 / 24.0, c6 = -1.0 / 720.0, c8 = 1.0 / 40320.0, c10 = -1.0 / 3628800.0,
+                   c12 = 1.0 / 479001600.0, c14 = -1.0 / 87178291200.0, c16 = 1.0 / 20922789888000.0;
+  const double d2 = d * d;
+  s = d + d * d2 * (s3 + d2 * (s5 + d2 * (s7 + d2 * (s9 + d2 * (s11 + d2 * (s13 + d2 * s15))))));
+  c = 1.0 + d2 * (c2 + d2 * (c4 + d2 * (c6 + d2 * (c8 + d2 * (c10 + d2 * (c12 + d2 * (c14 + d2 * c16)))))));
+}
+
+// Metric, inverse metric and (DERIV) x1/x2 derivatives at (x1, x2).  theta = pi x2 + delta with
+// delta = (1-h)/2 sin(2 pi x2): sin and cos of theta come from sincospi(x2) and the series of the
+// small angle delta (|delta| < 1/2 for h in (0, 1]) by angle addition.
 template <bool DERIV>
 __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double x2, Geo &G) {
   const double a = m.a, M = m.mass, a2 = a * a;
   double r = exp(x1);
-  double th, dth, d2th;
-  theta_map(m.hslope, x2, th, dth, d2th);
-  double s, c;
-  if (m.hslope == 1.0) sincospi(x2, &s, &c);
-  else sincos(th, &s, &c);
+  double sp, cp;
+  sincospi(x2, &sp, &cp);
+  double dth, d2th, s, c;
+  if (m.hslope == 1.0) {
+    dth = kPI;
+    d2th = 0.0;
+    s = sp;
+    c = cp;
+  } else {
+    const double hh = 0.5 * (1.0 - m.hslope);
+    const double s2x = 2.0 * sp * cp, c2x = (cp - sp) * (cp + sp);   // sin, cos of 2 pi x2
+    dth = kPI * (1.0 + 2.0 * hh * c2x);
+    d2th = -4.0 * kPI * kPI * hh * s2x;
+    double sd, cd;
+    sincos_small(hh * s2x, sd, cd);
+    s = sp * cd + cp * sd;
+    c = cp * cd - sp * sd;
+  }
   double s2 = s * s, c2 = c * c;
   double sig = r * r + a2 * c2;
-  // one division for 1/Sigma, 1/r and 1/sin^2
-  double q = 1.0 / (sig * r * s2);
-  double isig = q * r * s2, ir = q * sig * s2, is2 = q * sig * r;
+  // one division for 1/Sigma, 1/r, 1/sin^2 and 1/(dtheta/dx2)
+  const double rs = r * s2;
+  double Q = 1.0 / (sig * rs * dth);
+  double Qd = Q * dth;
+  double isig = Qd * rs, ir = Qd * sig * s2, is2 = Qd * sig * r, idth = Q * sig * rs;
   double f = 2.0 * M * r * isig;
   double opf = 1.0 + f;
   // Kerr-Schild components (t, r, theta, phi)
@@ -183,7 +213,6 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
   G.g33 = Gpp;
   // inverse: g^tt = -(1+f), g^tr = f, g^rr = (r^2 - 2Mr + a^2)/Sigma, g^rphi = a/Sigma,
   // g^thth = 1/Sigma, g^phph = 1/(Sigma sin^2); divided by the Jacobian factors
-  double idth = (m.hslope == 1.0) ? (1.0 / kPI) : 1.0 / dth;
   G.G00 = -opf;
   G.G01 = f * ir;
   G.G11 = (r * r - 2.0 * M * r + a2) * isig * ir * ir;
@@ -256,15 +285,16 @@ __device__ __forceinline__ void accel(const Geo &G, const double k[4], double A[
 // its scale (1 for ln r and phi, the distance to the nearer pole for x2).
 __device__ __forceinline__ double stepsize(const DevModel &m, const double X[4], const double K[4]) {
   // 1 / (1/d1 + 1/d2 + 1/d3) with d1 = eps/(|k1|+S), d2 = eps x2n/(|k2|+S), d3 = eps/(|k3|+S)
+  // = eps x2n / ((|k1| + |k3|) x2n + |k2|): one division
   const double SMALL = 1e-40;
   double x2n = fmin(fabs(X[2]), fabs(1.0 - X[2]));
-  double den = (fabs(K[1]) + SMALL) + (fabs(K[2]) + SMALL) / x2n + (fabs(K[3]) + SMALL);
-  return m.eps_geo / den;
+  double den = ((fabs(K[1]) + SMALL) + (fabs(K[3]) + SMALL)) * x2n + (fabs(K[2]) + SMALL);
+  return m.eps_geo * x2n / den;
 }
 
 // ---------------------------------------------------------------- tables
-__device__ __forceinline__ double cubic_table(const double *t, int n, double x0, double step, double x) {
-  double f = (x - x0) / step;
+__device__ __forceinline__ double cubic_table(const double *t, int n, double x0, double inv_step, double x) {
+  double f = (x - x0) * inv_step;
   int i = (int)floor(f);
   i = max(1, min(i, n - 3));
   double u = f - i;
@@ -281,17 +311,22 @@ __device__ __forceinline__ double F_of_lnK(const DevModel &m, double lnK) {
     // small-K power law F ~ K^(1/3) continued from the first node
     return exp(m.lnF[0] + (lnK - kFLnK0) / 3.0);
   }
-  return exp(cubic_table(m.lnF, m.nF, kFLnK0, kFStep, lnK));
+  return exp(cubic_table(m.lnF, m.nF, kFLnK0, 1.0 / kFStep, lnK));
 }
 
 __device__ __forceinline__ double K2_of(const DevModel &m, double thetae) {
   if (m.k2_mode == 1) return 2.0 * thetae * thetae;
-  return exp(cubic_table(m.lnK2, m.nK2, kK2LnT0, kK2Step, log(thetae)));
+  return exp(cubic_table(m.lnK2, m.nK2, kK2LnT0, 1.0 / kK2Step, log(thetae)));
 }
 
 __device__ __forceinline__ double K2_of_ln(const DevModel &m, double thetae, double lt) {
   if (m.k2_mode == 1) return 2.0 * thetae * thetae;
-  return exp(cubic_table(m.lnK2, m.nK2, kK2LnT0, kK2Step, lt));
+  return exp(cubic_table(m.lnK2, m.nK2, kK2LnT0, 1.0 / kK2Step, lt));
+}
+
+__device__ __forceinline__ double lnK2_of_ln(const DevModel &m, double lt) {
+  if (m.k2_mode == 1) return 0.6931471805599453 + 2.0 * lt;   // ln(2 Theta^2)
+  return cubic_table(m.lnK2, m.nK2, kK2LnT0, 1.0 / kK2Step, lt);
 }
 
 __device__ __forceinline__ float K2_of_f(const DevModel &m, float thetae) {
@@ -304,8 +339,9 @@ __device__ __forceinline__ float K2_of_f(const DevModel &m, float thetae) {
 }
 
 __device__ __forceinline__ double hot_lookup_ln(const DevModel &m, double lt, double le) {
-  double ft = (lt - kHotLT0) / (kHotLT1 - kHotLT0) * (kHotNT - 1);
-  double fe = (le - kHotLE0) / (kHotLE1 - kHotLE0) * (kHotNE - 1);
+  constexpr double st = (kHotNT - 1) / (kHotLT1 - kHotLT0), se = (kHotNE - 1) / (kHotLE1 - kHotLE0);
+  double ft = (lt - kHotLT0) * st;
+  double fe = (le - kHotLE0) * se;
   ft = fmin(fmax(ft, 0.0), (double)(kHotNT - 1));
   fe = fmin(fmax(fe, 0.0), (double)(kHotNE - 1));
   int i = min((int)ft, kHotNT - 2), j = min((int)fe, kHotNE - 2);
@@ -361,7 +397,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const double X[4
   int i, j;
   double di, dj;
   {
-    double f = (X[1] - m.x1_0) / m.dx1 - 0.5;
+    double f = (X[1] - m.x1_0) * m.idx1 - 0.5;
     i = (int)floor(f);
     di = f - i;
     if (m.n1 == 1) { i = 0; di = 0.0; }
@@ -369,7 +405,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const double X[4
     else if (i > m.n1 - 2) { i = m.n1 - 2; di = 1.0; }
   }
   {
-    double f = (X[2] - m.x2_0) / m.dx2 - 0.5;
+    double f = (X[2] - m.x2_0) * m.idx2 - 0.5;
     j = (int)floor(f);
     dj = f - j;
     if (m.n2 == 1) { j = 0; dj = 0.0; }
@@ -379,7 +415,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const double X[4
   int k0 = 0, k1 = 0;
   double dk = 0.0;
   if (m.n3 > 1) {
-    double f = (X[3] - m.x3_0) / m.dx3 - 0.5;
+    double f = (X[3] - m.x3_0) * m.idx3 - 0.5;
     double fl = floor(f);
     dk = f - fl;
     long long kk = (long long)fl;
@@ -447,7 +483,7 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &
   T alpha = rsqrt(-(T)G.G00);
   T q = g11 * U1 * U1 + g22 * U2 * U2 + g33 * U3 * U3 + (T)2 * g13 * U1 * U3;
   T gamma = sqrt((T)1 + q);
-  T u0 = gamma / alpha;
+  T u0 = gamma * (-(T)G.G00) * alpha;   // gamma / alpha, alpha = (-g^tt)^(-1/2)
   T u1 = U1 - gamma * alpha * (T)G.G01;
   T u2 = U2, u3 = U3;
   T uc0 = g00 * u0 + g01 * u1 + g03 * u3;
@@ -502,22 +538,28 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
   if (!P.on) return;
   double eps = -(K[0] * P.ucov[0] + K[1] * P.ucov[1] + K[2] * P.ucov[2] + K[3] * P.ucov[3]);
   if (!(eps > 0.0)) return;
-  double nu = eps * (kME * kCL * kCL / kHPL);
+  constexpr double kNuEps = kME * kCL * kCL / kHPL;   // nu / eps
+  const double ieps = 1.0 / eps;
+  double nu = eps * kNuEps;
   double lt = log(fmax(P.thetae, 1e-300));
   if (P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
     double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
-    double cth = fmin(1.0, fmax(-1.0, kb * rsqrt(P.bsq) / eps));
+    double cth = fmin(1.0, fmax(-1.0, kb * rsqrt(P.bsq) * ieps));
     double s2 = 1.0 - cth * cth;
     if (s2 > 0.0) {
       double nus = (2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL)) * P.B * P.thetae * P.thetae * sqrt(s2);
       double Xs = nu / nus;
-      double Gs = Gsyn(Xs);
-      if (Gs > 0.0) {
+      // G(X) / K2 with one exponential: G = t^2 exp(-X^1/3), t = X^1/2 + 2^(11/12) X^1/6
+      double x6 = cbrt(sqrt(Xs));
+      double x3 = x6 * x6;
+      if (x3 < 745.0) {   // beyond, exp(-X^1/3) underflows: no emission or absorption
+        double t = x6 * x3 + 1.8877486253633870 * x6;
+        double GoK = t * t * exp(-x3 - lnK2_of_ln(m, lt));
         // nu alpha_nu = nu j_nu / B_nu with j_nu = sqrt2 pi e^2 n_e nu_s G / (3 c K2) and
         // B_nu = 2 h nu^3 / (c^2 expm1(h nu / k T)), h nu / k T = eps / Theta_e:
-        // nu alpha_nu = (sqrt2 pi e^2 c / 6h) n_e G expm1(eps/Theta) / (K2 X nu), X = nu/nu_s
-        const double C1 = 1.4142135623730951 * kPI * kEE * kEE * kCL / (6.0 * kHPL);
-        c.ana = C1 * P.ne * Gs * expm1(eps / P.thetae) / (K2_of_ln(m, P.thetae, lt) * Xs * nu);
+        // nu alpha_nu = (sqrt2 pi e^2 c / 6h) n_e (G / K2) expm1(eps/Theta) nu_s / nu^2
+        const double C1 = 1.4142135623730951 * kPI * kEE * kEE * kCL / (6.0 * kHPL) / (kNuEps * kNuEps);
+        c.ana = C1 * P.ne * GoK * expm1(eps / P.thetae) * nus * (ieps * ieps);
       }
     }
   }
