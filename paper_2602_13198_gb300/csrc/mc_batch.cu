@@ -459,7 +459,11 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
   b.timeout_ns = 120e9;
   BatchKernel kern = pick_kernel(mixed, sur, minb);
   int smem = sur ? std::max(kTcSmemBytes, 40 * 1024) : 0;
-  if (smem) cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem) {
+    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // shared memory over L1 so that two CTAs of ~92 KB fit on an SM
+    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   void *args[] = {&b};
   if (timed) cudaEventRecord(bs->e0, st);
   e = cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(128), args, smem, st);
@@ -471,7 +475,11 @@ static int max_ctas(mc_ctx *c0, int minb) {
   const bool mixed = c0->p.precision == MC_PREC_MIXED, sur = c0->p.surrogate == 1;
   BatchKernel kern = pick_kernel(mixed, sur, minb);
   int smem = sur ? std::max(kTcSmemBytes, 40 * 1024) : 0;
-  if (smem) cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem) {
+    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // shared memory over L1 so that two CTAs of ~92 KB fit on an SM
+    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)kern, 128, smem);
   if (sur) n = std::min(n, 4);   // four CTAs x 128 TMEM columns fill an SM's tensor memory

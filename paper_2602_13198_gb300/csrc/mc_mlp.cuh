@@ -122,7 +122,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// z sigmoid(z) with the fast reciprocal division (a few ulp; the BF16 split keeps ~16 bits)
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // Per-CTA state of the tensor-core MLP: shared-memory tiles, TMEM base, mbarrier and its phase.
 struct TcMlp {
@@ -207,13 +208,19 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16(v - __bfloat162float(hi));
 }
 
-// Writes 64 activations of this thread's row as hi/lo BF16 rows of A2 / A2lo.
+// Writes 64 activations of this thread's row as hi/lo BF16 rows of A2 / A2lo (two values per
+// conversion: element 2q in the low half of each packed pair, as in memory order).
 __device__ __forceinline__ void put_hidden(TcMlp &T, int row, const float *h) {
 #pragma unroll
   for (int c = 0; c < 64; c += 8) {
-    __nv_bfloat16 hi[8], lo[8];
+    __nv_bfloat162 hi[4], lo[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) split_bf16(h[c + q], hi[q], lo[q]);
+    for (int q = 0; q < 4; ++q) {
+      const float a = h[c + 2 * q], b = h[c + 2 * q + 1];
+      hi[q] = __floats2bfloat162_rn(a, b);
+      const float2 back = __bfloat1622float2(hi[q]);
+      lo[q] = __floats2bfloat162_rn(a - back.x, b - back.y);
+    }
     *(uint4 *)(T.a2 + kmajor_off(row, c, 64)) = *(uint4 *)hi;
     *(uint4 *)(T.a2l + kmajor_off(row, c, 64)) = *(uint4 *)lo;
   }

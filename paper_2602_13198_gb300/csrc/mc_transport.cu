@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(128) k_push_sur(DevModel m, PushIO io, Surroga
 int push_sur_max_blocks_per_sm(int block, int smem) {
   int n = 0;
   cudaFuncSetAttribute(k_push_sur, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_push_sur, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push_sur, block, smem);
   return n;
 }
