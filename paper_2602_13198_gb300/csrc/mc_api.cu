@@ -147,6 +147,7 @@ DevModel make_model(const mc_ctx *c) {
   m.idx3 = 1.0 / c->dx3;
   m.prim64 = c->prim_f32 ? nullptr : (const double *)c->prim;
   m.prim32 = c->prim_f32 ? (const float *)c->prim : nullptr;
+  m.prim32x = c->prim_f32 ? (const float *)c->prim : c->prim_x32;
   m.lnF = c->lnF;
   m.nF = c->nF;
   m.lnK2 = c->lnK2;
@@ -289,9 +290,11 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   int64_t nz = (int64_t)g->n1 * g->n2 * g->n3;
   size_t esz = (g->dtype == MC_DTYPE_F32) ? 4 : 8;
   // free per-grid buffers
-  void *old[] = {c->prim, c->zvol, c->zpref, c->zlnuc, c->zgmax, c->znbar, c->counts, c->start, c->bsum, c->partial};
+  void *old[] = {c->prim, c->prim_x32, c->zvol, c->zpref, c->zlnuc, c->zgmax, c->znbar, c->counts, c->start, c->bsum,
+                 c->partial};
   for (void *ptr : old) dev_free(c, ptr);
   c->prim = nullptr;
+  c->prim_x32 = nullptr;
   c->have_grid = false;
   c->have_run = false;
   c->n1 = g->n1; c->n2 = g->n2; c->n3 = g->n3; c->nz = nz;
@@ -320,6 +323,15 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   }
   CU(cudaMemset(c->bad, 0, sizeof(int)));
   launch_grid_to_aos(src, c->prim_f32, c->prim, c->prim_f32, nz, c->bad, 0);
+  if (c->p.precision == MC_PREC_MIXED && !c->prim_f32) {
+    // the FP32 coefficient path reads FP32 primitives directly (no per-step conversions)
+    c->prim_x32 = (float *)dev_alloc(c, 4 * 8 * nz);
+    if (!c->prim_x32) {
+      if (staging) dev_free(c, staging);
+      return fail(c, MC_ERR_OOM, "grid allocation failed");
+    }
+    launch_grid_to_aos(src, 0, c->prim_x32, 1, nz, c->bad, 0);
+  }
   int bad = 0;
   CU(cudaMemcpy(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost));
   if (staging) dev_free(c, staging);

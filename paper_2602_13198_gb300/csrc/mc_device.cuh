@@ -57,6 +57,7 @@ struct DevModel {
   double idx1, idx2, idx3;   // 1 / dx_i
   const double *prim64;
   const float *prim32;
+  const float *prim32x;   // FP32 primitives for the FP32 coefficient path (the grid or a copy), or NULL
   // tables
   const double *lnF;      // angle integral
   int nF;
@@ -425,19 +426,29 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const double X[4
   int i1 = (m.n1 > 1) ? i + 1 : i, j1 = (m.n2 > 1) ? j + 1 : j;
   int64_t z00 = ((int64_t)i * m.n2 + j) * m.n3, z01 = ((int64_t)i * m.n2 + j1) * m.n3;
   int64_t z10 = ((int64_t)i1 * m.n2 + j) * m.n3, z11 = ((int64_t)i1 * m.n2 + j1) * m.n3;
-  T w00 = (T)((1 - di) * (1 - dj)), w01 = (T)((1 - di) * dj), w10 = (T)(di * (1 - dj)), w11 = (T)(di * dj);
+  // FP32 output reads FP32 primitives when there are any (no per-corner conversions)
+  constexpr bool kF32 = sizeof(T) == 4;
+  const bool rd32 = kF32 ? (m.prim32x != nullptr) : (m.prim_f32 != 0);
+  const float *p32 = kF32 ? m.prim32x : m.prim32;
+  T w00, w01, w10, w11;
+  if (kF32) {
+    const T a = (T)di, b = (T)dj;
+    w00 = (1 - a) * (1 - b); w01 = (1 - a) * b; w10 = a * (1 - b); w11 = a * b;
+  } else {
+    w00 = (T)((1 - di) * (1 - dj)); w01 = (T)((1 - di) * dj); w10 = (T)(di * (1 - dj)); w11 = (T)(di * dj);
+  }
   T wk0 = (T)(1 - dk), wk1 = (T)dk;
 #pragma unroll
   for (int f = 0; f < 8; ++f) pr[f] = (T)0;
   auto acc = [&](int64_t zb, T w) {
-    if (m.prim_f32) {
-      const float4 *p0 = reinterpret_cast<const float4 *>(m.prim32 + (zb + k0) * 8);
+    if (rd32) {
+      const float4 *p0 = reinterpret_cast<const float4 *>(p32 + (zb + k0) * 8);
       float4 a0 = __ldg(p0), a1 = __ldg(p0 + 1);
       T ww = w * wk0;
       pr[0] += ww * (T)a0.x; pr[1] += ww * (T)a0.y; pr[2] += ww * (T)a0.z; pr[3] += ww * (T)a0.w;
       pr[4] += ww * (T)a1.x; pr[5] += ww * (T)a1.y; pr[6] += ww * (T)a1.z; pr[7] += ww * (T)a1.w;
       if (m.n3 > 1) {
-        const float4 *p1 = reinterpret_cast<const float4 *>(m.prim32 + (zb + k1) * 8);
+        const float4 *p1 = reinterpret_cast<const float4 *>(p32 + (zb + k1) * 8);
         float4 b0 = __ldg(p1), b1 = __ldg(p1 + 1);
         ww = w * wk1;
         pr[0] += ww * (T)b0.x; pr[1] += ww * (T)b0.y; pr[2] += ww * (T)b0.z; pr[3] += ww * (T)b0.w;
