@@ -190,6 +190,13 @@ int mc_trace(mc_ctx *c, double n_s, uint64_t seed, const int64_t *uids, size_t n
  * NO_DEVICE, CUDA. */
 int mc_fma_peak(int device, int dtype, double *flops);
 
+/* Test hook: evaluates, on the current device, one of the library's own implementations of a
+ * special function next to CUDA's for the same inputs.  which = 0: sine of |x| < 1/2 by the Taylor
+ * series used in the metric (ref: CUDA sin); 1: its cosine (ref: CUDA cos); 2: x^(1/6) by the
+ * FP32-seeded Newton iteration used in the synchrotron function (ref: cbrt(sqrt(x))).  x, y, ref
+ * are n host doubles (caller-owned).  Errors: INVALID_ARG, NO_DEVICE, CUDA. */
+int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t n);
+
 /* Zone superphoton counts for (N_s, seed) -- the same numbers mc_run computes and
  * mc_get_zone_counts returns -- without allocating any device memory, for callers that cannot
  * allocate at this point (a stream being captured into a graph, a custom allocator's callback,

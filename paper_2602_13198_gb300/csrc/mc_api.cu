@@ -142,6 +142,8 @@ DevModel make_model(const mc_ctx *c) {
   m.x3_0 = c->x3_0;
   m.dx3 = c->dx3;
   m.x1_hi = c->x1_0 + c->n1 * c->dx1;
+  m.ithetae_max = 1.0 / p.thetae_max;
+  m.iB_unit = 1.0 / m.B_unit;
   m.idx1 = 1.0 / c->dx1;
   m.idx2 = 1.0 / c->dx2;
   m.idx3 = 1.0 / c->dx3;
@@ -714,6 +716,28 @@ int mc_fma_peak(int device, int dtype, double *flops) {
   cudaError_t e = fma_peak(dtype == MC_DTYPE_F64, &f);
   if (e != cudaSuccess) return fail(nullptr, MC_ERR_CUDA, cudaGetErrorString(e));
   *flops = f;
+  return MC_OK;
+}
+
+int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t n) {
+  if (which < 0 || which > 2 || n < 0 || (n > 0 && (!x || !y || !ref))) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(nullptr, MC_ERR_NO_DEVICE, "no CUDA device");
+  }
+  if (n == 0) return MC_OK;
+  double *d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 3 * n) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, MC_ERR_OOM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(d, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = selftest_math(which, d, d + n, d + 2 * n, n);
+  if (e == cudaSuccess) e = cudaMemcpy(y, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ref, d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(nullptr, MC_ERR_CUDA, cudaGetErrorString(e));
   return MC_OK;
 }
 

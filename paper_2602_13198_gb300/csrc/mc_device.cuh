@@ -39,6 +39,7 @@ struct DevModel {
   double a, mass, hslope, r_h;
   double rho_unit, B_unit, Ne_unit, Ccoef, L3;   // Ccoef = h L / (m_e c^2), L3 = L_unit^3
   double R_high, R_low, gam, thetae_min, thetae_max;
+  double ithetae_max, iB_unit;   // 1 / thetae_max, 1 / B_unit
   // emission band / weights
   double lnu_min, dlnu, dlntot;
   int n_nu;
@@ -372,6 +373,22 @@ __device__ __forceinline__ float hot_lookup_f(const DevModel &m, float thetae, f
   return (float)kSIGT * __expf(l);
 }
 
+// X^(1/6) for X in (1e-30, 1e30): z = X^(-1/6) from an FP32 seed (relative error < 1e-5) refined by two
+// division-free Newton steps on f(z) = z^-6 - X (z <- z + z (1 - X z^6) / 6, error ~3.5 e^2 per step),
+// then X^(1/6) = X z^5.  Outside that range: cbrt(sqrt(X)).
+__device__ __forceinline__ double pow_sixth(double X) {
+  if (!(X > 1e-30 && X < 1e30)) return cbrt(sqrt(X));
+  double z = (double)__expf(__logf((float)X) * (-1.0f / 6.0f));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double z2 = z * z;
+    const double t = fma(-X, z2 * z2 * z2, 1.0);
+    z = fma(z * t, 1.0 / 6.0, z);
+  }
+  const double z2 = z * z;
+  return X * (z2 * z2 * z);
+}
+
 // ---------------------------------------------------------------- synchrotron (section 2.2)
 // G(X) = (X^1/2 + 2^11/12 X^1/6)^2 exp(-X^1/3)
 __device__ __forceinline__ double Gsyn(double X) {
@@ -387,6 +404,8 @@ struct Plasma {
   T ne, thetae, B;
   T ucov[4], bcov[4];
   T bsq;
+  T rb;    // 1 / sqrt(b^2) (0 without field); FP64 path only
+  T ith;   // 1 / Theta_e (0 when Theta_e = 0); FP64 path only
   bool on;
 };
 
@@ -491,9 +510,11 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &
   T g00 = (T)G.g00, g01 = (T)G.g01, g03 = (T)G.g03, g11 = (T)G.g11, g13 = (T)G.g13, g22 = (T)G.g22, g33 = (T)G.g33;
   T rho = pr[0], uu = pr[1];
   T U1 = pr[5], U2 = pr[6], U3 = pr[7];
+  constexpr bool kF64 = sizeof(T) == 8;
   T alpha = rsqrt(-(T)G.G00);
   T q = g11 * U1 * U1 + g22 * U2 * U2 + g33 * U3 * U3 + (T)2 * g13 * U1 * U3;
-  T gamma = sqrt((T)1 + q);
+  T rg = rsqrt((T)1 + q);                   // 1 / gamma
+  T gamma = kF64 ? ((T)1 + q) * rg : sqrt((T)1 + q);
   T u0 = gamma * (-(T)G.G00) * alpha;   // gamma / alpha, alpha = (-g^tt)^(-1/2)
   T u1 = U1 - gamma * alpha * (T)G.G01;
   T u2 = U2, u3 = U3;
@@ -502,7 +523,7 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &
   T uc2 = g22 * u2;
   T uc3 = g03 * u0 + g13 * u1 + g33 * u3;
   T b0 = pr[2] * uc1 + pr[3] * uc2 + pr[4] * uc3;
-  T iu0 = (T)1 / u0;
+  T iu0 = kF64 ? alpha * rg : (T)1 / u0;   // alpha / gamma
   T b1 = (pr[2] + b0 * u1) * iu0, b2 = (pr[3] + b0 * u2) * iu0, b3 = (pr[4] + b0 * u3) * iu0;
   T bc0 = g00 * b0 + g01 * b1 + g03 * b3;
   T bc1 = g01 * b0 + g11 * b1 + g13 * b3;
@@ -514,19 +535,45 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &
   if (bcon_out) { bcon_out[0] = b0; bcon_out[1] = b1; bcon_out[2] = b2; bcon_out[3] = b3; }
   P.bsq = b0 * bc0 + b1 * bc1 + b2 * bc2 + b3 * bc3;
   P.ne = (rho > (T)0) ? rho * (T)m.Ne_unit : (T)0;
-  P.B = sqrt(fmax(P.bsq, (T)0)) * (T)m.B_unit;
+  P.rb = (T)0;
+  P.ith = (T)0;
+  if (kF64) {
+    // one reciprocal square root gives |b| (for B), 1/b^2 (for beta) and the 1/|b| of cos(theta_B)
+    const T rb = (P.bsq > (T)0) ? rsqrt(P.bsq) : (T)0;
+    P.rb = rb;
+    P.B = P.bsq * rb * (T)m.B_unit;
+  } else {
+    P.B = sqrt(fmax(P.bsq, (T)0)) * (T)m.B_unit;
+  }
   if (rho > (T)0 && uu > (T)0) {
     // Theta_e = (m_p/m_e)(gam-1)(u/rho)/(1 + T_i/T_e), T_i/T_e = (R_high beta^2 + R_low)/(1 + beta^2)
-    T th;
+    T num, den;
     if (P.bsq > (T)0) {
-      T beta = (T)2 * uu * ((T)m.gam - (T)1) / P.bsq;
+      T beta = kF64 ? (T)2 * uu * ((T)m.gam - (T)1) * P.rb * P.rb : (T)2 * uu * ((T)m.gam - (T)1) / P.bsq;
       T b2x = beta * beta;
-      th = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu * ((T)1 + b2x) /
-           (rho * ((T)1 + (T)m.R_low + ((T)1 + (T)m.R_high) * b2x));
+      num = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu * ((T)1 + b2x);
+      den = rho * ((T)1 + (T)m.R_low + ((T)1 + (T)m.R_high) * b2x);
     } else {
-      th = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu / (rho * ((T)1 + (T)m.R_high));
+      num = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu;
+      den = rho * ((T)1 + (T)m.R_high);
     }
-    P.thetae = fmin(th, (T)m.thetae_max);
+    T th, ith = (T)0;
+    const T nd = num * den;
+    if (kF64 && nd > (T)1e-300 && nd < (T)1e300) {
+      // Theta_e and 1/Theta_e from one reciprocal
+      const T inv = (T)1 / nd;
+      th = num * (num * inv);
+      ith = den * (den * inv);
+    } else {
+      th = num / den;
+      if (kF64) ith = den / num;
+    }
+    if (th > (T)m.thetae_max) {
+      th = (T)m.thetae_max;
+      ith = (T)m.ithetae_max;
+    }
+    P.thetae = th;
+    P.ith = ith;
   } else {
     P.thetae = (T)0;
   }
@@ -555,13 +602,16 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
   double lt = log(fmax(P.thetae, 1e-300));
   if (P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
     double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
-    double cth = fmin(1.0, fmax(-1.0, kb * rsqrt(P.bsq) * ieps));
+    double cth = fmin(1.0, fmax(-1.0, kb * P.rb * ieps));
     double s2 = 1.0 - cth * cth;
     if (s2 > 0.0) {
-      double nus = (2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL)) * P.B * P.thetae * P.thetae * sqrt(s2);
-      double Xs = nu / nus;
+      constexpr double kNus = (2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL));   // nu_s / (B Theta^2 sin)
+      const double rs = rsqrt(s2);
+      double nus = kNus * P.B * P.thetae * P.thetae * (s2 * rs);
+      // X = nu / nu_s from the reciprocals at hand: 1/B = rb / B_unit, 1/Theta, 1/sin = rs
+      double Xs = nu * (1.0 / kNus) * (P.rb * m.iB_unit) * (P.ith * P.ith) * rs;
       // G(X) / K2 with one exponential: G = t^2 exp(-X^1/3), t = X^1/2 + 2^(11/12) X^1/6
-      double x6 = cbrt(sqrt(Xs));
+      double x6 = pow_sixth(Xs);
       double x3 = x6 * x6;
       if (x3 < 745.0) {   // beyond, exp(-X^1/3) underflows: no emission or absorption
         double t = x6 * x3 + 1.8877486253633870 * x6;
@@ -570,7 +620,7 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
         // B_nu = 2 h nu^3 / (c^2 expm1(h nu / k T)), h nu / k T = eps / Theta_e:
         // nu alpha_nu = (sqrt2 pi e^2 c / 6h) n_e (G / K2) expm1(eps/Theta) nu_s / nu^2
         const double C1 = 1.4142135623730951 * kPI * kEE * kEE * kCL / (6.0 * kHPL) / (kNuEps * kNuEps);
-        c.ana = C1 * P.ne * GoK * expm1(eps / P.thetae) * nus * (ieps * ieps);
+        c.ana = C1 * P.ne * GoK * expm1(eps * P.ith) * nus * (ieps * ieps);
       }
     }
   }

@@ -89,6 +89,7 @@ void launch_scan(const int64_t *counts, int64_t *start, int64_t *bsum, int64_t n
 void launch_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, int64_t nz, int *bad, cudaStream_t st);
 // FMA-chain throughput of the FP64 or FP32 pipe in FLOP/s (mc_tables.cu)
 cudaError_t fma_peak(bool fp64, double *flops);
+cudaError_t selftest_math(int which, const double *x_dev, double *y_dev, double *ref_dev, int64_t n);
 // transport (mc_transport.cu)
 int push_max_blocks_per_sm(int mixed, int phase, int block);
 void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st);

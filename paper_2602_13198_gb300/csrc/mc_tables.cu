@@ -337,4 +337,27 @@ static cudaError_t fma_peak_t(double *flops) {
 
 cudaError_t fma_peak(bool fp64, double *flops) { return fp64 ? fma_peak_t<double>(flops) : fma_peak_t<float>(flops); }
 
+// ---------------------------------------------------------------- special-function self-test
+__global__ void k_selftest_math(int which, const double *x, double *y, double *ref, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  if (which == 2) {
+    y[i] = pow_sixth(v);
+    ref[i] = cbrt(sqrt(v));
+    return;
+  }
+  double s, c, rs, rc;
+  sincos_small(v, s, c);
+  sincos(v, &rs, &rc);
+  y[i] = (which == 0) ? s : c;
+  ref[i] = (which == 0) ? rs : rc;
+}
+
+cudaError_t selftest_math(int which, const double *x_dev, double *y_dev, double *ref_dev, int64_t n) {
+  if (n > 0) k_selftest_math<<<(unsigned)((n + 255) / 256), 256>>>(which, x_dev, y_dev, ref_dev, n);
+  cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : cudaDeviceSynchronize();
+}
+
 }  // namespace mcgb

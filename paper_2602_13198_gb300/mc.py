@@ -108,6 +108,8 @@ def lib():
         L.mc_version.restype = C.c_char_p
         L.mc_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
         L.mc_fma_peak.restype = C.c_int
+        L.mc_selftest_math.argtypes = [C.c_int, vp, vp, vp, C.c_int64]
+        L.mc_selftest_math.restype = C.c_int
         L.mc_run_batch.argtypes = [C.POINTER(vp), C.c_int, dp, C.POINTER(u64), C.c_int, vp, C.POINTER(RunStats)]
         L.mc_run_batch.restype = C.c_int
         L.mc_zone_counts_noalloc.argtypes = [vp, C.c_double, u64, vp, vp, vp, vp]
@@ -323,6 +325,17 @@ def fma_peak(device: int = 0, fp64: bool = True) -> float:
     if rc != MC_OK:
         raise MCError(rc, lib().mc_last_error(None).decode())
     return f.value
+
+
+def selftest_math(which: int, x):
+    """Test hook: (library implementation, CUDA reference) of special function `which` at x (see
+    mc_selftest_math in include/mc.h)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y, ref = np.empty_like(x), np.empty_like(x)
+    rc = lib().mc_selftest_math(int(which), x.ctypes.data, y.ctypes.data, ref.ctypes.data, len(x))
+    if rc != MC_OK:
+        raise MCError(rc, lib().mc_last_error(None).decode())
+    return y, ref
 
 
 def version() -> str:

@@ -1,0 +1,39 @@
+"""The library's own special-function implementations against CUDA's on the device: the Taylor
+sine/cosine of the small theta-map angle (metric evaluation) and the Newton x^(1/6) of the
+synchrotron function."""
+import numpy as np
+import pytest
+
+from helpers import requires_gpu
+
+pytestmark = [pytest.mark.gpu, requires_gpu]
+
+
+def _mc():
+    from paper_2602_13198_gb300 import build, mc
+    build.build()
+    return mc
+
+
+def test_small_angle_sine_and_cosine_match_cuda():
+    mc = _mc()
+    x = np.concatenate([np.linspace(-0.5, 0.5, 200001), np.array([0.0, 1e-300, -1e-12, 0.35, -0.35])])
+    s, s_ref = mc.selftest_math(0, x)
+    c, c_ref = mc.selftest_math(1, x)
+    # a few units in the last place of the result
+    assert np.all(np.abs(s - s_ref) <= 4 * np.spacing(np.abs(s_ref)) + 1e-300)
+    assert np.all(np.abs(c - c_ref) <= 4 * np.spacing(np.abs(c_ref)))
+    # the exact small-argument behaviour: sin x = x, cos x = 1
+    assert s[-4] == 1e-300 and c[-4] == 1.0
+
+
+def test_sixth_root_matches_cuda():
+    mc = _mc()
+    rng = np.random.default_rng(4)
+    x = np.concatenate([10.0 ** rng.uniform(-29.9, 29.9, 200000),
+                        np.array([1.0, 64.0, 1e-30, 1e30, 1e-40, 1e40, 3.0e-31, 7.0e35])])
+    y, ref = mc.selftest_math(2, x)
+    rel = np.abs(y / ref - 1.0)
+    # X z^5 takes four roundings after the Newton steps, cbrt(sqrt(x)) two: within 10 ulp
+    assert rel.max() < 10 * 2.2e-16, rel.max()
+    assert abs(y[-8] - 1.0) <= 2.3e-16 and abs(y[-7] - 2.0) <= 4.5e-16   # x = 1 and x = 64
