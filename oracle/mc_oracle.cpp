@@ -1082,16 +1082,19 @@ void transport(const Model &M, Photon &p, std::vector<Child> &stack, Acc &acc) {
 }
 
 // Emission of primary superphoton uid (section 2.3): zone from the exclusive scan of counts,
-// frequency by rejection against the zone's dN/dln(nu) (piecewise linear in ln nu between the
-// weight-table nodes, reading), direction by rejection against j_nu(theta)/j_nu(pi/2),
-// azimuth uniform, wavevector built in the emission tetrad at the zone centre.
+// frequency proposed by rejection against the piecewise-linear interpolant (in ln nu) of the
+// zone's dN/dln(nu) node values g_j, direction by rejection against j_nu(theta)/j_nu(pi/2),
+// azimuth uniform, wavevector built in the emission tetrad at the zone centre.  The weight is
+// w(nu) g(nu) / g_lin(nu) = int dOmega j_nu(nu) / g_lin(nu): with it the expected emitted spectrum
+// is the zone's exact dN/dln(nu) (section 2.3 accepts against dN/dln(nu) at the drawn nu itself),
+// and the trapezoid zone count cancels from the normalisation.
 void emit(const Model &M, int64_t uid, Photon &p, int64_t *rejcap) {
   const or_params &P = M.P;
   int64_t z = (int64_t)(std::upper_bound(M.start.begin(), M.start.end(), uid) - M.start.begin()) - 1;
   p.s = Stream{M.seed, (uint64_t)uid, 0u};
   const double *gz = &M.g[(size_t)z * M.nnu];
   double gm = M.gmax[z];
-  double lnu = M.lnumin;
+  double lnu = M.lnumin, glin = 0.0;
   int it;
   for (it = 0; it < 100000; ++it) {
     double r1 = uniform(p.s);
@@ -1099,9 +1102,9 @@ void emit(const Model &M, int64_t uid, Photon &p, int64_t *rejcap) {
     double fj = (lnu - M.lnumin) / M.dlnu;
     int j = std::min(std::max((int)std::floor(fj), 0), M.nnu - 2);
     double fr = fj - j;
-    double gv = (1.0 - fr) * gz[j] + fr * gz[j + 1];
+    glin = (1.0 - fr) * gz[j] + fr * gz[j + 1];
     double r2 = uniform(p.s);
-    if (r2 * gm < gv) break;
+    if (r2 * gm < glin) break;
   }
   if (it == 100000) (*rejcap)++;
   double nu = std::exp(lnu);
@@ -1132,11 +1135,8 @@ void emit(const Model &M, int64_t uid, Photon &p, int64_t *rejcap) {
     p.X[m] = X[m];
     p.K[m] = kf[0] * e[0][m] + kf[1] * e[1][m] + kf[2] * e[2][m] + kf[3] * e[3][m];
   }
-  // superphoton weight: ln w interpolated linearly in ln nu between table nodes
-  double fj = (lnu - M.lnumin) / M.dlnu;
-  int j = std::min(std::max((int)std::floor(fj), 0), M.nnu - 2);
-  double fr = fj - j;
-  p.w = std::exp((1.0 - fr) * M.lnw[j] + fr * M.lnw[j + 1]);
+  // superphoton weight: int dOmega j_nu at the drawn nu over the interpolated target
+  p.w = glin > 0.0 ? jnu_angint(P, nu, F.ne, F.thetae, F.B) / glin : 0.0;
   p.nsc = 0;
 }
 

@@ -46,7 +46,8 @@ static __device__ void init_transport(const DevModel &m, Ph &p) {
   p.wb = p.w;
 }
 
-// Emission of primary uid (section 2.3) at the centre of its zone.
+// Emission of primary uid (section 2.3) at the centre of its zone: frequency proposed from the
+// piecewise-linear interpolant of the zone's dN/dln(nu) node values, weighted back to the exact one.
 static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &ls) {
   int64_t lo = 0, hi = m.nz - 1;
   while (lo < hi) {
@@ -57,7 +58,7 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
   const int64_t z = lo;
   rng_init(p.s, (uint64_t)uid, 0u);
   const double pref = m.zpref[z], lnuc = m.zlnuc[z], gm = m.zgmax[z];
-  double lnu = m.lnu_min;
+  double lnu = m.lnu_min, glin = 0.0;
   int it;
   for (it = 0; it < 100000; ++it) {
     double r1 = rng_u(p.s, m.seed);
@@ -67,9 +68,9 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
     double fr = fj - j;
     double g0 = pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc) * m.winv[j];
     double g1 = pref * F_of_lnK(m, m.lnu_min + (j + 1) * m.dlnu - lnuc) * m.winv[j + 1];
-    double gv = (1.0 - fr) * g0 + fr * g1;
+    glin = (1.0 - fr) * g0 + fr * g1;
     double r2 = rng_u(p.s, m.seed);
-    if (r2 * gm < gv) break;
+    if (r2 * gm < glin) break;
   }
   if (it == 100000) ls.rejcap++;
   // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
@@ -111,10 +112,9 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
     p.X[q] = X[q];
     p.K[q] = kf[0] * e[0][q] + kf[1] * e[1][q] + kf[2] * e[2][q] + kf[3] * e[3][q];
   }
-  double fj = (lnu - m.lnu_min) / m.dlnu;
-  int j = min(max((int)floor(fj), 0), m.n_nu - 2);
-  double fr = fj - j;
-  p.w = exp((1.0 - fr) * m.lnw[j] + fr * m.lnw[j + 1]);
+  // weight w(nu) g(nu) / g_lin(nu) = int dOmega j_nu(nu) / g_lin(nu): the proposal follows the
+  // piecewise-linear target, the weight restores the zone's exact dN/dln(nu) (section 2.3)
+  p.w = glin > 0.0 ? pref * F_of_lnK(m, lnu - lnuc) / glin : 0.0;
   p.nsc = 0;
 }
 

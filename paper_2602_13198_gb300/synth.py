@@ -70,10 +70,24 @@ def _zone_centres(g):
     return X1.ravel(), X2.ravel(), X3.ravel()
 
 
+def inside_fraction(g, R, sub):
+    """Fraction of each zone inside r < R (section 4.1 partial cells): the zone is split into
+    sub x sub sub-cells in (x1, x2) and the sub-cell centres with r = exp(x1) < R are counted.
+    sub = 0: 1 for zones whose centre lies inside, else 0 (an abrupt edge)."""
+    X1, X2, _ = _zone_centres(g)
+    if sub == 0:
+        return (np.exp(X1) < R).astype(float)
+    off = (np.arange(sub) + 0.5) / sub - 0.5
+    x1s = X1[:, None] + off[None, :] * g["dx1"]
+    # a sphere's edge depends on r only, so the x2 sub-cells repeat the same count sub times
+    inside = (np.exp(x1s) < R).sum(axis=1) * sub
+    return inside / float(sub * sub)
+
+
 def sphere(metric: str = "ks", *, R: float = 10.0, n1: int = 1024, n2: int = 128,
            ne: float = 1e13, thetae: float = 10.0, B_gauss: float = 10.0,
            m_bh_msun: float = 4e6, L_unit: float | None = None, r_in: float | None = None,
-           dh: float = 0.05, **over):
+           dh: float = 0.05, r_out: float | None = None, partial: int = 0, **over):
     """Uniform static sphere with a vertical magnetic field (section 4.1 set-up).
 
     ``metric='ks'``: Schwarzschild (a = 0) in Kerr-Schild form with the hole at the
@@ -82,6 +96,9 @@ def sphere(metric: str = "ks", *, R: float = 10.0, n1: int = 1024, n2: int = 128
     strength ``B_gauss`` along the static frame's vertical direction.
     ``metric='flat'``: Minkowski space (the paper's analytic test), grid ln r in
     [ln r_in, ln R].
+    ``r_out`` > R extends the grid beyond the sphere (the paper's 10^4 cm), with no gas outside
+    R: rho and u of each zone are scaled by its inside fraction (``inside_fraction`` with
+    ``partial`` sub-cells per side; 0 = the zone centre decides), which keeps Theta_e.
     Density and temperature: rho = 1 with M_unit chosen so that n_e = ``ne``;
     R_high = R_low = 1 and u/rho chosen so the temperature model gives ``thetae``.
     """
@@ -92,7 +109,8 @@ def sphere(metric: str = "ks", *, R: float = 10.0, n1: int = 1024, n2: int = 128
         r0 = r_in if r_in is not None else 1e-3 * R
     else:
         r0 = 2.0 * (1.0 + dh)
-    g = _grid(n1, n2, 1, math.log(r0), math.log(R))
+    r1 = R if r_out is None else r_out
+    g = _grid(n1, n2, 1, math.log(r0), math.log(r1))
     X1, X2, _ = _zone_centres(g)
     r = np.exp(X1)
     th = math.pi * X2
@@ -121,6 +139,10 @@ def sphere(metric: str = "ks", *, R: float = 10.0, n1: int = 1024, n2: int = 128
         # b^r = B0 cos th f^1/2, b^th = -B0 sin th / r  ->  B^r = B0 cos th, B^th = -B0 sin th / (r f^1/2)
         prim[2] = B0 * np.cos(th) / r
         prim[3] = -B0 * np.sin(th) / (r * np.sqrt(f)) / math.pi
+    if r1 > R:
+        frac = inside_fraction(g, R, partial)
+        prim[0] *= frac
+        prim[1] *= frac
     params = base_params(
         mass=0.0 if flat else 1.0, a=0.0, hslope=1.0, L_unit=L_unit, M_unit=M_unit,
         R_high=1.0, R_low=1.0, dh=dh)
