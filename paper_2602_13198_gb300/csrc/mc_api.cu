@@ -476,12 +476,13 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
   if (use_sur && !c->sur_ready) return fail(c, MC_ERR_STATE, "surrogate requested but no trained weights");
   SurrogateView sv;
   std::memset(&sv, 0, sizeof(sv));
-  // >= 56 KB of shared memory per CTA: at most four CTAs (4 x 128 TMEM columns) per SM
-  const int sur_smem = std::max(kTcSmemBytes, 56 * 1024);
+  // two 128-row groups of the network per CTA (tensor-memory kernels run one CTA per SM)
+  const int sur_block = 128 * kTcGroupsMax;
+  const int sur_smem = tc_smem_bytes(kTcGroupsMax);
   int occ_sur = 1;
   if (use_sur) {
     sv = surrogate_view(c);
-    occ_sur = std::max(1, std::min(4, push_sur_max_blocks_per_sm(128, sur_smem)));
+    occ_sur = std::max(1, std::min(4, push_sur_max_blocks_per_sm(sur_block, sur_smem)));
     if (c->p.ctas_per_sm > 0) occ_sur = std::min(occ_sur, (int)c->p.ctas_per_sm);
     CU(cudaMemsetAsync(c->sur_err, 0, sizeof(unsigned int), st));
   }
@@ -535,7 +536,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
           pio.list_out = c->list_free;
           pio.out_counter = CNT_L1;   // continues after the n_free entries already listed
           if (use_sur) {
-            int grid = (int)std::min<int64_t>((int64_t)c->sms * occ_sur, (n_grid + 127) / 128);
+            int grid = (int)std::min<int64_t>((int64_t)c->sms * occ_sur, (n_grid + sur_block - 1) / sur_block);
             TIMED_LAUNCH(1, launch_push_sur(m, pio, sv, grid, sur_smem, st));
           } else {
             int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[0], (n_grid + block - 1) / block);

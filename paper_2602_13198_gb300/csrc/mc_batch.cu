@@ -163,7 +163,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
 }
 
 template <bool MIXED, bool SUR, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_batch(BatchIO b) {
+__global__ void __launch_bounds__(SUR ? 256 : 128, MINB) k_batch(BatchIO b) {
   __shared__ DevModel sm[kMaxBatch];
   __shared__ int64_t soff[kMaxBatch + 1];
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -286,7 +286,7 @@ __global__ void k_batch_offsets(const int64_t *const *totals, int n, int64_t *pr
 typedef void (*BatchKernel)(BatchIO);
 
 static BatchKernel pick_kernel(bool mixed, bool sur, int minb) {
-  if (sur) return minb == 1 ? k_batch<true, true, 1> : k_batch<true, true, 2>;
+  if (sur) return k_batch<true, true, 1>;   // tensor-memory kernels run one CTA per SM
   if (mixed) return minb == 1 ? k_batch<true, false, 1> : k_batch<true, false, 3>;
   return minb == 1 ? k_batch<false, false, 1> : k_batch<false, false, 3>;
 }
@@ -458,15 +458,15 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
   if (sur) b.sv = surrogate_view(c0);
   b.timeout_ns = 120e9;
   BatchKernel kern = pick_kernel(mixed, sur, minb);
-  int smem = sur ? std::max(kTcSmemBytes, 40 * 1024) : 0;
+  int smem = sur ? tc_smem_bytes(kTcGroupsMax) : 0;
   if (smem) {
     cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    // shared memory over L1 so that two CTAs of ~92 KB fit on an SM
+    // shared memory over L1: a CTA with two network row groups needs ~127 KB
     cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
   void *args[] = {&b};
   if (timed) cudaEventRecord(bs->e0, st);
-  e = cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(128), args, smem, st);
+  e = cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(sur ? 128 * kTcGroupsMax : 128), args, smem, st);
   if (timed) cudaEventRecord(bs->e1, st);
   return e;
 }
@@ -474,15 +474,15 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
 static int max_ctas(mc_ctx *c0, int minb) {
   const bool mixed = c0->p.precision == MC_PREC_MIXED, sur = c0->p.surrogate == 1;
   BatchKernel kern = pick_kernel(mixed, sur, minb);
-  int smem = sur ? std::max(kTcSmemBytes, 40 * 1024) : 0;
+  int smem = sur ? tc_smem_bytes(kTcGroupsMax) : 0;
   if (smem) {
     cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    // shared memory over L1 so that two CTAs of ~92 KB fit on an SM
+    // shared memory over L1: a CTA with two network row groups needs ~127 KB
     cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)kern, 128, smem);
-  if (sur) n = std::min(n, 4);   // four CTAs x 128 TMEM columns fill an SM's tensor memory
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)kern, sur ? 128 * kTcGroupsMax : 128, smem);
+  if (sur) n = std::min(n, 4);   // at most four CTAs x 128 TMEM columns per SM
   return std::max(n, 0);
 }
 
@@ -534,8 +534,9 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
     const double frac = std::min(1.0, std::max(0.05, 5e6 / ns_tot));
     for (int i = 0; i < n; ++i) ns_small[i] = std::max(1.0, frac * n_s[i]);
     double best = 1e300;
-    const int minbs[2] = {1, (c0->p.surrogate == 1) ? 2 : 3};
+    const int minbs[2] = {1, 3};
     for (int mb : minbs) {
+      if (mb != 1 && c0->p.surrogate == 1) continue;   // one launch-bounds variant with the network
       int mx = max_ctas(c0, mb);
       for (int per = 1; per <= mx; ++per) {
         int ctas = per * c0->sms;

@@ -373,7 +373,7 @@ int mc_surrogate_infer(mc_ctx *c, const float *x, float *y, int64_t n, int tenso
     cudaMemset(c->sur_err, 0, sizeof(unsigned int));
     if (tensor_cores) {
       // >= 56 KB of shared memory per CTA keeps at most four CTAs (4 x 128 TMEM columns) on an SM
-      int sm = kTcSmemBytes > 56 * 1024 ? kTcSmemBytes : 56 * 1024;
+      int sm = tc_smem_bytes(1);
       cudaFuncSetAttribute(k_sur_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
       k_sur_infer_tc<<<(unsigned)((n + 127) / 128), 128, sm>>>(surrogate_view(c), dx, dy, n);
     } else {

@@ -126,23 +126,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // Per-CTA state of the tensor-core MLP: shared-memory tiles, TMEM base, mbarrier and its phase.
+// A CTA of 128 x G threads evaluates G groups of 128 rows (G = 1 or 2); group g has its own A tiles
+// and accumulates in TMEM columns [64 g, 64 g + 64).  The tensor-memory kernels run one CTA per SM,
+// so two groups are how an SM gets eight warps of the surrogate transport.
+constexpr int kTcGroupsMax = 2;
 struct TcMlp {
-  unsigned char *a1, *a2, *a2l, *b1, *b2, *b2l, *b3, *b3l;   // shared-memory tiles
+  unsigned char *a1[kTcGroupsMax], *a2[kTcGroupsMax], *a2l[kTcGroupsMax];   // per-group A tiles
+  unsigned char *b1, *b2, *b2l, *b3, *b3l;                                  // shared weight tiles
   const float *bias;                        // b1 b2 b3 in shared memory
   uint32_t tmem, mbar, phase;
+  int groups;
   unsigned int *err;
 };
 
-// Shared memory needed by one CTA (tiles + biases + mbarrier + TMEM address slot).
-constexpr int kTcSmemBytes = kTileA1 + 2 * kTileA2 + kPackedBytes + 4 * (64 + 64 + 16) + 64;
+// Shared memory needed by one CTA of `groups` row groups (tiles + biases + mbarrier + TMEM slot).
+__host__ __device__ constexpr int tc_smem_bytes(int groups) {
+  return groups * (kTileA1 + 2 * kTileA2) + kPackedBytes + 4 * (64 + 64 + 16) + 64;
+}
 
-// Set-up by all 128 threads of the CTA: carve shared memory, copy packed weights and biases,
-// initialise the mbarrier, warp 0 allocates kTmemCols TMEM columns.
+// Set-up by all threads of the CTA (blockDim.x = 128 or 256): carve shared memory, copy packed
+// weights and biases, initialise the mbarrier, warp 0 allocates kTmemCols TMEM columns.
 __device__ __forceinline__ void tc_setup(TcMlp &T, unsigned char *smem, const SurrogateView &sv) {
-  T.a1 = smem;
-  T.a2 = T.a1 + kTileA1;
-  T.a2l = T.a2 + kTileA2;
-  T.b1 = T.a2l + kTileA2;
+  const int G = (int)(blockDim.x >> 7);
+  T.groups = G;
+  unsigned char *q = smem;
+  for (int g = 0; g < G; ++g) { T.a1[g] = q; q += kTileA1; }
+  for (int g = 0; g < G; ++g) { T.a2[g] = q; q += kTileA2; }
+  for (int g = 0; g < G; ++g) { T.a2l[g] = q; q += kTileA2; }
+  for (int g = G; g < kTcGroupsMax; ++g) T.a1[g] = T.a2[g] = T.a2l[g] = nullptr;
+  T.b1 = q;
   T.b2 = T.b1 + kTileB1;
   T.b2l = T.b2 + kTileB2;
   T.b3 = T.b2l + kTileB2;
@@ -175,9 +187,10 @@ __device__ __forceinline__ void tc_teardown(TcMlp &T) {
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(T.tmem, kTmemCols);
 }
 
-// One layer: D[128 x N] = sum over the np (A, B) pairs of A[128 x K] B[N x K]^T in TMEM columns
-// [0, N), issued by thread 0; returns after every thread has seen the MMAs complete.
-__device__ __forceinline__ bool tc_layer(TcMlp &T, const unsigned char *const *as, const unsigned char *const *bs,
+// One layer: for every row group g, D_g[128 x N] = sum over the np (A, B) pairs of A_g[128 x K] B[N x K]^T
+// in TMEM columns [64 g, 64 g + N), issued by thread 0; returns after every thread has seen the
+// MMAs complete.
+__device__ __forceinline__ bool tc_layer(TcMlp &T, const unsigned char *const (*as)[3], const unsigned char *const *bs,
                                          int np, int K, int N) {
   fence_async_smem();
   tc_fence_before();
@@ -186,13 +199,15 @@ __device__ __forceinline__ bool tc_layer(TcMlp &T, const unsigned char *const *a
   if (threadIdx.x == 0) {
     const uint32_t sbo = (K / 8) * 128;
     const uint32_t id = idesc_bf16(128, N);
-    for (int p = 0; p < np; ++p) {
-      const uint32_t ab = smem_addr(as[p]), bb = smem_addr(bs[p]);
-      for (int k = 0; k < K / 16; ++k) {
-        // advancing 16 elements along K = two core matrices = 256 bytes
-        uint64_t da = umma_desc(ab + k * 256, 128, sbo);
-        uint64_t db = umma_desc(bb + k * 256, 128, sbo);
-        tc_mma(T.tmem, da, db, id, (p > 0 || k > 0) ? 1u : 0u);
+    for (int g = 0; g < T.groups; ++g) {
+      for (int p = 0; p < np; ++p) {
+        const uint32_t ab = smem_addr(as[g][p]), bb = smem_addr(bs[p]);
+        for (int k = 0; k < K / 16; ++k) {
+          // advancing 16 elements along K = two core matrices = 256 bytes
+          uint64_t da = umma_desc(ab + k * 256, 128, sbo);
+          uint64_t db = umma_desc(bb + k * 256, 128, sbo);
+          tc_mma(T.tmem + 64u * g, da, db, id, (p > 0 || k > 0) ? 1u : 0u);
+        }
       }
     }
     tc_commit(T.mbar);
@@ -208,9 +223,9 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16(v - __bfloat162float(hi));
 }
 
-// Writes 64 activations of this thread's row as hi/lo BF16 rows of A2 / A2lo (two values per
-// conversion: element 2q in the low half of each packed pair, as in memory order).
-__device__ __forceinline__ void put_hidden(TcMlp &T, int row, const float *h) {
+// Writes 64 activations of this thread's row as hi/lo BF16 rows of its group's A2 / A2lo (two
+// values per conversion: element 2q in the low half of each packed pair, as in memory order).
+__device__ __forceinline__ void put_hidden(TcMlp &T, int grp, int row, const float *h) {
 #pragma unroll
   for (int c = 0; c < 64; c += 8) {
     __nv_bfloat162 hi[4], lo[4];
@@ -221,16 +236,17 @@ __device__ __forceinline__ void put_hidden(TcMlp &T, int row, const float *h) {
       const float2 back = __bfloat1622float2(hi[q]);
       lo[q] = __floats2bfloat162_rn(a - back.x, b - back.y);
     }
-    *(uint4 *)(T.a2 + kmajor_off(row, c, 64)) = *(uint4 *)hi;
-    *(uint4 *)(T.a2l + kmajor_off(row, c, 64)) = *(uint4 *)lo;
+    *(uint4 *)(T.a2[grp] + kmajor_off(row, c, 64)) = *(uint4 *)hi;
+    *(uint4 *)(T.a2l[grp] + kmajor_off(row, c, 64)) = *(uint4 *)lo;
   }
 }
 
-// Evaluates the network for this thread's row (all 128 threads of the CTA must call it).
+// Evaluates the network for this thread's row (all threads of the CTA must call it).
 // in[3]: normalised inputs; out[3]: raw outputs.  Returns false if a wait timed out.
 __device__ __forceinline__ bool tc_mlp_eval(TcMlp &T, const float in[3], float out[3]) {
-  const int row = threadIdx.x;
-  const uint32_t lane_base = (uint32_t)((threadIdx.x >> 5) * 32) << 16;
+  const int grp = threadIdx.x >> 7, row = threadIdx.x & 127;
+  // TMEM lanes of this warp (warp w reads lanes 32 (w mod 4) ...) and this group's columns
+  const uint32_t tbase = T.tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16) + 64u * grp;
   // layer 1 operand: [x_hi(3) | x_hi(3) | x_lo(3) | 0 ...] against [W1_hi | W1_lo | W1_hi]
   {
     __nv_bfloat16 v[16];
@@ -244,28 +260,30 @@ __device__ __forceinline__ bool tc_mlp_eval(TcMlp &T, const float in[3], float o
       v[3 + q] = hi;
       v[6 + q] = lo;
     }
-    *(uint4 *)(T.a1 + kmajor_off(row, 0, 16)) = *(uint4 *)v;
-    *(uint4 *)(T.a1 + kmajor_off(row, 8, 16)) = *(uint4 *)(v + 8);
+    *(uint4 *)(T.a1[grp] + kmajor_off(row, 0, 16)) = *(uint4 *)v;
+    *(uint4 *)(T.a1[grp] + kmajor_off(row, 8, 16)) = *(uint4 *)(v + 8);
   }
-  const unsigned char *a_l1[1] = {T.a1}, *b_l1[1] = {T.b1};
+  const unsigned char *a_l1[kTcGroupsMax][3] = {{T.a1[0], nullptr, nullptr}, {T.a1[1], nullptr, nullptr}};
+  const unsigned char *b_l1[1] = {T.b1};
   bool ok = tc_layer(T, a_l1, b_l1, 1, 16, 64);
   float h[64];
 #pragma unroll
-  for (int c = 0; c < 64; c += 16) tmem_ld16(T.tmem + lane_base + c, h + c);
+  for (int c = 0; c < 64; c += 16) tmem_ld16(tbase + c, h + c);
 #pragma unroll
   for (int c = 0; c < 64; ++c) h[c] = silu_f(h[c] + T.bias[c]);
-  put_hidden(T, row, h);
-  const unsigned char *a_l2[3] = {T.a2, T.a2l, T.a2}, *b_l2[3] = {T.b2, T.b2, T.b2l};
+  put_hidden(T, grp, row, h);
+  const unsigned char *a_l2[kTcGroupsMax][3] = {{T.a2[0], T.a2l[0], T.a2[0]}, {T.a2[1], T.a2l[1], T.a2[1]}};
+  const unsigned char *b_l2[3] = {T.b2, T.b2, T.b2l};
   ok = tc_layer(T, a_l2, b_l2, 3, 64, 64) && ok;
 #pragma unroll
-  for (int c = 0; c < 64; c += 16) tmem_ld16(T.tmem + lane_base + c, h + c);
+  for (int c = 0; c < 64; c += 16) tmem_ld16(tbase + c, h + c);
 #pragma unroll
   for (int c = 0; c < 64; ++c) h[c] = silu_f(h[c] + T.bias[64 + c]);
-  put_hidden(T, row, h);   // the layer-2 MMAs have completed, so A2 may be overwritten
-  const unsigned char *a_l3[3] = {T.a2, T.a2l, T.a2}, *b_l3[3] = {T.b3, T.b3, T.b3l};
-  ok = tc_layer(T, a_l3, b_l3, 3, 64, 16) && ok;
+  put_hidden(T, grp, row, h);   // the layer-2 MMAs have completed, so A2 may be overwritten
+  const unsigned char *b_l3[3] = {T.b3, T.b3, T.b3l};
+  ok = tc_layer(T, a_l2, b_l3, 3, 64, 16) && ok;
   float y[16];
-  tmem_ld16(T.tmem + lane_base, y);
+  tmem_ld16(tbase, y);
   out[0] = y[0] + T.bias[128];
   out[1] = y[1] + T.bias[129];
   out[2] = y[2] + T.bias[130];

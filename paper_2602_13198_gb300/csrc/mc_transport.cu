@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
 // Persistent in-grid push with the network; every thread of the CTA reaches the same tensor-core
 // evaluation once per iteration (idle lanes contribute a zero row), and the loop ends for the
 // whole CTA together.
-__global__ void __launch_bounds__(128) k_push_sur(DevModel m, PushIO io, SurrogateView sv) {
+__global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, PushIO io, SurrogateView sv) {
   extern __shared__ __align__(128) unsigned char smem_sur[];
   TcMlp T;
   tc_setup(T, smem_sur, sv);
@@ -188,7 +188,7 @@ int push_sur_max_blocks_per_sm(int block, int smem) {
 }
 
 void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &sv, int grid, int smem, cudaStream_t st) {
-  k_push_sur<<<grid, 128, smem, st>>>(m, io, sv);
+  k_push_sur<<<grid, 128 * kTcGroupsMax, smem, st>>>(m, io, sv);
 }
 
 int push_max_blocks_per_sm(int mixed, int phase, int block) {
