@@ -72,6 +72,9 @@ typedef struct mc_model_params {
   double lnu_lo, lnu_hi;   /* spectrum range, log10(nu/Hz) */
   double roulette_w, roulette_p;  /* Russian roulette when w < roulette_w * w_birth, survival roulette_p */
   double bias_max;     /* upper bound on the bias b (any b >= 1 leaves the estimate unbiased) */
+  double bias_target;  /* > 0: tune the bias per scattering generation on the fly so that each
+                          generation produces about bias_target scattered superphotons per
+                          superphoton it carries (mc_run only); 0: the bias as configured */
   int64_t max_steps;   /* drop a superphoton after this many steps */
   int32_t n_nu;        /* weight-table nodes in ln nu (>= 2) */
   int32_t verlet_maxit;/* cap on Verlet predictor iterations */
@@ -163,6 +166,14 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g);
 int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards, void *stream,
            mc_run_stats *stats);
 
+/* Bias scales s_g (g = 0 .. n_sc_max) of the last mc_run: generation g scatters with
+ * b = clamp(s_g b_0, 1, bias_max), b_0 the configured bias.  s_0 = 1; with bias_target > 0, after
+ * generation g of the first batch of primaries, s_{g+1} = s_g clamp(bias_target / r_g, 1/8, 8) with
+ * r_g = (children produced) / (superphotons carried) (8 when r_g = 0); later batches and
+ * mc_trace reuse the sequence.  Without tuning every s_g = 1.  Errors: STATE (no run),
+ * SIZE (n != n_sc_max + 1). */
+int mc_get_bias_scales(mc_ctx *c, double *scales, int n);
+
 /* Spectrum of the last mc_run: nu L_nu [erg/s] per (inclination, frequency) bin, its Monte
  * Carlo standard error, and the superphoton count, each n_incl*n_bins host doubles
  * (inclination-major).  Any pointer may be NULL.  Errors: SIZE if n_elems != n_incl*n_bins. */
@@ -179,7 +190,9 @@ int mc_get_zone_counts(mc_ctx *c, int64_t *counts, size_t n_elems);
 /* Transports only the listed primaries (host array of uids of the job defined by N_s and
  * seed) and their descendants, writing one mc_log_rec per finished superphoton to the host
  * buffer `out` (capacity `cap`, number written in *n_out).  The spectrum sums of these
- * superphotons replace the context's.  Errors: SIZE (uid out of range), STATE, CUDA. */
+ * superphotons replace the context's.  With bias tuning the generations scatter with the bias
+ * scales of the context's last mc_run (see mc_get_bias_scales), so a trace after a run of the same
+ * job follows the run's histories.  Errors: SIZE (uid out of range), STATE, CUDA. */
 int mc_trace(mc_ctx *c, double n_s, uint64_t seed, const int64_t *uids, size_t n_uids, mc_log_rec *out,
              size_t cap, size_t *n_out, void *stream);
 

@@ -38,6 +38,7 @@ class Params(C.Structure):
         ("r_record", C.c_double), ("dh", C.c_double), ("bias_p0", C.c_double),
         ("lnu_lo", C.c_double), ("lnu_hi", C.c_double),
         ("roulette_w", C.c_double), ("roulette_p", C.c_double), ("bias_max", C.c_double),
+        ("bias_target", C.c_double),
         ("max_steps", C.c_int64),
         ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32),
         ("n_sc_max", C.c_int32), ("n_bins", C.c_int32), ("n_incl", C.c_int32),
@@ -128,6 +129,7 @@ def lib():
         L.or_get_zone.argtypes = [C.c_void_p, P(I64), PD, PD, PD]
         L.or_get_weights.argtypes = [C.c_void_p, PD]
         L.or_run.argtypes = [C.c_void_p, I64, I64, P(I64), I64, PD, P(Stats), C.c_void_p, I64, P(I64), C.c_int]
+        L.or_get_bias_scales.argtypes = [C.c_void_p, PD, C.c_int]
         _lib = L
     return _lib
 
@@ -306,6 +308,12 @@ class Model:
         lib().or_fluid(self._h, _pd(X), _pd(out))
         return {"ne": out[0], "thetae": out[1], "B": out[2], "plasma": bool(out[3]),
                 "ucon": out[4:8].copy(), "bcon": out[8:12].copy()}
+
+    def bias_scales(self):
+        """Bias scale per scattering generation of the last range run."""
+        out = np.empty(int(self.cfg["n_sc_max"]) + 1)
+        lib().or_get_bias_scales(self._h, _pd(out), len(out))
+        return out
 
     def run(self, uid0=0, uid1=None, uids=None, nthreads=None, log=False, log_cap=None):
         c = self.cfg

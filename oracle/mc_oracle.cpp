@@ -147,6 +147,7 @@ struct or_params {
   double lnu_lo, lnu_hi;       // spectrum range, log10(nu / Hz)
   double roulette_w, roulette_p;
   double bias_max;             // upper bound on b (reading: any b >= 1 keeps the estimate unbiased)
+  double bias_target;          // > 0: per-generation bias tuning (reading), 0: off
   int64_t max_steps;
   int32_t n_nu;                // weight-table nodes
   int32_t verlet_maxit;
@@ -782,6 +783,11 @@ struct Model {
   int64_t total = 0;
   uint64_t seed = 0;
   double r_h = 0.0;
+  std::vector<double> bscale;        // bias scale per scattering generation (last full run)
+  double scale_of(int nsc) const {
+    if (bscale.empty()) return 1.0;
+    return bscale[std::min((size_t)nsc, bscale.size() - 1)];
+  }
 };
 
 void zone_center(const Model &M, int64_t z, double X[4]) {
@@ -875,12 +881,25 @@ void coefficients(const Model &M, const double X[4], const double K[4], bool wan
   }
 }
 
-double bias_of(const or_params &P, double thetae, int nsc) {
+// Bias b >= 1 (section 2.7): the configured form b_0, clamped to [1, bias_max], times the scale of
+// the superphoton's generation, clamped again.
+double bias_of(const or_params &P, double thetae, int nsc, double scale) {
   double b;
   if (P.bias_mode == 1) b = P.bias_p0 * (nsc + 1.0) * (nsc + 1.0);
   else if (P.bias_mode == 2) b = P.bias_p0 * thetae * thetae;
   else b = P.bias_p0;
-  return std::max(1.0, std::min(b, P.bias_max));
+  const double b0 = std::max(1.0, std::min(b, P.bias_max));
+  return std::max(1.0, std::min(scale * b0, P.bias_max));
+}
+
+// Bias tuning (reading; the paper names it as future work): the next generation's scale from this
+// generation's scattered superphotons per superphoton carried, r: s' = s clamp(target / r, 1/8, 8),
+// 8 when r = 0, at most 1e12.
+double tune_next_scale(double s, int64_t carried, int64_t children, double target) {
+  double r = carried > 0 ? (double)children / (double)carried : 0.0;
+  double f = r > 0.0 ? target / r : 8.0;
+  f = std::min(8.0, std::max(0.125, f));
+  return std::min(1e12, s * f);
 }
 
 // ---------------------------------------------------------------- transport (sections 2.4-2.7, 3)
@@ -1009,7 +1028,7 @@ void transport(const Model &M, Photon &p, std::vector<Child> &stack, Acc &acc) {
     if (scat) {
       double tau_s = 0.5 * (p.ans + c.ans) * C * dl;
       if (tau_s > 0.0) {
-        double b = bias_of(P, c.thetae, p.nsc);
+        double b = bias_of(P, c.thetae, p.nsc, M.scale_of(p.nsc));
         double d = b * tau_s;
         if (p.acc + d > p.x1t) {
           double f = (p.x1t - p.acc) / d;
@@ -1363,7 +1382,9 @@ void or_get_weights(void *h, double *lnw) {
 
 // Run primaries [uid0, uid1) (or the explicit uid list when uids != NULL) with all their
 // descendants; accumulate the spectrum sums [n_incl][n_bins][3] and counters.  With a log
-// buffer, every finished superphoton appends its end state.
+// buffer, every finished superphoton appends its end state.  A range run resets the bias scales
+// (and tunes them when bias_target > 0); a uid-list run scatters with the scales of the last
+// range run.
 int or_run(void *h, int64_t uid0, int64_t uid1, const int64_t *uids, int64_t nuids, double *spec, or_stats *st,
            or_log *logbuf, int64_t log_cap, int64_t *log_n, int nthreads) {
   Model &M = *(Model *)h;
@@ -1377,6 +1398,53 @@ int or_run(void *h, int64_t uid0, int64_t uid1, const int64_t *uids, int64_t nui
     std::memset(&a.st, 0, sizeof(a.st));
     a.want_log = (logbuf != nullptr);
   }
+  const bool tuning = P.bias_target > 0.0 && uids == nullptr;
+  if (uids == nullptr) M.bscale.assign(P.n_sc_max + 1, 1.0);
+  if (tuning) {
+    // generation by generation (the bias of a generation depends on the previous ones), in
+    // batches of 2^24 primaries as the device path runs them; the first batch sets the scales
+    const int64_t kBatch = (int64_t)1 << 24;
+    const int n_gen = P.n_sc_max + 1;
+    for (int64_t b0 = 0; b0 < n; b0 += kBatch) {
+      const int64_t nb = std::min(kBatch, n - b0);
+      std::vector<Child> cur, next;
+      for (int gen = 0;; ++gen) {
+        const int64_t n_items = gen == 0 ? nb : (int64_t)cur.size();
+        if (n_items == 0) break;
+        next.clear();
+#pragma omp parallel num_threads(nthreads)
+        {
+          int tid = 0;
+#ifdef _OPENMP
+          tid = omp_get_thread_num();
+#endif
+          Acc &acc = accs[tid];
+          std::vector<Child> local;
+#pragma omp for schedule(dynamic, 16)
+          for (int64_t q = 0; q < n_items; ++q) {
+            Photon p;
+            if (gen == 0) {
+              emit(M, uid0 + b0 + q, p, &acc.st.n_rej_cap);
+              acc.st.n_emit++;
+            } else {
+              const Child &c = cur[q];
+              for (int m = 0; m < 4; ++m) { p.X[m] = c.X[m]; p.K[m] = c.K[m]; }
+              p.w = c.w;
+              p.nsc = c.nsc;
+              p.s = Stream{M.seed, c.id, c.ctr};
+            }
+            init_transport(M, p);
+            transport(M, p, local, acc);
+          }
+#pragma omp critical
+          next.insert(next.end(), local.begin(), local.end());
+        }
+        if (b0 == 0 && gen + 1 < n_gen)
+          M.bscale[gen + 1] = tune_next_scale(M.bscale[gen], n_items, (int64_t)next.size(), P.bias_target);
+        cur.swap(next);
+      }
+    }
+  } else
 #pragma omp parallel num_threads(nthreads)
   {
     int tid = 0;
@@ -1417,6 +1485,12 @@ int or_run(void *h, int64_t uid0, int64_t uid1, const int64_t *uids, int64_t nui
         if (nl < log_cap) logbuf[nl++] = L;
   }
   if (log_n) *log_n = nl;
+  return 0;
+}
+
+int or_get_bias_scales(void *h, double *out, int n) {
+  Model &M = *(Model *)h;
+  for (int g = 0; g < n; ++g) out[g] = M.scale_of(g);
   return 0;
 }
 

@@ -120,6 +120,7 @@ DevModel make_model(const mc_ctx *c) {
   m.bias_mode = p.bias_mode;
   m.bias_p0 = p.bias_p0;
   m.bias_max = p.bias_max;
+  m.bias_scale = 1.0;
   m.n_sc_max = p.n_sc_max;
   m.scatter = p.scatter;
   m.k2_mode = p.k2_mode;
@@ -181,6 +182,7 @@ static int check_params(const mc_model_params *p, std::string &why) {
   if (p->n_incl * (int64_t)p->n_bins > (1 << 24)) return bad("too many spectrum bins");
   if (p->bias_mode < 0 || p->bias_mode > 2) return bad("bias_mode must be 0, 1 or 2");
   if (!(p->bias_max >= 1.0)) return bad("bias_max must be >= 1");
+  if (!(p->bias_target >= 0.0 && p->bias_target < 1e30)) return bad("bias_target must be >= 0");
   if (p->n_sc_max < 0 || p->n_sc_max > 1000) return bad("n_sc_max out of range");
   if (!(p->roulette_p > 0.0 && p->roulette_p <= 1.0) || !(p->roulette_w >= 0.0)) return bad("bad roulette");
   if (p->max_steps < 1 || p->max_steps > 2000000000LL) return bad("max_steps out of range");
@@ -461,10 +463,22 @@ static int set_counter(mc_ctx *c, int idx, unsigned long long v, cudaStream_t st
 // Transports primaries [u0, u1) (or the uid list) and all their descendants: per batch and per
 // scattering generation, k_init fills the pool, then the in-grid and free push phases alternate
 // until no superphoton of the generation is left.
+// Next generation's bias scale from this generation's children per superphoton (see
+// mc_get_bias_scales in mc.h).
+static double tune_next_scale(double s, int64_t carried, int64_t children, double target) {
+  const double r = carried > 0 ? (double)children / (double)carried : 0.0;
+  double f = r > 0.0 ? target / r : 8.0;
+  f = std::min(8.0, std::max(0.125, f));
+  return std::min(1e12, s * f);
+}
+
 static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_dev, int64_t n_list, mc_log_rec *log_dev,
-                     int64_t log_cap, uint64_t seed, cudaStream_t st) {
+                     int64_t log_cap, uint64_t seed, cudaStream_t st, bool tune) {
   DevModel m = make_model(c);
   m.seed = seed;
+  const int n_gen = c->p.n_sc_max + 1;
+  if (tune || (int)c->bscale.size() != n_gen) c->bscale.assign(n_gen, 1.0);
+  const bool tuning = tune && c->p.bias_target > 0.0;
   const int block = c->p.block ? c->p.block : 128;
   const int mixed = c->p.precision == MC_PREC_MIXED;
   int occ[2];
@@ -511,6 +525,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
     int64_t n_items = nb;
     while (n_items > 0) {
       if (n_items > c->qcap) return fail(c, MC_ERR_QUEUE_OVERFLOW, "generation larger than the superphoton pool");
+      m.bias_scale = c->bscale[std::min(gen, n_gen - 1)];
       iio.n_items = n_items;
       if (gen == 0) {
         iio.mode = uid_list_dev ? 1 : 0;
@@ -564,7 +579,10 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
           if (rc) return rc;
         }
       }
-      n_items = (int64_t)c->cnt_host[CNT_OUT];
+      const int64_t children = (int64_t)c->cnt_host[CNT_OUT];
+      if (tuning && b0 == 0 && gen + 1 < n_gen)
+        c->bscale[gen + 1] = tune_next_scale(c->bscale[gen], n_items, children, c->p.bias_target);
+      n_items = children;
       ++gen;
     }
   }
@@ -612,7 +630,7 @@ int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards
     c->t_transport = 0.0;
     c->t_phase[0] = c->t_phase[1] = c->t_phase[2] = 0.0;
     c->n_launch = 0;
-    rc = transport(c, u0, u1, nullptr, 0, nullptr, 0, seed, st);
+    rc = transport(c, u0, u1, nullptr, 0, nullptr, 0, seed, st, true);
     if (rc != MC_ERR_QUEUE_OVERFLOW || attempt == 3) break;
     int64_t need = (int64_t)c->cnt_host[CNT_OUT];   // slots the overflowing generation asked for
     int64_t want = std::max<int64_t>(need + need / 2, 2 * c->qcap);
@@ -657,7 +675,7 @@ int mc_trace(mc_ctx *c, double n_s, uint64_t seed, const int64_t *uids, size_t n
     dev_free(c, ld);
     return fail(c, MC_ERR_CUDA, cudaGetErrorString(e));
   }
-  rc = (n_uids > 0) ? transport(c, 0, 0, ud, (int64_t)n_uids, ld, (int64_t)cap, seed, st) : MC_OK;
+  rc = (n_uids > 0) ? transport(c, 0, 0, ud, (int64_t)n_uids, ld, (int64_t)cap, seed, st, false) : MC_OK;
   if (rc == MC_OK) {
     size_t n = std::min<size_t>((size_t)c->cnt_host[CNT_LOG], cap);
     e = cudaMemcpyAsync(out, ld, sizeof(mc_log_rec) * n, cudaMemcpyDeviceToHost, st);
@@ -717,6 +735,14 @@ int mc_fma_peak(int device, int dtype, double *flops) {
   cudaError_t e = fma_peak(dtype == MC_DTYPE_F64, &f);
   if (e != cudaSuccess) return fail(nullptr, MC_ERR_CUDA, cudaGetErrorString(e));
   *flops = f;
+  return MC_OK;
+}
+
+int mc_get_bias_scales(mc_ctx *c, double *scales, int n) {
+  if (!c || !scales) return fail(c, MC_ERR_INVALID_ARG, "null argument");
+  if (!c->have_run || (int)c->bscale.size() != c->p.n_sc_max + 1) return fail(c, MC_ERR_STATE, "no run yet");
+  if (n != c->p.n_sc_max + 1) return fail(c, MC_ERR_SIZE, "scales buffer must hold n_sc_max + 1 elements");
+  for (int g = 0; g < n; ++g) scales[g] = c->bscale[g];
   return MC_OK;
 }
 

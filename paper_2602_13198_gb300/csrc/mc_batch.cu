@@ -499,6 +499,7 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
         ctxs[i]->p.surrogate != c0->p.surrogate)
       return set_err(c0, MC_ERR_INVALID_ARG, "models of a batch share device, precision and surrogate mode");
     if (ctxs[i]->p.n_sc_max + 2 > kMaxGen) return set_err(c0, MC_ERR_INVALID_ARG, "n_sc_max too large for a batch");
+    if (ctxs[i]->p.bias_target > 0.0) return set_err(c0, MC_ERR_INVALID_ARG, "bias tuning runs in mc_run only");
   }
   if (c0->p.surrogate == 1 && !c0->sur_ready) return set_err(c0, MC_ERR_STATE, "surrogate requested but no weights");
   if (cudaSetDevice(c0->p.device) != cudaSuccess) return set_err(c0, MC_ERR_CUDA, "cudaSetDevice failed");

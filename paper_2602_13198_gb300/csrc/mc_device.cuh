@@ -47,6 +47,7 @@ struct DevModel {
   double eps_geo, verlet_tol, r_record, r_capture;
   int verlet_maxit, bias_mode, n_sc_max, scatter, k2_mode;
   double bias_p0, bias_max, roulette_w, roulette_p;
+  double bias_scale;   // multiplies the configured bias of the generation being transported
   int64_t max_steps;
   // record
   double lnu_lo, dlog_bin;
@@ -748,7 +749,8 @@ __device__ __forceinline__ double bias_of(const DevModel &m, double thetae, int 
   if (m.bias_mode == 1) b = m.bias_p0 * (nsc + 1.0) * (nsc + 1.0);
   else if (m.bias_mode == 2) b = m.bias_p0 * thetae * thetae;
   else b = m.bias_p0;
-  return fmax(1.0, fmin(b, m.bias_max));
+  const double b0 = fmax(1.0, fmin(b, m.bias_max));
+  return fmax(1.0, fmin(m.bias_scale * b0, m.bias_max));   // = b0 at scale 1
 }
 
 // ---------------------------------------------------------------- tetrads (sections 2.1, 2.7)

@@ -114,6 +114,7 @@ struct mc_ctx {
   int nF = 0, nK2 = 0;
   // grid
   bool have_grid = false;
+  std::vector<double> bscale;   // bias scale per scattering generation (last mc_run)
   uint64_t grid_epoch = 0;   // bumped by every mc_set_grid (captured batch graphs hold grid pointers)
   void *prim = nullptr;
   float *prim_x32 = nullptr;   // FP32 copy of an FP64 grid, read by the mixed-precision transport

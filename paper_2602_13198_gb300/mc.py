@@ -40,6 +40,7 @@ class ModelParams(C.Structure):
         ("eps_geo", C.c_double), ("verlet_tol", C.c_double), ("r_record", C.c_double), ("dh", C.c_double),
         ("bias_p0", C.c_double), ("lnu_lo", C.c_double), ("lnu_hi", C.c_double),
         ("roulette_w", C.c_double), ("roulette_p", C.c_double), ("bias_max", C.c_double),
+        ("bias_target", C.c_double),
         ("max_steps", C.c_int64),
         ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32), ("n_sc_max", C.c_int32),
         ("n_bins", C.c_int32), ("n_incl", C.c_int32), ("k2_mode", C.c_int32), ("scatter", C.c_int32),
@@ -108,6 +109,8 @@ def lib():
         L.mc_version.restype = C.c_char_p
         L.mc_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
         L.mc_fma_peak.restype = C.c_int
+        L.mc_get_bias_scales.argtypes = [vp, C.POINTER(C.c_double), C.c_int]
+        L.mc_get_bias_scales.restype = C.c_int
         L.mc_selftest_math.argtypes = [C.c_int, vp, vp, vp, C.c_int64]
         L.mc_selftest_math.restype = C.c_int
         L.mc_run_batch.argtypes = [C.POINTER(vp), C.c_int, dp, C.POINTER(u64), C.c_int, vp, C.POINTER(RunStats)]
@@ -174,6 +177,7 @@ class Model:
         self._h = h
         self.n_incl = int(params["n_incl"])
         self.n_bins = int(params["n_bins"])
+        self.n_sc_max = int(params["n_sc_max"])
         self.nz = 0
 
     def close(self):
@@ -231,6 +235,12 @@ class Model:
                                           cnt.ctypes.data_as(dp), n))
         sh = (self.n_incl, self.n_bins)
         return nuL.reshape(sh), sig.reshape(sh), cnt.reshape(sh)
+
+    def bias_scales(self):
+        """Bias scale per scattering generation of the last run (mc_get_bias_scales)."""
+        out = np.zeros(self.n_sc_max + 1)
+        self._check(lib().mc_get_bias_scales(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), len(out)))
+        return out
 
     def spectrum_sums(self):
         n = self.n_incl * self.n_bins * 3
