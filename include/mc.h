@@ -89,7 +89,7 @@ typedef struct mc_model_params {
   int32_t block;       /* threads per CTA of the transport kernel (0: default 128) */
   int32_t ctas_per_sm; /* resident CTAs per SM for the persistent launch (0: occupancy maximum) */
   int32_t device;      /* CUDA device ordinal */
-  int32_t pad0;
+  int32_t brems;       /* 1: add thermal bremsstrahlung emission and absorption (not with the surrogate) */
   mc_alloc_fn alloc;   /* optional device allocator (NULL: cudaMalloc) */
   mc_free_fn free;
   void *alloc_user;

@@ -42,7 +42,7 @@ class Params(C.Structure):
         ("max_steps", C.c_int64),
         ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32),
         ("n_sc_max", C.c_int32), ("n_bins", C.c_int32), ("n_incl", C.c_int32),
-        ("k2_mode", C.c_int32), ("scatter", C.c_int32),
+        ("k2_mode", C.c_int32), ("scatter", C.c_int32), ("brems", C.c_int32),
     ]
 
 
@@ -130,6 +130,12 @@ def lib():
         L.or_get_weights.argtypes = [C.c_void_p, PD]
         L.or_run.argtypes = [C.c_void_p, I64, I64, P(I64), I64, PD, P(Stats), C.c_void_p, I64, P(I64), C.c_int]
         L.or_get_bias_scales.argtypes = [C.c_void_p, PD, C.c_int]
+        L.or_brems_q.argtypes = [D, D]
+        L.or_brems_q.restype = D
+        L.or_brems_angint.argtypes = [P(Params), D, D, D]
+        L.or_brems_angint.restype = D
+        L.or_brems_nu_alpha.argtypes = [P(Params), D, D, D]
+        L.or_brems_nu_alpha.restype = D
         _lib = L
     return _lib
 
@@ -228,6 +234,20 @@ def Fang(K):
 def jnu_angint(cfg, nu, ne, thetae, B):
     p = params_from(cfg)
     return lib().or_jnu_angint(C.byref(p), nu, ne, thetae, B)
+
+
+def brems_q(ne, thetae):
+    return lib().or_brems_q(ne, thetae)
+
+
+def brems_angint(cfg, nu, ne, thetae):
+    p = params_from(cfg)
+    return lib().or_brems_angint(C.byref(p), nu, ne, thetae)
+
+
+def brems_nu_alpha(cfg, nu, ne, thetae):
+    p = params_from(cfg)
+    return lib().or_brems_nu_alpha(C.byref(p), nu, ne, thetae)
 
 
 def sigma_kn(e):

@@ -156,6 +156,7 @@ struct or_params {
   int32_t n_bins, n_incl;
   int32_t k2_mode;             // 0: exact K2(1/Theta); 1: K2 ~ 2 Theta^2
   int32_t scatter;             // 0: Compton scattering off
+  int32_t brems;               // 1: thermal bremsstrahlung emission and absorption (reading)
 };
 
 struct or_grid {
@@ -493,6 +494,46 @@ double jnu_angint(const or_params &P, double nu, double ne, double thetae, doubl
   double nuc = nu_c_of(thetae, B);
   double A = std::sqrt(2.0) * PI * EE * EE * ne / (3.0 * CL * K2_of(P, thetae));
   return 4.0 * PI * A * nuc * Fang(nu / nuc);
+}
+
+// ---------------------------------------------------------------- bremsstrahlung (future work in section 6)
+// Thermal bremsstrahlung of a hydrogen plasma (reading): total cooling rate q = q_ei + q_ee
+// [erg s^-1 cm^-3] from the fits of Stepney & Guilbert (1983) in the form of Narayan & Yi (1995),
+//   q_ei = 1.25 n_e n_i sigma_T c alpha_f m_e c^2 F_ei(Theta),
+//     F_ei = 4 (2 Theta / pi^3)^1/2 (1 + 1.781 Theta^1.34)           (Theta < 1)
+//          = 9 Theta / (2 pi) (ln(1.123 Theta + 0.48) + 1.5)          (Theta >= 1),
+//   q_ee = n_e^2 c r_e^2 alpha_f m_e c^2 (20 / 9 sqrt(pi)) (44 - 3 pi^2) Theta^3/2
+//          (1 + 1.1 Theta + Theta^2 - 1.25 Theta^5/2)                  (Theta < 1)
+//        = n_e^2 c r_e^2 alpha_f m_e c^2 24 Theta (ln(1.1232 Theta) + 1.28)   (Theta >= 1),
+// n_i = n_e, and an isotropic spectrum 4 pi j_nu = q (h / k T) exp(-h nu / k T) (a flat Gaunt shape
+// normalised to q); absorption by Kirchhoff's law, alpha_nu = j_nu / B_nu.
+const double ALPHA_F = 7.2973525693e-3;    // fine-structure constant
+const double R_E = 2.8179403262e-13;       // classical electron radius [cm]
+
+double brems_q(double ne, double th) {
+  const double mc2 = ME * CL * CL;
+  double fei = th < 1.0 ? 4.0 * std::sqrt(2.0 * th / (PI * PI * PI)) * (1.0 + 1.781 * std::pow(th, 1.34))
+                        : 9.0 * th / (2.0 * PI) * (std::log(1.123 * th + 0.48) + 1.5);
+  double qei = 1.25 * ne * ne * SIGMA_T * CL * ALPHA_F * mc2 * fei;
+  double fee = th < 1.0 ? 20.0 / (9.0 * std::sqrt(PI)) * (44.0 - 3.0 * PI * PI) * std::pow(th, 1.5) *
+                              (1.0 + 1.1 * th + th * th - 1.25 * std::pow(th, 2.5))
+                        : 24.0 * th * (std::log(1.1232 * th) + 1.28);
+  double qee = ne * ne * CL * R_E * R_E * ALPHA_F * mc2 * fee;
+  return qei + qee;
+}
+
+// int dOmega j_nu = 4 pi j_nu of the bremsstrahlung (0 when off)
+double brems_angint(const or_params &P, double nu, double ne, double th) {
+  if (!P.brems || ne <= 0.0 || th <= 0.0) return 0.0;
+  const double kt = th * ME * CL * CL;
+  return brems_q(ne, th) * HPL / kt * std::exp(-HPL * nu / kt);
+}
+
+// nu alpha_nu = nu j_nu / B_nu = q c^2 (1 - exp(-h nu / k T)) / (8 pi k T nu^2)
+double brems_nu_alpha(const or_params &P, double nu, double ne, double th) {
+  if (!P.brems || ne <= 0.0 || th <= 0.0) return 0.0;
+  const double kt = th * ME * CL * CL;
+  return brems_q(ne, th) * CL * CL * (-std::expm1(-HPL * nu / kt)) / (8.0 * PI * kt * nu * nu);
 }
 
 // ---------------------------------------------------------------- Compton (section 2.7)
@@ -875,6 +916,7 @@ void coefficients(const Model &M, const double X[4], const double K[4], bool wan
   }
   double j = jnu(M.P, nu, c.F.ne, c.F.thetae, c.F.B, cth);
   if (j > 0.0) c.ana = nu * j / bnu(nu, c.F.thetae);
+  c.ana += brems_nu_alpha(M.P, nu, c.F.ne, c.F.thetae);
   if (want_scatter) {
     double th = std::max(c.F.thetae, 1e-300);
     c.ans = nu * c.F.ne * hot_table().lookup(th, eps);
@@ -1135,27 +1177,38 @@ void emit(const Model &M, int64_t uid, Photon &p, int64_t *rejcap) {
   gcov_at(P, X, g);
   Fluid F;
   fluid_from_prims(P, M.un, pr, g, F);
-  double jmax = jnu(P, nu, F.ne, F.thetae, F.B, 0.0);
+  const double jsyn = jnu_angint(P, nu, F.ne, F.thetae, F.B), jbr = brems_angint(P, nu, F.ne, F.thetae);
+  // with bremsstrahlung on, the emitting process is drawn in proportion to the two
+  // angle-integrated emissivities; the bremsstrahlung direction is isotropic
+  bool synchrotron = true;
+  if (P.brems) synchrotron = uniform(p.s) * (jsyn + jbr) < jsyn;
   double cth = 0.0;
-  for (it = 0; it < 100000; ++it) {
-    double r3 = uniform(p.s);
-    cth = 2.0 * r3 - 1.0;
-    double r4 = uniform(p.s);
-    if (r4 * jmax < jnu(P, nu, F.ne, F.thetae, F.B, cth)) break;
+  if (synchrotron) {
+    double jmax = jnu(P, nu, F.ne, F.thetae, F.B, 0.0);
+    for (it = 0; it < 100000; ++it) {
+      double r3 = uniform(p.s);
+      cth = 2.0 * r3 - 1.0;
+      double r4 = uniform(p.s);
+      if (r4 * jmax < jnu(P, nu, F.ne, F.thetae, F.B, cth)) break;
+    }
+    if (it == 100000) (*rejcap)++;
+  } else {
+    cth = 2.0 * uniform(p.s) - 1.0;
   }
-  if (it == 100000) (*rejcap)++;
   double phi = 2.0 * PI * uniform(p.s);
   double sth = std::sqrt(std::max(0.0, 1.0 - cth * cth));
   double eps = HPL * nu / (ME * CL * CL);
   double e[4][4];
-  tetrad_emission(g, F, e);
+  // without a field (a bremsstrahlung-only plasma) the frame of the scattering tetrad serves
+  if (F.bsq > 0.0) tetrad_emission(g, F, e);
+  else tetrad_scatter(g, F, e);
   double kf[4] = {eps, eps * sth * std::cos(phi), eps * sth * std::sin(phi), eps * cth};
   for (int m = 0; m < 4; ++m) {
     p.X[m] = X[m];
     p.K[m] = kf[0] * e[0][m] + kf[1] * e[1][m] + kf[2] * e[2][m] + kf[3] * e[3][m];
   }
   // superphoton weight: int dOmega j_nu at the drawn nu over the interpolated target
-  p.w = glin > 0.0 ? jnu_angint(P, nu, F.ne, F.thetae, F.B) / glin : 0.0;
+  p.w = glin > 0.0 ? (jsyn + jbr) / glin : 0.0;
   p.nsc = 0;
 }
 
@@ -1187,7 +1240,10 @@ int prepare(Model &M, double n_s, uint64_t seed) {
       fluid_from_prims(P, M.un, pr, g, F);
       Zone zz{F.ne, F.thetae, F.B};
       if (!(zz.ne == last.ne && zz.thetae == last.thetae && zz.B == last.B)) {
-        for (int j = 0; j < M.nnu; ++j) row[j] = jnu_angint(P, std::exp(M.lnumin + j * M.dlnu), zz.ne, zz.thetae, zz.B);
+        for (int j = 0; j < M.nnu; ++j) {
+          const double nuj = std::exp(M.lnumin + j * M.dlnu);
+          row[j] = jnu_angint(P, nuj, zz.ne, zz.thetae, zz.B) + brems_angint(P, nuj, zz.ne, zz.thetae);
+        }
         last = zz;
       }
       for (int j = 0; j < M.nnu; ++j) M.g[(size_t)z * M.nnu + j] = row[j];
@@ -1486,6 +1542,14 @@ int or_run(void *h, int64_t uid0, int64_t uid1, const int64_t *uids, int64_t nui
   }
   if (log_n) *log_n = nl;
   return 0;
+}
+
+double or_brems_q(double ne, double thetae) { return brems_q(ne, thetae); }
+double or_brems_angint(const or_params *P, double nu, double ne, double thetae) {
+  return brems_angint(*P, nu, ne, thetae);
+}
+double or_brems_nu_alpha(const or_params *P, double nu, double ne, double thetae) {
+  return brems_nu_alpha(*P, nu, ne, thetae);
 }
 
 int or_get_bias_scales(void *h, double *out, int n) {

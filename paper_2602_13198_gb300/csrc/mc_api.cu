@@ -151,6 +151,9 @@ DevModel make_model(const mc_ctx *c) {
   m.prim64 = c->prim_f32 ? nullptr : (const double *)c->prim;
   m.prim32 = c->prim_f32 ? (const float *)c->prim : nullptr;
   m.prim32x = c->prim_f32 ? (const float *)c->prim : c->prim_x32;
+  m.brems = p.brems;
+  m.zbq = c->zbq;
+  m.zbnt = c->zbnt;
   m.lnF = c->lnF;
   m.nF = c->nF;
   m.lnK2 = c->lnK2;
@@ -183,6 +186,8 @@ static int check_params(const mc_model_params *p, std::string &why) {
   if (p->bias_mode < 0 || p->bias_mode > 2) return bad("bias_mode must be 0, 1 or 2");
   if (!(p->bias_max >= 1.0)) return bad("bias_max must be >= 1");
   if (!(p->bias_target >= 0.0 && p->bias_target < 1e30)) return bad("bias_target must be >= 0");
+  if (p->brems != 0 && p->brems != 1) return bad("brems must be 0 or 1");
+  if (p->brems && p->surrogate) return bad("the coefficient surrogate does not model bremsstrahlung");
   if (p->n_sc_max < 0 || p->n_sc_max > 1000) return bad("n_sc_max out of range");
   if (!(p->roulette_p > 0.0 && p->roulette_p <= 1.0) || !(p->roulette_w >= 0.0)) return bad("bad roulette");
   if (p->max_steps < 1 || p->max_steps > 2000000000LL) return bad("max_steps out of range");
@@ -295,10 +300,11 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   size_t esz = (g->dtype == MC_DTYPE_F32) ? 4 : 8;
   // free per-grid buffers
   void *old[] = {c->prim, c->prim_x32, c->zvol, c->zpref, c->zlnuc, c->zgmax, c->znbar, c->counts, c->start, c->bsum,
-                 c->partial};
+                 c->partial, c->zbq, c->zbnt};
   for (void *ptr : old) dev_free(c, ptr);
   c->prim = nullptr;
   c->prim_x32 = nullptr;
+  c->zbq = c->zbnt = nullptr;
   c->have_grid = false;
   c->have_run = false;
   c->n1 = g->n1; c->n2 = g->n2; c->n3 = g->n3; c->nz = nz;
@@ -317,6 +323,11 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   c->partial = (double *)dev_alloc(c, 8 * (size_t)c->nchunks * c->p.n_nu);
   if (!c->prim || !c->zvol || !c->zpref || !c->zlnuc || !c->zgmax || !c->znbar || !c->counts || !c->start || !c->bsum || !c->partial)
     return fail(c, MC_ERR_OOM, "grid allocation failed");
+  if (c->p.brems) {
+    c->zbq = (double *)dev_alloc(c, 8 * nz);
+    c->zbnt = (double *)dev_alloc(c, 8 * nz);
+    if (!c->zbq || !c->zbnt) return fail(c, MC_ERR_OOM, "grid allocation failed");
+  }
   const void *src = g->prim;
   void *staging = nullptr;
   if (g->location == MC_LOC_HOST) {

@@ -69,6 +69,8 @@ struct DevModel {
   // per-run generation data
   const int64_t *start;   // exclusive scan of zone counts
   const double *zpref;    // 4 pi A nu_c per zone (int dOmega j_nu = zpref F(nu/nu_c))
+  int brems;              // thermal bremsstrahlung on
+  double *zbq, *zbnt;     // per zone: q / nu_T and nu_T = k T_e / h (bremsstrahlung only)
   const double *zlnuc;    // ln nu_c per zone
   const double *zgmax;    // max_j g_ij per zone
   const double *lnw;      // ln w_j (n_nu)
@@ -390,6 +392,40 @@ __device__ __forceinline__ double pow_sixth(double X) {
   return X * (z2 * z2 * z);
 }
 
+// ---------------------------------------------------------------- bremsstrahlung (future work in section 6)
+// Total thermal bremsstrahlung cooling rate of a hydrogen plasma [erg s^-1 cm^-3], electron-ion plus
+// electron-electron, from the fits of Stepney & Guilbert (1983) in the form of Narayan & Yi (1995);
+// the spectrum is 4 pi j_nu = q (h / k T) exp(-h nu / k T) and absorption follows Kirchhoff's law.
+__device__ __forceinline__ double brems_q(double ne, double th) {
+  constexpr double kAlphaF = 7.2973525693e-3, kRe = 2.8179403262e-13, kMc2 = kME * kCL * kCL;
+  double fei, fee;
+  if (th < 1.0) {
+    fei = 4.0 * sqrt(2.0 * th / (kPI * kPI * kPI)) * (1.0 + 1.781 * pow(th, 1.34));
+    fee = 20.0 / (9.0 * sqrt(kPI)) * (44.0 - 3.0 * kPI * kPI) * th * sqrt(th) *
+          (1.0 + 1.1 * th + th * th - 1.25 * th * th * sqrt(th));
+  } else {
+    fei = 9.0 * th / (2.0 * kPI) * (log(1.123 * th + 0.48) + 1.5);
+    fee = 24.0 * th * (log(1.1232 * th) + 1.28);
+  }
+  return ne * ne * kAlphaF * kMc2 * kCL * (1.25 * kSIGT * fei + kRe * kRe * fee);
+}
+
+// nu alpha_nu = nu j_nu / B_nu = q c^2 (1 - exp(-h nu / k T)) / (8 pi k T nu^2)
+__device__ __forceinline__ double brems_nu_alpha(double ne, double th, double nu) {
+  if (!(ne > 0.0 && th > 0.0)) return 0.0;
+  const double kt = th * kME * kCL * kCL;
+  return brems_q(ne, th) * kCL * kCL * (-expm1(-kHPL * nu / kt)) / (8.0 * kPI * kt * nu * nu);
+}
+
+// int dOmega j_nu of zone z at weight-table node j: synchrotron (pref F(nu/nu_c); 0 when the zone
+// has no synchrotron) plus, when on, bremsstrahlung (q / nu_T) exp(-nu / nu_T).
+__device__ __forceinline__ double F_of_lnK(const DevModel &m, double lnK);
+__device__ __forceinline__ double zone_E(const DevModel &m, int64_t z, double pref, double lnuc, int j) {
+  double e = (pref == 0.0) ? 0.0 : pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc);
+  if (m.brems && m.zbq[z] > 0.0) e += m.zbq[z] * exp(-exp(m.lnu_min + j * m.dlnu) / m.zbnt[z]);
+  return e;
+}
+
 // ---------------------------------------------------------------- synchrotron (section 2.2)
 // G(X) = (X^1/2 + 2^11/12 X^1/6)^2 exp(-X^1/3)
 __device__ __forceinline__ double Gsyn(double X) {
@@ -625,6 +661,7 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
       }
     }
   }
+  if (m.brems) c.ana += brems_nu_alpha(P.ne, P.thetae, nu);
   if (want_s) c.ans = nu * P.ne * hot_lookup_ln(m, lt, log(eps));
 }
 
@@ -665,6 +702,8 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, 
     }
   }
   c.ana = (double)ana;
+  // bremsstrahlung absorption in FP64 (n_e^2 leaves the FP32 range in dense plasma)
+  if (m.brems) c.ana += brems_nu_alpha((double)P.ne, (double)P.thetae, (double)nu9 * 1e9);
   if (want_s) {
     float sh = hot_lookup_f(m, fmaxf(P.thetae, 1e-30f), eps);
     c.ans = (double)(nu9 * P.ne * (sh * 1e9f));

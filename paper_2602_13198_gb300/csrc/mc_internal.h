@@ -118,6 +118,7 @@ struct mc_ctx {
   uint64_t grid_epoch = 0;   // bumped by every mc_set_grid (captured batch graphs hold grid pointers)
   void *prim = nullptr;
   float *prim_x32 = nullptr;   // FP32 copy of an FP64 grid, read by the mixed-precision transport
+  double *zbq = nullptr, *zbnt = nullptr;   // per-zone bremsstrahlung normalisation and k T_e / h
   int prim_f32 = 0;
   int n1 = 0, n2 = 0, n3 = 0;
   int64_t nz = 0;

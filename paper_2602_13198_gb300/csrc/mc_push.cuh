@@ -66,25 +66,35 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
     double fj = (lnu - m.lnu_min) / m.dlnu;
     int j = min(max((int)floor(fj), 0), m.n_nu - 2);
     double fr = fj - j;
-    double g0 = pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc) * m.winv[j];
-    double g1 = pref * F_of_lnK(m, m.lnu_min + (j + 1) * m.dlnu - lnuc) * m.winv[j + 1];
+    double g0 = zone_E(m, z, pref, lnuc, j) * m.winv[j];
+    double g1 = zone_E(m, z, pref, lnuc, j + 1) * m.winv[j + 1];
     glin = (1.0 - fr) * g0 + fr * g1;
     double r2 = rng_u(p.s, m.seed);
     if (r2 * gm < glin) break;
   }
   if (it == 100000) ls.rejcap++;
-  // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
-  double K0 = exp(lnu - lnuc);
-  double jmax = Gsyn(K0);
+  const double jsyn = (pref == 0.0) ? 0.0 : pref * F_of_lnK(m, lnu - lnuc);
+  const double jbr = (m.brems && m.zbq[z] > 0.0) ? m.zbq[z] * exp(-exp(lnu) / m.zbnt[z]) : 0.0;
+  // with bremsstrahlung on, the process is drawn in proportion to the two angle-integrated
+  // emissivities; bremsstrahlung is isotropic
+  bool synchrotron = true;
+  if (m.brems) synchrotron = rng_u(p.s, m.seed) * (jsyn + jbr) < jsyn;
   double cth = 0.0;
-  for (it = 0; it < 100000; ++it) {
-    double r3 = rng_u(p.s, m.seed);
-    cth = 2.0 * r3 - 1.0;
-    double r4 = rng_u(p.s, m.seed);
-    double sth = sqrt(1.0 - cth * cth);
-    if (r4 * jmax < sth * Gsyn(K0 / sth)) break;
+  if (synchrotron) {
+    // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
+    double K0 = exp(lnu - lnuc);
+    double jmax = Gsyn(K0);
+    for (it = 0; it < 100000; ++it) {
+      double r3 = rng_u(p.s, m.seed);
+      cth = 2.0 * r3 - 1.0;
+      double r4 = rng_u(p.s, m.seed);
+      double sth = sqrt(1.0 - cth * cth);
+      if (r4 * jmax < sth * Gsyn(K0 / sth)) break;
+    }
+    if (it == 100000) ls.rejcap++;
+  } else {
+    cth = 2.0 * rng_u(p.s, m.seed) - 1.0;
   }
-  if (it == 100000) ls.rejcap++;
   double phi = 2.0 * rng_u(p.s, m.seed);   // units of pi
   double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
   double eps = exp(lnu) * (kHPL / (kME * kCL * kCL));
@@ -103,7 +113,9 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
   double ucon[4], bcon[4];
   plasma_from_prims<double>(m, G, pr, P, ucon, bcon);
   double e[4][4];
-  tetrad_emission(G, ucon, bcon, P.bsq, e);
+  // without a field (a bremsstrahlung-only plasma) the frame of the scattering tetrad serves
+  if (P.bsq > 0.0) tetrad_emission(G, ucon, bcon, P.bsq, e);
+  else tetrad_scatter(G, ucon, e);
   double sp, cp;
   sincospi(phi, &sp, &cp);
   double kf[4] = {eps, eps * sth * cp, eps * sth * sp, eps * cth};
@@ -114,7 +126,7 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
   }
   // weight w(nu) g(nu) / g_lin(nu) = int dOmega j_nu(nu) / g_lin(nu): the proposal follows the
   // piecewise-linear target, the weight restores the zone's exact dN/dln(nu) (section 2.3)
-  p.w = glin > 0.0 ? pref * F_of_lnK(m, lnu - lnuc) / glin : 0.0;
+  p.w = glin > 0.0 ? (jsyn + jbr) / glin : 0.0;
   p.nsc = 0;
 }
 

@@ -134,17 +134,19 @@ __global__ void k_zone_prep(DevModel m, double *zvol, double *zpref, double *zln
   }
   zpref[z] = pref;
   zlnuc[z] = lnuc;
+  if (m.brems) {
+    // int dOmega j_nu = (q / nu_T) exp(-nu / nu_T), nu_T = k T_e / h
+    const double nut = P.thetae * (kME * kCL * kCL / kHPL);
+    const bool on = P.ne > 0.0 && P.thetae > 0.0;
+    m.zbnt[z] = on ? nut : 1.0;
+    m.zbq[z] = on ? brems_q(P.ne, P.thetae) / nut : 0.0;
+  }
 }
 
 void launch_zone_prep(const DevModel &m, double *zvol, double *zpref, double *zlnuc, int *bad, cudaStream_t st) {
   k_zone_prep<<<(unsigned)((m.nz + 127) / 128), 128, 0, st>>>(m, zvol, zpref, zlnuc, bad);
 }
 
-// int dOmega j_nu at node j for a zone (0 when the zone does not emit)
-__device__ __forceinline__ double zone_E(const DevModel &m, double pref, double lnuc, int j) {
-  if (pref == 0.0) return 0.0;
-  return pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc);
-}
 
 constexpr int kChunk = 2048;
 
@@ -158,7 +160,7 @@ __global__ void k_weight_partial(DevModel m, const double *zvol, const double *z
   double s = 0.0;
   for (int q = threadIdx.x; q < kChunk; q += blockDim.x) {
     int64_t z = z0 + q;
-    if (z < m.nz) s += zvol[z] * zone_E(m, zpref[z], zlnuc[z], j);
+    if (z < m.nz) s += zvol[z] * zone_E(m, z, zpref[z], zlnuc[z], j);
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -197,9 +199,9 @@ __global__ void k_zone_counts(DevModel m, const double *zvol, const double *zpre
   if (z >= m.nz) return;
   double pref = zpref[z], lnuc = zlnuc[z];
   double s = 0.0, gm = 0.0;
-  if (pref != 0.0) {
+  if (pref != 0.0 || (m.brems && m.zbq[z] > 0.0)) {
     for (int j = 0; j < m.n_nu; ++j) {
-      double g = zone_E(m, pref, lnuc, j) * m.winv[j];
+      double g = zone_E(m, z, pref, lnuc, j) * m.winv[j];
       double t = (j == 0 || j == m.n_nu - 1) ? 0.5 * m.dlnu : m.dlnu;
       s += t * g;
       gm = fmax(gm, g);

@@ -45,7 +45,7 @@ class ModelParams(C.Structure):
         ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32), ("n_sc_max", C.c_int32),
         ("n_bins", C.c_int32), ("n_incl", C.c_int32), ("k2_mode", C.c_int32), ("scatter", C.c_int32),
         ("precision", C.c_int32), ("surrogate", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
-        ("device", C.c_int32), ("pad0", C.c_int32),
+        ("device", C.c_int32), ("brems", C.c_int32),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
     ]
 
