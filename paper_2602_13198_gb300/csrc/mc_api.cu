@@ -494,7 +494,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
   const int mixed = c->p.precision == MC_PREC_MIXED;
   int occ[2];
   for (int ph = 0; ph < 2; ++ph) {
-    occ[ph] = std::max(1, push_max_blocks_per_sm(mixed, ph, block));
+    occ[ph] = std::max(1, push_max_blocks_per_sm(mixed, ph, block, m.a != 0.0 ? 1 : 0));
     if (c->p.ctas_per_sm > 0) occ[ph] = std::min(occ[ph], (int)c->p.ctas_per_sm);
   }
   const bool use_sur = c->p.surrogate == 1;

@@ -172,9 +172,10 @@ __device__ __forceinline__ void sincos_small(double d, double &s, double &c) {
 // Metric, inverse metric and (DERIV) x1/x2 derivatives at (x1, x2).  theta = pi x2 + delta with
 // delta = (1-h)/2 sin(2 pi x2): sin and cos of theta come from sincospi(x2) and the series of the
 // small angle delta (|delta| < 1/2 for h in (0, 1]) by angle addition.
-template <bool DERIV>
+// KERR = false: the a = 0 (Schwarzschild) form, with the terms that vanish at a = 0 left out.
+template <bool DERIV, bool KERR = true>
 __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double x2, Geo &G) {
-  const double a = m.a, M = m.mass, a2 = a * a;
+  const double a = KERR ? m.a : 0.0, M = m.mass, a2 = a * a;
   double r = exp(x1);
   double sp, cp;
   sincospi(x2, &sp, &cp);
@@ -195,7 +196,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
     c = cp * cd - sp * sd;
   }
   double s2 = s * s, c2 = c * c;
-  double sig = r * r + a2 * c2;
+  double sig = KERR ? r * r + a2 * c2 : r * r;
   // one division for 1/Sigma, 1/r, 1/sin^2 and 1/(dtheta/dx2)
   const double rs = r * s2;
   double Q = 1.0 / (sig * rs * dth);
@@ -204,8 +205,9 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
   double f = 2.0 * M * r * isig;
   double opf = 1.0 + f;
   // Kerr-Schild components (t, r, theta, phi)
-  double Gtt = f - 1.0, Gtr = f, Gtp = -a * f * s2, Grr = opf, Grp = -a * s2 * opf, Ghh = sig;
-  double Gpp = s2 * (sig + a2 * s2 * opf);
+  double Gtt = f - 1.0, Gtr = f, Grr = opf, Ghh = sig;
+  double Gtp = KERR ? -a * f * s2 : 0.0, Grp = KERR ? -a * s2 * opf : 0.0;
+  double Gpp = KERR ? s2 * (sig + a2 * s2 * opf) : s2 * sig;
   G.r = r;
   G.sth = s;
   G.cth = c;
@@ -220,13 +222,27 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
   // g^thth = 1/Sigma, g^phph = 1/(Sigma sin^2); divided by the Jacobian factors
   G.G00 = -opf;
   G.G01 = f * ir;
-  G.G11 = (r * r - 2.0 * M * r + a2) * isig * ir * ir;
-  G.G13 = a * isig * ir;
+  G.G11 = (KERR ? r * r - 2.0 * M * r + a2 : r * r - 2.0 * M * r) * isig * ir * ir;
+  G.G13 = KERR ? a * isig * ir : 0.0;
   G.G22 = isig * idth * idth;
   G.G33 = isig * is2;
   if (!DERIV) return;
   // derivatives of the KS components with respect to r and theta
   double dfr = 2.0 * M * (sig - 2.0 * r * r) * isig * isig;
+  if constexpr (!KERR) {
+    // a = 0: f, g_tr, g_rr depend on r only; g_thth = r^2, g_phph = r^2 sin^2
+    G.d100 = r * dfr;
+    G.d101 = r * (r * dfr + Gtr);
+    G.d103 = 0.0;
+    G.d111 = r * r * (r * dfr + 2.0 * Grr);
+    G.d113 = 0.0;
+    G.d122 = r * (2.0 * r) * dth * dth;
+    G.d133 = r * (2.0 * r * s2);
+    G.d200 = G.d201 = G.d203 = G.d211 = G.d213 = 0.0;
+    G.d222 = Ghh * 2.0 * dth * d2th;
+    G.d233 = dth * (2.0 * s * c * sig);
+    return;
+  }
   double dft = 4.0 * M * r * a2 * s * c * isig * isig;
   double dGtp_r = -a * s2 * dfr, dGtp_t = -a * (dft * s2 + 2.0 * f * s * c);
   double dGrp_r = -a * s2 * dfr, dGrp_t = -a * (2.0 * s * c * opf + s2 * dft);
@@ -265,7 +281,28 @@ __device__ __forceinline__ double dot(const Geo &G, const double a[4], const dou
 }
 
 // dk^mu/dlambda = -Gamma^mu_ab k^a k^b = -g^{mu nu} (k^1 (d1 g k)_nu + k^2 (d2 g k)_nu - 1/2 d_nu g_ab k^a k^b)
+template <bool KERR = true>
 __device__ __forceinline__ void accel(const Geo &G, const double k[4], double A[4]) {
+  if constexpr (!KERR) {
+    // a = 0: d103 = d113 = d2(0,1,3) = G13 = 0
+    double p0 = G.d100 * k[0] + G.d101 * k[1];
+    double p1 = G.d101 * k[0] + G.d111 * k[1];
+    double p2 = G.d122 * k[2];
+    double p3 = G.d133 * k[3];
+    double q2 = G.d222 * k[2];
+    double q3 = G.d233 * k[3];
+    double kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
+    double kDk2 = k[2] * q2 + k[3] * q3;
+    double w0 = k[1] * p0;
+    double w1 = k[1] * p1 - 0.5 * kDk1;
+    double w2 = k[1] * p2 + k[2] * q2 - 0.5 * kDk2;
+    double w3 = k[1] * p3 + k[2] * q3;
+    A[0] = -(G.G00 * w0 + G.G01 * w1);
+    A[1] = -(G.G01 * w0 + G.G11 * w1);
+    A[2] = -(G.G22 * w2);
+    A[3] = -(G.G33 * w3);
+    return;
+  }
   double p0 = G.d100 * k[0] + G.d101 * k[1] + G.d103 * k[3];
   double p1 = G.d101 * k[0] + G.d111 * k[1] + G.d113 * k[3];
   double p2 = G.d122 * k[2];

@@ -91,7 +91,7 @@ void launch_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, in
 cudaError_t fma_peak(bool fp64, double *flops);
 cudaError_t selftest_math(int which, const double *x_dev, double *y_dev, double *ref_dev, int64_t n);
 // transport (mc_transport.cu)
-int push_max_blocks_per_sm(int mixed, int phase, int block);
+int push_max_blocks_per_sm(int mixed, int phase, int block, int kerr);
 void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st);
 // phase 0: superphotons inside the radial extent of the grid; 1: outside it
 void launch_push(const DevModel &m, const PushIO &io, int mixed, int phase, int grid, int block, cudaStream_t st);

@@ -29,18 +29,18 @@ __device__ __forceinline__ void coefs(const DevModel &m, const Geo &G, const dou
   else coefficients64(m, G, X, K, ws, c);
 }
 
-template <bool MIXED>
+template <bool MIXED, bool KERR = true>
 static __device__ void init_transport(const DevModel &m, Ph &p) {
   p.x1t = -log(rng_u(p.s, m.seed));
   p.acc = 0.0;
   bool scat = m.scatter && p.nsc < m.n_sc_max;
   Geo G;
-  metric_eval<true>(m, p.X[1], p.X[2], G);
+  metric_eval<true, KERR>(m, p.X[1], p.X[2], G);
   Coef c;
   coefs<MIXED>(m, G, p.X, p.K, scat, c);
   p.ana = c.ana;
   p.ans = c.ans;
-  accel(G, p.K, p.A);
+  accel<KERR>(G, p.K, p.A);
   p.nsteps = 0;
   p.nev = 0;
   p.wb = p.w;
@@ -222,7 +222,7 @@ static __device__ void write_log(const PushIO &io, const Ph &p, int status) {
 }
 
 // One geodesic step with absorption, scattering and the termination tests; false when finished.
-template <bool MIXED>
+template <bool MIXED, bool KERR = true>
 static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
   const bool scat = m.scatter && p.nsc < m.n_sc_max;
   double dl = stepsize(m, p.X, p.K);
@@ -235,12 +235,12 @@ static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalSta
     Kp[q] = K0[q] + p.A[q] * dl;
   }
   Geo G;
-  metric_eval<true>(m, p.X[1], p.X[2], G);
+  metric_eval<true, KERR>(m, p.X[1], p.X[2], G);
   int it = 0;
   bool conv = false;
   double Kn[4];
   while (true) {
-    accel(G, Kp, An);
+    accel<KERR>(G, Kp, An);
     double num = 0.0, den = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -341,6 +341,7 @@ static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalSta
 // weight is unchanged): the same Verlet arithmetic and termination tests as step().  If the new
 // point lies inside the grid the step is discarded (state untouched) and 2 is returned, so the
 // in-grid phase redoes it with the coefficients.  Returns 0 to continue, 1 when finished.
+template <bool KERR = true>
 static __device__ int step_free(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
   double dl = stepsize(m, p.X, p.K);
   double Xn[4], Kp[4], An[4], Kn[4];
@@ -351,11 +352,11 @@ static __device__ int step_free(const DevModel &m, const PushIO &io, Ph &p, Loca
   }
   if (in_grid(m, Xn)) return 2;
   Geo G;
-  metric_eval<true>(m, Xn[1], Xn[2], G);
+  metric_eval<true, KERR>(m, Xn[1], Xn[2], G);
   int it = 0;
   bool conv = false;
   while (true) {
-    accel(G, Kp, An);
+    accel<KERR>(G, Kp, An);
     double num = 0.0, den = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {

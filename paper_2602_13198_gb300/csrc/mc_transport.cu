@@ -19,7 +19,7 @@
 
 namespace mcgb {
 // Emission or child loading + transport initialisation, one item per thread (grid-stride).
-template <bool MIXED>
+template <bool MIXED, bool KERR>
 __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
         ls.emit++;
       }
       p.model = 0;
-      init_transport<MIXED>(m, p);
+      init_transport<MIXED, KERR>(m, p);
       save_ph(io.pool, idx, p);
       grid_phase = in_grid(m, p.X);
     }
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
 // Persistent transport of one phase over io.list_in; PHASE 0 keeps superphotons while they are in
 // the grid, PHASE 1 while they are outside it.  A lane whose superphoton ends or changes phase is
 // refilled from the list (one atomic per warp).
-template <bool MIXED, int PHASE>
+template <bool MIXED, int PHASE, bool KERR>
 __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -101,10 +101,10 @@ __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
     if (live) {
       bool handoff;
       if (PHASE == 0) {
-        live = step<MIXED>(m, io, p, ls);
+        live = step<MIXED, KERR>(m, io, p, ls);
         handoff = live && !in_grid(m, p.X);
       } else {
-        int r = step_free(m, io, p, ls);
+        int r = step_free<KERR>(m, io, p, ls);
         live = (r != 1);
         handoff = (r == 2);
       }
@@ -191,30 +191,53 @@ void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &s
   k_push_sur<<<grid, 128 * kTcGroupsMax, smem, st>>>(m, io, sv);
 }
 
-int push_max_blocks_per_sm(int mixed, int phase, int block) {
+// Kernel of one launch configuration: precision, phase and spin (general Kerr, or a = 0).
+template <bool MIXED, int PHASE>
+static const void *push_kernel(bool kerr) {
+  return kerr ? (const void *)k_push<MIXED, PHASE, true> : (const void *)k_push<MIXED, PHASE, false>;
+}
+
+static const void *push_kernel(int mixed, int phase, bool kerr) {
+  if (mixed) return phase == 0 ? push_kernel<true, 0>(kerr) : push_kernel<true, 1>(kerr);
+  return phase == 0 ? push_kernel<false, 0>(kerr) : push_kernel<false, 1>(kerr);
+}
+
+int push_max_blocks_per_sm(int mixed, int phase, int block, int kerr) {
   int n = 0;
-  if (mixed) {
-    if (phase == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<true, 0>, block, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<true, 1>, block, 0);
-  } else {
-    if (phase == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<false, 0>, block, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push<false, 1>, block, 0);
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, push_kernel(mixed, phase, kerr != 0), block, 0);
   return n;
 }
 
 void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st) {
-  if (mixed) k_init<true><<<grid, block, 0, st>>>(m, io);
-  else k_init<false><<<grid, block, 0, st>>>(m, io);
+  const bool kerr = m.a != 0.0;
+  if (mixed) {
+    if (kerr) k_init<true, true><<<grid, block, 0, st>>>(m, io);
+    else k_init<true, false><<<grid, block, 0, st>>>(m, io);
+  } else {
+    if (kerr) k_init<false, true><<<grid, block, 0, st>>>(m, io);
+    else k_init<false, false><<<grid, block, 0, st>>>(m, io);
+  }
 }
 
+// a = 0 takes the Schwarzschild form of the metric and of the geodesic acceleration.
 void launch_push(const DevModel &m, const PushIO &io, int mixed, int phase, int grid, int block, cudaStream_t st) {
+  const bool kerr = m.a != 0.0;
   if (mixed) {
-    if (phase == 0) k_push<true, 0><<<grid, block, 0, st>>>(m, io);
-    else k_push<true, 1><<<grid, block, 0, st>>>(m, io);
+    if (phase == 0) {
+      if (kerr) k_push<true, 0, true><<<grid, block, 0, st>>>(m, io);
+      else k_push<true, 0, false><<<grid, block, 0, st>>>(m, io);
+    } else {
+      if (kerr) k_push<true, 1, true><<<grid, block, 0, st>>>(m, io);
+      else k_push<true, 1, false><<<grid, block, 0, st>>>(m, io);
+    }
   } else {
-    if (phase == 0) k_push<false, 0><<<grid, block, 0, st>>>(m, io);
-    else k_push<false, 1><<<grid, block, 0, st>>>(m, io);
+    if (phase == 0) {
+      if (kerr) k_push<false, 0, true><<<grid, block, 0, st>>>(m, io);
+      else k_push<false, 0, false><<<grid, block, 0, st>>>(m, io);
+    } else {
+      if (kerr) k_push<false, 1, true><<<grid, block, 0, st>>>(m, io);
+      else k_push<false, 1, false><<<grid, block, 0, st>>>(m, io);
+    }
   }
 }
 
