@@ -217,15 +217,8 @@ __global__ void __launch_bounds__(SUR ? 256 : 128, MINB) k_batch(BatchIO b) {
             emit(sm[lo], idx - soff[lo], p, ls);
             ls.emit++;
           } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              p.X[q] = qin.X[q][idx];
-              p.K[q] = qin.K[q][idx];
-            }
-            p.w = qin.w[idx];
-            rng_init(p.s, qin.id[idx], qin.ctr[idx]);
-            p.nsc = qin.nsc[idx];
             p.model = qin.model[idx];
+            load_child(sm[p.model], qin, idx, p, ls);
           }
           init_transport<MIXED>(sm[p.model], p);
           save_ph(b.pool, idx, p);

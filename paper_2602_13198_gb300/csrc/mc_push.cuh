@@ -130,10 +130,13 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
   p.nsc = 0;
 }
 
-// Compton event at Xe with pre-event wavevector Ke (section 2.7): child in the plasma frame of the
-// event point (radial lookup clamped to the grid), written to the next generation's queue.
-static __device__ void scatter_child(const DevModel &m, const PushIO &io, const double Xe[4], const double Ke[4], double wc,
-                              uint64_t cid, int nsc, int model, LocalStats &ls) {
+// Compton kinematics of a scattered superphoton (section 2.7): at the event point Xe with the
+// pre-event wavevector Ke, in the plasma frame there (radial lookup clamped to the grid), drawing from
+// the child's own stream (cid from its start).  Returns the child's wavevector and the stream
+// position after the draws.  Run when the child is loaded for the next generation, not inside the
+// push: the child's stream is its own, so the result is the same as at the event itself.
+static __device__ void child_kinematics(const DevModel &m, const double Xe[4], const double Ke[4], uint64_t cid,
+                                        double Kc[4], uint32_t &ctr, LocalStats &ls) {
   Geo G;
   metric_eval<false>(m, Xe[1], Xe[2], G);
   double Xc[4] = {Xe[0], fmin(fmax(Xe[1], m.x1_0), m.x1_hi), Xe[2], Xe[3]};
@@ -161,6 +164,15 @@ static __device__ void scatter_child(const DevModel &m, const PushIO &io, const 
   int rej = 0;
   compton_fluid(fmax(P.thetae, 1e-8), eps, n, s, m.seed, eo, dir, rej);
   ls.rejcap += rej;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Kc[q] = eo * e[0][q] + dir[0] * e[1][q] + dir[1] * e[2][q] + dir[2] * e[3][q];
+  ctr = s.n;
+}
+
+// Compton event at Xe with pre-event wavevector Ke: the child (weight wc, stream cid, generation nsc)
+// goes to the next generation's queue with stream position 0, which marks its kinematics as pending.
+static __device__ void scatter_child(const PushIO &io, const double Xe[4], const double Ke[4], double wc, uint64_t cid,
+                                     int nsc, int model, LocalStats &ls) {
   unsigned long long slot = atomicAdd(io.cnt + CNT_OUT, 1ull);
   ls.child++;
   if ((int64_t)slot >= io.out_cap) {
@@ -170,13 +182,34 @@ static __device__ void scatter_child(const DevModel &m, const PushIO &io, const 
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     io.out.X[q][slot] = Xe[q];
-    io.out.K[q][slot] = eo * e[0][q] + dir[0] * e[1][q] + dir[1] * e[2][q] + dir[2] * e[3][q];
+    io.out.K[q][slot] = Ke[q];
   }
   io.out.w[slot] = wc;
   io.out.id[slot] = cid;
-  io.out.ctr[slot] = s.n;
+  io.out.ctr[slot] = 0u;
   io.out.nsc[slot] = nsc;
   if (io.out.model) io.out.model[slot] = (int16_t)model;
+}
+
+// Loads child idx of a queue into p, running its pending Compton kinematics.
+static __device__ void load_child(const DevModel &m, const ChildBuf &q, int64_t idx, Ph &p, LocalStats &ls) {
+  double Ke[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    p.X[k] = q.X[k][idx];
+    Ke[k] = q.K[k][idx];
+  }
+  p.w = q.w[idx];
+  const uint64_t id = q.id[idx];
+  uint32_t ctr = q.ctr[idx];
+  if (ctr == 0u) {
+    child_kinematics(m, p.X, Ke, id, p.K, ctr, ls);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p.K[k] = Ke[k];
+  }
+  rng_init(p.s, id, ctr);
+  p.nsc = q.nsc[idx];
 }
 
 __device__ __forceinline__ bool in_grid(const DevModel &m, const double X[4]) {
@@ -289,7 +322,7 @@ static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalSta
         }
         double we = w0 * exp(-f * tau_a);
         uint64_t cid = child_id(p.s.id, p.nev);
-        scatter_child(m, io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
+        scatter_child(io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
         p.nev++;
         ls.events++;
         wn *= (1.0 - 1.0 / b);
@@ -564,7 +597,7 @@ static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, Ph &p, co
         }
         double we = w0 * exp(-f * tau_a);
         uint64_t cid = child_id(p.s.id, p.nev);
-        scatter_child(m, io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
+        scatter_child(io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
         p.nev++;
         ls.events++;
         wn *= (1.0 - 1.0 / b);

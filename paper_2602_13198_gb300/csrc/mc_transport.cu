@@ -30,14 +30,7 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
     if (have) {
       Ph p;
       if (io.mode == 2) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          p.X[q] = io.in.X[q][idx];
-          p.K[q] = io.in.K[q][idx];
-        }
-        p.w = io.in.w[idx];
-        rng_init(p.s, io.in.id[idx], io.in.ctr[idx]);
-        p.nsc = io.in.nsc[idx];
+        load_child(m, io.in, idx, p, ls);
       } else {
         int64_t uid = (io.mode == 1) ? io.uids[idx] : io.uid0 + idx;
         emit(m, uid, p, ls);
