@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("r_record", C.c_double), ("dh", C.c_double), ("bias_p0", C.c_double),
         ("lnu_lo", C.c_double), ("lnu_hi", C.c_double),
         ("roulette_w", C.c_double), ("roulette_p", C.c_double), ("bias_max", C.c_double),
-        ("bias_target", C.c_double),
+        ("kappa", C.c_double), ("bias_target", C.c_double),
         ("max_steps", C.c_int64),
         ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32),
         ("n_sc_max", C.c_int32), ("n_bins", C.c_int32), ("n_incl", C.c_int32),
@@ -130,6 +130,12 @@ def lib():
         L.or_get_weights.argtypes = [C.c_void_p, PD]
         L.or_run.argtypes = [C.c_void_p, I64, I64, P(I64), I64, PD, P(Stats), C.c_void_p, I64, P(I64), C.c_int]
         L.or_get_bias_scales.argtypes = [C.c_void_p, PD, C.c_int]
+        L.or_F_sync.argtypes = [D]
+        L.or_F_sync.restype = D
+        L.or_jnu_kappa.argtypes = [P(Params), D, D, D, D, D]
+        L.or_jnu_kappa.restype = D
+        L.or_nu_alpha_kappa.argtypes = [P(Params), D, D, D, D, D]
+        L.or_nu_alpha_kappa.restype = D
         L.or_brems_q.argtypes = [D, D]
         L.or_brems_q.restype = D
         L.or_brems_angint.argtypes = [P(Params), D, D, D]
@@ -234,6 +240,20 @@ def Fang(K):
 def jnu_angint(cfg, nu, ne, thetae, B):
     p = params_from(cfg)
     return lib().or_jnu_angint(C.byref(p), nu, ne, thetae, B)
+
+
+def F_sync(x):
+    return lib().or_F_sync(x)
+
+
+def jnu_kappa(cfg, nu, ne, thetae, B, costh):
+    p = params_from(cfg)
+    return lib().or_jnu_kappa(C.byref(p), nu, ne, thetae, B, costh)
+
+
+def nu_alpha_kappa(cfg, nu, ne, thetae, B, costh):
+    p = params_from(cfg)
+    return lib().or_nu_alpha_kappa(C.byref(p), nu, ne, thetae, B, costh)
 
 
 def brems_q(ne, thetae):

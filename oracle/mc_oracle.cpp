@@ -22,6 +22,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <vector>
+#include <mutex>
+#include <map>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -147,6 +149,7 @@ struct or_params {
   double lnu_lo, lnu_hi;       // spectrum range, log10(nu / Hz)
   double roulette_w, roulette_p;
   double bias_max;             // upper bound on b (reading: any b >= 1 keeps the estimate unbiased)
+  double kappa;                // > 3: kappa-distributed electrons for synchrotron (reading), 0: thermal
   double bias_target;          // > 0: per-generation bias tuning (reading), 0: off
   int64_t max_steps;
   int32_t n_nu;                // weight-table nodes
@@ -447,7 +450,191 @@ double K2_of(const or_params &P, double thetae) {
   return std::cyl_bessel_k(2.0, 1.0 / thetae);
 }
 
+// Gauss-Legendre rule on [a, b] with n nodes.
+struct GL {
+  int n;
+  std::vector<double> x, w;
+  GL(int n_, double a, double b) : n(n_), x(n_), w(n_) { gauss_legendre(n, a, b, x.data(), w.data()); }
+};
+
+// ---------------------------------------------------------------- kappa electrons (future work in section 6)
+// Synchrotron emission and absorption of electrons with the kappa distribution
+//   f(gamma) = N gamma (gamma^2 - 1)^1/2 (1 + (gamma - 1) / (kappa w))^-(kappa + 1),  w = Theta_e (kappa - 3) / kappa,
+// from the single-electron spectrum in the ultrarelativistic limit (Rybicki & Lightman ch. 6):
+//   j_nu = (sqrt3 e^3 n_e B sin / (4 pi m_e c^2)) J(X, w),       J = int f F(2X / 3 gamma^2) dgamma,
+//   alpha_nu = (c^2 / 8 pi nu^2) (sqrt3 e^3 n_e B sin / (m_e c^2)^2) A(X, w),
+//   A = - int F(2X / 3 gamma^2) gamma^2 d/dgamma(f / gamma^2) dgamma,
+// X = nu / (nu_B sin), nu_B = e B / (2 pi m_e c), F(x) = x int_x^inf K_5/3 the synchrotron function; and
+// int dOmega j_nu = 4 pi (sqrt3 e^3 n_e B / (4 pi m_e c^2)) I(nu / nu_B, w), I(Y, w) = int_0^1 sin J(Y / sin, w) dmu.
+// ln J, ln A and ln I are tabulated on the grid below and interpolated bilinearly (reading).  The
+// oracle computes F from the library Bessel function K_5/3 and the node integrals over
+// t = ln(gamma - 1) by Gauss-Legendre panels.
+const int KAP_NX = 601, KAP_NW = 61;
+const double KAP_LX0 = -9.210340371976184, KAP_LX1 = 36.841361487904734;   // ln X in [1e-4, 1e16]
+const double KAP_LW0 = -6.907755278982137, KAP_LW1 = 6.907755278982137;    // ln w in [1e-3, 1e3]
+const double KAP_FLOOR = -700.0;
+
+// synchrotron function by its definition (library K_5/3; t = x e^s, Gauss-Legendre panels in s on
+// [0, ln(1 + 60 / x)], which resolves the t^-5/3 growth of K_5/3 near t = x)
+double F_sync_direct(double x) {
+  static const GL g(48, 0.0, 1.0);
+  const double S = std::log1p(60.0 / x);
+  const int np = std::max(8, (int)std::ceil(S / 0.125));
+  const double h = S / np;
+  double s = 0.0;
+  for (int k = 0; k < np; ++k)
+    for (int i = 0; i < g.n; ++i) {
+      const double t = x * std::exp((k + g.x[i]) * h);
+      s += g.w[i] * h * t * std::cyl_bessel_k(5.0 / 3.0, t);
+    }
+  return x * s;
+}
+
+struct KappaTables {
+  double kappa = 0.0;
+  std::vector<double> lnF;                 // ln F on ln x in [-30, ln 200], 6001 nodes (cubic)
+  std::vector<double> lnJ, lnA, lnI;       // [KAP_NX][KAP_NW]
+  double F(double x) const {
+    const double l0 = -30.0, l1 = std::log(200.0);
+    if (x >= 200.0) return 0.0;
+    double lx = std::log(x);
+    if (lx <= l0) return std::exp(lnF[0] + (lx - l0) / 3.0);   // F ~ x^1/3 below
+    double f = (lx - l0) / (l1 - l0) * 6000.0;
+    int i = std::max(1, std::min((int)std::floor(f), 6000 - 2));
+    double u = f - i;
+    double y0 = lnF[i - 1], y1 = lnF[i], y2 = lnF[i + 1], y3 = lnF[i + 2];
+    double v = -y0 * u * (u - 1) * (u - 2) / 6.0 + y1 * (u + 1) * (u - 1) * (u - 2) / 2.0 -
+               y2 * (u + 1) * u * (u - 2) / 2.0 + y3 * (u + 1) * u * (u - 1) / 6.0;
+    return std::exp(v);
+  }
+};
+
+double kap_interp(const std::vector<double> &t, double lx, double lw) {
+  double fx = (lx - KAP_LX0) / (KAP_LX1 - KAP_LX0) * (KAP_NX - 1);
+  double fw = (lw - KAP_LW0) / (KAP_LW1 - KAP_LW0) * (KAP_NW - 1);
+  fx = std::min(std::max(fx, 0.0), (double)(KAP_NX - 1));
+  fw = std::min(std::max(fw, 0.0), (double)(KAP_NW - 1));
+  int i = std::min((int)fx, KAP_NX - 2), j = std::min((int)fw, KAP_NW - 2);
+  double a = fx - i, b = fw - j;
+  double l = (1 - a) * (1 - b) * t[i * KAP_NW + j] + (1 - a) * b * t[i * KAP_NW + j + 1] +
+             a * (1 - b) * t[(i + 1) * KAP_NW + j] + a * b * t[(i + 1) * KAP_NW + j + 1];
+  return std::exp(l);
+}
+
+void build_kappa(KappaTables &T, double kappa) {
+  T.kappa = kappa;
+  T.lnF.resize(6001);
+  const double l0 = -30.0, l1 = std::log(200.0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int i = 0; i <= 6000; ++i) T.lnF[i] = std::log(F_sync_direct(std::exp(l0 + (l1 - l0) * i / 6000.0)));
+  T.lnJ.assign((size_t)KAP_NX * KAP_NW, KAP_FLOOR);
+  T.lnA.assign((size_t)KAP_NX * KAP_NW, KAP_FLOOR);
+  T.lnI.assign((size_t)KAP_NX * KAP_NW, KAP_FLOOR);
+  static const GL gp(32, 0.0, 1.0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int jw = 0; jw < KAP_NW; ++jw) {
+    const double w = std::exp(KAP_LW0 + (KAP_LW1 - KAP_LW0) * jw / (KAP_NW - 1));
+    const double kw = kappa * w;
+    // t = ln(gamma - 1) over [ln(kappa w) - 25, ln(kappa w) + 45] in 280 panels of 32 nodes
+    const double t0 = std::log(kw) - 25.0, h = 0.25;
+    const int np = 280;
+    std::vector<double> tt, ww;
+    for (int k = 0; k < np; ++k)
+      for (int i = 0; i < gp.n; ++i) { tt.push_back(t0 + (k + gp.x[i]) * h); ww.push_back(gp.w[i] * h); }
+    const size_t nq = tt.size();
+    std::vector<double> gam(nq), base(nq), aterm(nq);
+    double norm = 0.0;
+    for (size_t q = 0; q < nq; ++q) {
+      const double e = std::exp(tt[q]), g = 1.0 + e, rt = std::sqrt(e * (2.0 + e));   // sqrt(gamma^2 - 1)
+      const double lp = -(kappa + 1.0) * std::log1p(e / kw);
+      gam[q] = g;
+      base[q] = std::exp(lp + tt[q]);                       // P(gamma) dgamma/dt
+      norm += ww[q] * g * rt * base[q];
+      aterm[q] = g * rt * (kappa + 1.0) / (kw + e) - 1.0 / rt;   // gamma^2 d/dgamma(f/gamma^2) / (-f-free part)
+    }
+    for (int ix = 0; ix < KAP_NX; ++ix) {
+      const double X = std::exp(KAP_LX0 + (KAP_LX1 - KAP_LX0) * ix / (KAP_NX - 1));
+      double sj = 0.0, sa = 0.0;
+      for (size_t q = 0; q < nq; ++q) {
+        const double x = 2.0 * X / (3.0 * gam[q] * gam[q]);
+        if (x >= 200.0) continue;
+        const double Fq = T.F(x);
+        const double rt = std::sqrt((gam[q] - 1.0) * (gam[q] + 1.0));
+        sj += ww[q] * gam[q] * rt * base[q] * Fq;
+        sa += ww[q] * aterm[q] * base[q] * Fq;
+      }
+      sj /= norm;
+      sa /= norm;
+      T.lnJ[(size_t)ix * KAP_NW + jw] = sj > 0.0 ? std::max(KAP_FLOOR, std::log(sj)) : KAP_FLOOR;
+      T.lnA[(size_t)ix * KAP_NW + jw] = sa > 0.0 ? std::max(KAP_FLOOR, std::log(sa)) : KAP_FLOOR;
+    }
+  }
+  // I(Y, w) = int_0^1 sin J(Y / sin, w) dmu = int_0^{pi/2} sin^2 J(Y / sin, w) dtheta over the interpolated
+  // J, defined (reading) as the midpoint sum with 2048 points in theta
+  const int M = 2048;
+#pragma omp parallel for schedule(static)
+  for (int ix = 0; ix < KAP_NX; ++ix) {
+    const double lY = KAP_LX0 + (KAP_LX1 - KAP_LX0) * ix / (KAP_NX - 1);
+    for (int jw = 0; jw < KAP_NW; ++jw) {
+      const double lw = KAP_LW0 + (KAP_LW1 - KAP_LW0) * jw / (KAP_NW - 1);
+      double s = 0.0;
+      for (int k = 0; k < M; ++k) {
+        const double st = std::sin((k + 0.5) * (0.5 * PI / M));
+        s += st * st * kap_interp(T.lnJ, lY - std::log(st), lw);
+      }
+      s *= 0.5 * PI / M;
+      T.lnI[(size_t)ix * KAP_NW + jw] = s > 0.0 ? std::max(KAP_FLOOR, std::log(s)) : KAP_FLOOR;
+    }
+  }
+}
+
+const KappaTables &kappa_tables(double kappa) {
+  static std::mutex mu;
+  static std::map<double, KappaTables> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(kappa);
+  if (it == cache.end()) {
+    KappaTables T;
+    build_kappa(T, kappa);
+    it = cache.emplace(kappa, std::move(T)).first;
+  }
+  return it->second;
+}
+
+double kappa_w(const or_params &P, double thetae) { return thetae * (P.kappa - 3.0) / P.kappa; }
+
+double jnu_kappa(const or_params &P, double nu, double ne, double thetae, double B, double costh) {
+  double s2 = 1.0 - costh * costh;
+  if (s2 <= 0.0) return 0.0;
+  const double sth = std::sqrt(s2), nuB = EE * B / (2.0 * PI * ME * CL);
+  const KappaTables &T = kappa_tables(P.kappa);
+  double Jv = kap_interp(T.lnJ, std::log(nu / (nuB * sth)), std::log(kappa_w(P, thetae)));
+  return std::sqrt(3.0) * EE * EE * EE * ne * B * sth / (4.0 * PI * ME * CL * CL) * Jv;
+}
+
+// nu alpha_nu of the kappa population
+double nu_alpha_kappa(const or_params &P, double nu, double ne, double thetae, double B, double costh) {
+  double s2 = 1.0 - costh * costh;
+  if (s2 <= 0.0) return 0.0;
+  const double sth = std::sqrt(s2), nuB = EE * B / (2.0 * PI * ME * CL);
+  const KappaTables &T = kappa_tables(P.kappa);
+  double Av = kap_interp(T.lnA, std::log(nu / (nuB * sth)), std::log(kappa_w(P, thetae)));
+  const double mc2 = ME * CL * CL;
+  return CL * CL / (8.0 * PI * nu) * std::sqrt(3.0) * EE * EE * EE * ne * B * sth / (mc2 * mc2) * Av;
+}
+
+double jnu_angint_kappa(const or_params &P, double nu, double ne, double thetae, double B) {
+  const double nuB = EE * B / (2.0 * PI * ME * CL);
+  const KappaTables &T = kappa_tables(P.kappa);
+  double Iv = kap_interp(T.lnI, std::log(nu / nuB), std::log(kappa_w(P, thetae)));
+  return std::sqrt(3.0) * EE * EE * EE * ne * B / (ME * CL * CL) * Iv;   // 4 pi x (sqrt3 e^3 n_e B / 4 pi m_e c^2) I
+}
+
 double jnu(const or_params &P, double nu, double ne, double thetae, double B, double costh) {
+  if (P.kappa > 0.0) {
+    if (thetae < P.thetae_min || ne <= 0.0 || B <= 0.0) return 0.0;
+    return jnu_kappa(P, nu, ne, thetae, B, costh);
+  }
   if (thetae < P.thetae_min || ne <= 0.0 || B <= 0.0) return 0.0;
   double s2 = 1.0 - costh * costh;
   if (s2 <= 0.0) return 0.0;
@@ -466,11 +653,6 @@ double bnu(double nu, double thetae) {
 // Angle integral F(K) = int_0^{pi/2} sin^2(th) G(K / sin th) dth, G(X) = (X^1/2 + 2^11/12 X^1/6)^2 e^{-X^1/3},
 // so that int dOmega j_nu = 4 pi A nu_c F(nu / nu_c) with A = sqrt(2) pi e^2 n_e / (3 c K2).
 // Gauss-Legendre with 64 nodes in theta (reading).
-struct GL {
-  int n;
-  std::vector<double> x, w;
-  GL(int n_, double a, double b) : n(n_), x(n_), w(n_) { gauss_legendre(n, a, b, x.data(), w.data()); }
-};
 
 double Fang(double K) {
   static const GL gl(64, 0.0, PI / 2.0);
@@ -491,6 +673,7 @@ double nu_c_of(double thetae, double B) {
 // int dOmega j_nu at frequency nu for a zone state.
 double jnu_angint(const or_params &P, double nu, double ne, double thetae, double B) {
   if (thetae < P.thetae_min || ne <= 0.0 || B <= 0.0) return 0.0;
+  if (P.kappa > 0.0) return jnu_angint_kappa(P, nu, ne, thetae, B);
   double nuc = nu_c_of(thetae, B);
   double A = std::sqrt(2.0) * PI * EE * EE * ne / (3.0 * CL * K2_of(P, thetae));
   return 4.0 * PI * A * nuc * Fang(nu / nuc);
@@ -914,8 +1097,14 @@ void coefficients(const Model &M, const double X[4], const double K[4], bool wan
     cth = kb / (eps * std::sqrt(c.F.bsq));
     cth = std::min(1.0, std::max(-1.0, cth));
   }
-  double j = jnu(M.P, nu, c.F.ne, c.F.thetae, c.F.B, cth);
-  if (j > 0.0) c.ana = nu * j / bnu(nu, c.F.thetae);
+  if (M.P.kappa > 0.0) {
+    // a non-thermal population: alpha from its own integral, not Kirchhoff's law
+    if (c.F.thetae >= M.P.thetae_min && c.F.ne > 0.0 && c.F.B > 0.0)
+      c.ana = nu_alpha_kappa(M.P, nu, c.F.ne, c.F.thetae, c.F.B, cth);
+  } else {
+    double j = jnu(M.P, nu, c.F.ne, c.F.thetae, c.F.B, cth);
+    if (j > 0.0) c.ana = nu * j / bnu(nu, c.F.thetae);
+  }
   c.ana += brems_nu_alpha(M.P, nu, c.F.ne, c.F.thetae);
   if (want_scatter) {
     double th = std::max(c.F.thetae, 1e-300);
@@ -1411,6 +1600,7 @@ void *or_create(const or_params *P, const or_grid *G) {
   M->prim.assign(G->prim, G->prim + (size_t)8 * M->nz);
   M->r_h = (P->mass > 0.0) ? 1.0 + std::sqrt(1.0 - P->a * P->a) : 0.0;
   if (P->scatter) hot_table();
+  if (P->kappa > 0.0) kappa_tables(P->kappa);
   return M;
 }
 
@@ -1545,6 +1735,13 @@ int or_run(void *h, int64_t uid0, int64_t uid1, const int64_t *uids, int64_t nui
 }
 
 double or_brems_q(double ne, double thetae) { return brems_q(ne, thetae); }
+double or_F_sync(double x) { return F_sync_direct(x); }
+double or_jnu_kappa(const or_params *P, double nu, double ne, double thetae, double B, double costh) {
+  return jnu(*P, nu, ne, thetae, B, costh);
+}
+double or_nu_alpha_kappa(const or_params *P, double nu, double ne, double thetae, double B, double costh) {
+  return nu_alpha_kappa(*P, nu, ne, thetae, B, costh);
+}
 double or_brems_angint(const or_params *P, double nu, double ne, double thetae) {
   return brems_angint(*P, nu, ne, thetae);
 }

@@ -152,6 +152,11 @@ DevModel make_model(const mc_ctx *c) {
   m.prim32 = c->prim_f32 ? (const float *)c->prim : nullptr;
   m.prim32x = c->prim_f32 ? (const float *)c->prim : c->prim_x32;
   m.brems = p.brems;
+  m.kappa = p.kappa;
+  m.kapJ = c->kapJ;
+  m.kapA = c->kapA;
+  m.kapI = c->kapI;
+  m.zlnw = c->zlnw;
   m.zbq = c->zbq;
   m.zbnt = c->zbnt;
   m.lnF = c->lnF;
@@ -188,6 +193,8 @@ static int check_params(const mc_model_params *p, std::string &why) {
   if (!(p->bias_target >= 0.0 && p->bias_target < 1e30)) return bad("bias_target must be >= 0");
   if (p->brems != 0 && p->brems != 1) return bad("brems must be 0 or 1");
   if (p->brems && p->surrogate) return bad("the coefficient surrogate does not model bremsstrahlung");
+  if (!(p->kappa == 0.0 || (p->kappa > 3.0 && p->kappa <= 1e8))) return bad("kappa must be 0 or in (3, 1e8]");
+  if (p->kappa > 0.0 && p->surrogate) return bad("the coefficient surrogate does not model kappa electrons");
   if (p->n_sc_max < 0 || p->n_sc_max > 1000) return bad("n_sc_max out of range");
   if (!(p->roulette_p > 0.0 && p->roulette_p <= 1.0) || !(p->roulette_w >= 0.0)) return bad("bad roulette");
   if (p->max_steps < 1 || p->max_steps > 2000000000LL) return bad("max_steps out of range");
@@ -276,6 +283,17 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
     mc_free(c);
     return fail(nullptr, MC_ERR_CUDA, "table upload failed");
   }
+  if (p->kappa > 0.0) {
+    c->kapF = (double *)dev_alloc(c, sizeof(double) * kKapNF);
+    c->kapJ = (double *)dev_alloc(c, sizeof(double) * kKapNX * kKapNW);
+    c->kapA = (double *)dev_alloc(c, sizeof(double) * kKapNX * kKapNW);
+    c->kapI = (double *)dev_alloc(c, sizeof(double) * kKapNX * kKapNW);
+    if (!c->kapF || !c->kapJ || !c->kapA || !c->kapI) {
+      mc_free(c);
+      return fail(nullptr, MC_ERR_OOM, "device allocation failed");
+    }
+    launch_kappa_tables(p->kappa, c->kapF, c->kapJ, c->kapA, c->kapI, 0);
+  }
   DevModel m = make_model(c);
   launch_tables(m, c->lnF, c->lnK2, c->hot, c->gl, c->gl + 128, c->gl + 256, 0);
   cudaError_t e = cudaDeviceSynchronize();
@@ -300,11 +318,12 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   size_t esz = (g->dtype == MC_DTYPE_F32) ? 4 : 8;
   // free per-grid buffers
   void *old[] = {c->prim, c->prim_x32, c->zvol, c->zpref, c->zlnuc, c->zgmax, c->znbar, c->counts, c->start, c->bsum,
-                 c->partial, c->zbq, c->zbnt};
+                 c->partial, c->zbq, c->zbnt, c->zlnw};
   for (void *ptr : old) dev_free(c, ptr);
   c->prim = nullptr;
   c->prim_x32 = nullptr;
   c->zbq = c->zbnt = nullptr;
+  c->zlnw = nullptr;
   c->have_grid = false;
   c->have_run = false;
   c->n1 = g->n1; c->n2 = g->n2; c->n3 = g->n3; c->nz = nz;
@@ -323,6 +342,10 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   c->partial = (double *)dev_alloc(c, 8 * (size_t)c->nchunks * c->p.n_nu);
   if (!c->prim || !c->zvol || !c->zpref || !c->zlnuc || !c->zgmax || !c->znbar || !c->counts || !c->start || !c->bsum || !c->partial)
     return fail(c, MC_ERR_OOM, "grid allocation failed");
+  if (c->p.kappa > 0.0) {
+    c->zlnw = (double *)dev_alloc(c, 8 * nz);
+    if (!c->zlnw) return fail(c, MC_ERR_OOM, "grid allocation failed");
+  }
   if (c->p.brems) {
     c->zbq = (double *)dev_alloc(c, 8 * nz);
     c->zbnt = (double *)dev_alloc(c, 8 * nz);

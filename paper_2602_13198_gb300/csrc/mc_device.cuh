@@ -70,6 +70,9 @@ struct DevModel {
   const int64_t *start;   // exclusive scan of zone counts
   const double *zpref;    // 4 pi A nu_c per zone (int dOmega j_nu = zpref F(nu/nu_c))
   int brems;              // thermal bremsstrahlung on
+  double kappa;           // > 0: kappa-distributed electrons for the synchrotron terms
+  const double *kapJ, *kapA, *kapI;   // ln J, ln A, ln I on the kappa grid [kKapNX][kKapNW]
+  const double *zlnw;     // per zone: ln w of the kappa population (kappa only)
   double *zbq, *zbnt;     // per zone: q / nu_T and nu_T = k T_e / h (bremsstrahlung only)
   const double *zlnuc;    // ln nu_c per zone
   const double *zgmax;    // max_j g_ij per zone
@@ -429,6 +432,40 @@ __device__ __forceinline__ double pow_sixth(double X) {
   return X * (z2 * z2 * z);
 }
 
+// ---------------------------------------------------------------- kappa electrons (future work in section 6)
+// Synchrotron terms of kappa-distributed electrons from the single-electron spectrum: with
+// X = nu / (nu_B sin), nu_B = e B / (2 pi m_e c) and F the synchrotron function,
+//   j_nu = (sqrt3 e^3 n_e B sin / 4 pi m_e c^2) J(X, w),  J = int f F(2X / 3 gamma^2) dgamma,
+//   nu alpha_nu = (c^2 / 8 pi nu) (sqrt3 e^3 n_e B sin / (m_e c^2)^2) A(X, w),
+//   int dOmega j_nu = (sqrt3 e^3 n_e B / m_e c^2) I(nu / nu_B, w);
+// ln J, ln A, ln I tabulated on this grid and interpolated bilinearly.
+constexpr int kKapNX = 601, kKapNW = 61, kKapNF = 6001;
+constexpr double kKapLX0 = -9.210340371976184, kKapLX1 = 36.841361487904734;   // ln X in [1e-4, 1e16]
+constexpr double kKapLW0 = -6.907755278982137, kKapLW1 = 6.907755278982137;    // ln w in [1e-3, 1e3]
+constexpr double kKapLF0 = -30.0, kKapLF1 = 5.298317366548036;                 // ln x of the F table
+constexpr double kKapFloor = -700.0;
+constexpr double kKapCj = 1.7320508075688772 * kEE * kEE * kEE / (kME * kCL * kCL);   // sqrt3 e^3 / m_e c^2
+constexpr double kNuB1 = kEE / (2.0 * kPI * kME * kCL);                                // nu_B / B
+
+__device__ __forceinline__ double kap_interp(const double *t, double lx, double lw) {
+  constexpr double sx = (kKapNX - 1) / (kKapLX1 - kKapLX0), sw = (kKapNW - 1) / (kKapLW1 - kKapLW0);
+  double fx = fmin(fmax((lx - kKapLX0) * sx, 0.0), (double)(kKapNX - 1));
+  double fw = fmin(fmax((lw - kKapLW0) * sw, 0.0), (double)(kKapNW - 1));
+  int i = min((int)fx, kKapNX - 2), j = min((int)fw, kKapNW - 2);
+  double a = fx - i, b = fw - j;
+  const double *r = t + i * kKapNW + j;
+  double l = (1 - a) * (1 - b) * r[0] + (1 - a) * b * r[1] + a * (1 - b) * r[kKapNW] + a * b * r[kKapNW + 1];
+  return exp(l);
+}
+
+// nu alpha_nu of the kappa population at angle sth to the field
+__device__ __forceinline__ double kappa_nu_alpha(const DevModel &m, double ne, double thetae, double B, double sth,
+                                                 double nu) {
+  const double lx = log(nu / (kNuB1 * B * sth)), lw = log(thetae * (m.kappa - 3.0) / m.kappa);
+  constexpr double kCa = kCL * kCL / (8.0 * kPI) * kKapCj / (kME * kCL * kCL);
+  return kCa * ne * B * sth * kap_interp(m.kapA, lx, lw) / nu;
+}
+
 // ---------------------------------------------------------------- bremsstrahlung (future work in section 6)
 // Total thermal bremsstrahlung cooling rate of a hydrogen plasma [erg s^-1 cm^-3], electron-ion plus
 // electron-electron, from the fits of Stepney & Guilbert (1983) in the form of Narayan & Yi (1995);
@@ -457,8 +494,12 @@ __device__ __forceinline__ double brems_nu_alpha(double ne, double th, double nu
 // int dOmega j_nu of zone z at weight-table node j: synchrotron (pref F(nu/nu_c); 0 when the zone
 // has no synchrotron) plus, when on, bremsstrahlung (q / nu_T) exp(-nu / nu_T).
 __device__ __forceinline__ double F_of_lnK(const DevModel &m, double lnK);
+__device__ __forceinline__ double kap_interp(const double *t, double lx, double lw);
 __device__ __forceinline__ double zone_E(const DevModel &m, int64_t z, double pref, double lnuc, int j) {
-  double e = (pref == 0.0) ? 0.0 : pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc);
+  // kappa: lnuc holds ln nu_B and the zone's ln w sits in zlnw
+  double e = (pref == 0.0) ? 0.0
+             : (m.kappa > 0.0) ? pref * kap_interp(m.kapI, m.lnu_min + j * m.dlnu - lnuc, m.zlnw[z])
+                               : pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc);
   if (m.brems && m.zbq[z] > 0.0) e += m.zbq[z] * exp(-exp(m.lnu_min + j * m.dlnu) / m.zbnt[z]);
   return e;
 }
@@ -674,7 +715,12 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
   const double ieps = 1.0 / eps;
   double nu = eps * kNuEps;
   double lt = log(fmax(P.thetae, 1e-300));
-  if (P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
+  if (m.kappa > 0.0 && P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
+    double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
+    double cth = fmin(1.0, fmax(-1.0, kb * P.rb * ieps));
+    double s2 = 1.0 - cth * cth;
+    if (s2 > 0.0) c.ana = kappa_nu_alpha(m, P.ne, P.thetae, P.B, s2 * rsqrt(s2), nu);
+  } else if (P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
     double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
     double cth = fmin(1.0, fmax(-1.0, kb * P.rb * ieps));
     double s2 = 1.0 - cth * cth;
@@ -739,6 +785,16 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, 
     }
   }
   c.ana = (double)ana;
+  if (m.kappa > 0.0) {
+    // kappa population: its absorption integral (FP64 tables) in place of the thermal fit
+    c.ana = 0.0;
+    if (P.thetae >= (float)m.thetae_min && P.B > 0.0f && P.bsq > 0.0f) {
+      double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
+      double cth = fmin(1.0, fmax(-1.0, kb / ((double)eps * sqrt((double)P.bsq))));
+      double s2 = 1.0 - cth * cth;
+      if (s2 > 0.0) c.ana = kappa_nu_alpha(m, (double)P.ne, (double)P.thetae, (double)P.B, sqrt(s2), (double)nu9 * 1e9);
+    }
+  }
   // bremsstrahlung absorption in FP64 (n_e^2 leaves the FP32 range in dense plasma)
   if (m.brems) c.ana += brems_nu_alpha((double)P.ne, (double)P.thetae, (double)nu9 * 1e9);
   if (want_s) {

@@ -73,14 +73,29 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
     if (r2 * gm < glin) break;
   }
   if (it == 100000) ls.rejcap++;
-  const double jsyn = (pref == 0.0) ? 0.0 : pref * F_of_lnK(m, lnu - lnuc);
+  const double jsyn = (pref == 0.0) ? 0.0
+                      : (m.kappa > 0.0) ? pref * kap_interp(m.kapI, lnu - lnuc, m.zlnw[z])
+                                        : pref * F_of_lnK(m, lnu - lnuc);
   const double jbr = (m.brems && m.zbq[z] > 0.0) ? m.zbq[z] * exp(-exp(lnu) / m.zbnt[z]) : 0.0;
   // with bremsstrahlung on, the process is drawn in proportion to the two angle-integrated
   // emissivities; bremsstrahlung is isotropic
   bool synchrotron = true;
   if (m.brems) synchrotron = rng_u(p.s, m.seed) * (jsyn + jbr) < jsyn;
   double cth = 0.0;
-  if (synchrotron) {
+  if (synchrotron && m.kappa > 0.0) {
+    // kappa: accept with j(theta)/j(pi/2) = sin(th) J(X / sin th, w) / J(X, w), X = nu / nu_B
+    const double lX = lnu - lnuc, lw = m.zlnw[z];
+    const double jmax = kap_interp(m.kapJ, lX, lw);
+    for (it = 0; it < 100000; ++it) {
+      double r3 = rng_u(p.s, m.seed);
+      cth = 2.0 * r3 - 1.0;
+      double r4 = rng_u(p.s, m.seed);
+      double sth = sqrt(1.0 - cth * cth);
+      double jt = sth > 0.0 ? sth * kap_interp(m.kapJ, lX - log(sth), lw) : 0.0;
+      if (r4 * jmax < jt) break;
+    }
+    if (it == 100000) ls.rejcap++;
+  } else if (synchrotron) {
     // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
     double K0 = exp(lnu - lnuc);
     double jmax = Gsyn(K0);

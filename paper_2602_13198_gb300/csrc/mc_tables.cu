@@ -72,6 +72,86 @@ void launch_tables(const DevModel &m, double *lnF, double *lnK2, double *hot, co
   k_table_hot<<<(kHotNT * kHotNE + 127) / 128, 128, 0, st>>>(hot, gl_s, gl_s + 64, gl_mu, gl_mu + 32);
 }
 
+// ---------------------------------------------------------------- kappa electrons
+// ln F of the synchrotron function F(x) = x int_0^inf cosh(5u/3) / cosh(u) e^{-x cosh u} du (the integral
+// representation of K_5/3 integrated over [x, inf)), by the trapezoid rule in u (even integrand).
+__global__ void k_kap_F(double *lnF) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kKapNF) return;
+  const double x = exp(kKapLF0 + (kKapLF1 - kKapLF0) * i / (kKapNF - 1));
+  const double U = acosh(fmax(1.0, 760.0 / x)) + 2.0;
+  const int n = (int)ceil(U / 0.004);
+  const double h = U / n;
+  double s = 0.0;
+  for (int k = 0; k <= n; ++k) {
+    const double u = k * h;
+    const double v = exp(-x * cosh(u) + u * (2.0 / 3.0)) * (1.0 + exp(-u * (10.0 / 3.0))) / (1.0 + exp(-2.0 * u));
+    s += (k == 0 || k == n) ? 0.5 * v : v;
+  }
+  lnF[i] = log(x * s * h);
+}
+
+__device__ __forceinline__ double kap_F(const double *lnF, double x) {
+  if (x >= 200.0) return 0.0;
+  const double lx = log(x);
+  if (lx <= kKapLF0) return exp(lnF[0] + (lx - kKapLF0) / 3.0);   // F ~ x^1/3 below the table
+  return exp(cubic_table(lnF, kKapNF, kKapLF0, (kKapNF - 1) / (kKapLF1 - kKapLF0), lx));
+}
+
+// ln J and ln A at one (X, w) node: trapezoid rule in t = ln(gamma - 1) over
+// [ln(kappa w) - 25, ln(kappa w) + 45] with step 0.01, normalised by the same rule.
+__global__ void k_kap_JA(const double *lnF, double kappa, double *lnJ, double *lnA) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= kKapNX * kKapNW) return;
+  const int ix = node / kKapNW, jw = node % kKapNW;
+  const double X = exp(kKapLX0 + (kKapLX1 - kKapLX0) * ix / (kKapNX - 1));
+  const double w = exp(kKapLW0 + (kKapLW1 - kKapLW0) * jw / (kKapNW - 1));
+  const double kw = kappa * w;
+  const double t0 = log(kw) - 25.0, h = 0.01;
+  const int n = 7000;
+  double sn = 0.0, sj = 0.0, sa = 0.0;
+  for (int k = 0; k <= n; ++k) {
+    const double t = t0 + k * h, e = exp(t), g = 1.0 + e, rt = sqrt(e * (2.0 + e));
+    const double base = exp(t - (kappa + 1.0) * log1p(e / kw));   // P(gamma) dgamma/dt
+    const double wt = (k == 0 || k == n) ? 0.5 : 1.0;
+    sn += wt * g * rt * base;
+    const double x = 2.0 * X / (3.0 * g * g);
+    if (x >= 200.0) continue;
+    const double Fx = kap_F(lnF, x);
+    sj += wt * g * rt * base * Fx;
+    sa += wt * (g * rt * (kappa + 1.0) / (kw + e) - 1.0 / rt) * base * Fx;
+  }
+  sj /= sn;
+  sa /= sn;
+  lnJ[node] = sj > 0.0 ? fmax(kKapFloor, log(sj)) : kKapFloor;
+  lnA[node] = sa > 0.0 ? fmax(kKapFloor, log(sa)) : kKapFloor;
+}
+
+// ln I(Y, w): I = int_0^{pi/2} sin^2 J(Y / sin, w) dtheta over the interpolated J, the midpoint sum with
+// 2048 points in theta.
+__global__ void k_kap_I(const double *lnJ, double *lnI) {
+  int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= kKapNX * kKapNW) return;
+  const int ix = node / kKapNW, jw = node % kKapNW;
+  const double lY = kKapLX0 + (kKapLX1 - kKapLX0) * ix / (kKapNX - 1);
+  const double lw = kKapLW0 + (kKapLW1 - kKapLW0) * jw / (kKapNW - 1);
+  const int M = 2048;
+  double s = 0.0;
+  for (int k = 0; k < M; ++k) {
+    const double st = sin((k + 0.5) * (0.5 * kPI / M));
+    s += st * st * kap_interp(lnJ, lY - log(st), lw);
+  }
+  s *= 0.5 * kPI / M;
+  lnI[node] = s > 0.0 ? fmax(kKapFloor, log(s)) : kKapFloor;
+}
+
+void launch_kappa_tables(double kappa, double *lnF, double *lnJ, double *lnA, double *lnI, cudaStream_t st) {
+  k_kap_F<<<(kKapNF + 127) / 128, 128, 0, st>>>(lnF);
+  const int nn = kKapNX * kKapNW;
+  k_kap_JA<<<(nn + 127) / 128, 128, 0, st>>>(lnF, kappa, lnJ, lnA);
+  k_kap_I<<<(nn + 127) / 128, 128, 0, st>>>(lnJ, lnI);
+}
+
 // ---------------------------------------------------------------- grid layout
 __global__ void k_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, int64_t nz, int *bad) {
   int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,7 +206,16 @@ __global__ void k_zone_prep(DevModel m, double *zvol, double *zpref, double *zln
   plasma_from_prims<double>(m, G, pr, P, nullptr, nullptr);
   if (!isfinite(P.thetae) || !isfinite(P.B) || !isfinite(P.ne)) atomicOr(bad, 2);
   double pref = 0.0, lnuc = 0.0;
-  if (P.thetae >= m.thetae_min && P.ne > 0.0 && P.B > 0.0) {
+  if (m.kappa > 0.0) {
+    // kappa: int dOmega j_nu = (sqrt3 e^3 n_e B / m_e c^2) I(nu / nu_B, w); lnuc holds ln nu_B
+    double lw = 0.0;
+    if (P.thetae >= m.thetae_min && P.ne > 0.0 && P.B > 0.0) {
+      pref = kKapCj * P.ne * P.B;
+      lnuc = log(kNuB1 * P.B);
+      lw = log(P.thetae * (m.kappa - 3.0) / m.kappa);
+    }
+    ((double *)m.zlnw)[z] = lw;
+  } else if (P.thetae >= m.thetae_min && P.ne > 0.0 && P.B > 0.0) {
     double nuc = (2.0 / 9.0) * (kEE * P.B / (2.0 * kPI * kME * kCL)) * P.thetae * P.thetae;
     double A = 1.4142135623730951 * kPI * kEE * kEE * P.ne / (3.0 * kCL * K2_of(m, P.thetae));
     pref = 4.0 * kPI * A * nuc;

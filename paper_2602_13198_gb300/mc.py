@@ -40,7 +40,7 @@ class ModelParams(C.Structure):
         ("eps_geo", C.c_double), ("verlet_tol", C.c_double), ("r_record", C.c_double), ("dh", C.c_double),
         ("bias_p0", C.c_double), ("lnu_lo", C.c_double), ("lnu_hi", C.c_double),
         ("roulette_w", C.c_double), ("roulette_p", C.c_double), ("bias_max", C.c_double),
-        ("bias_target", C.c_double),
+        ("kappa", C.c_double), ("bias_target", C.c_double),
         ("max_steps", C.c_int64),
         ("n_nu", C.c_int32), ("verlet_maxit", C.c_int32), ("bias_mode", C.c_int32), ("n_sc_max", C.c_int32),
         ("n_bins", C.c_int32), ("n_incl", C.c_int32), ("k2_mode", C.c_int32), ("scatter", C.c_int32),

@@ -43,7 +43,7 @@ def base_params(**over) -> dict:
         eps_geo=0.04, verlet_tol=1e-3,
         r_record=1000.0, dh=0.05, bias_p0=1.0,
         lnu_lo=8.0, lnu_hi=24.0,
-        roulette_w=1e-12, roulette_p=0.1, bias_max=1e300, bias_target=0.0, brems=0,
+        roulette_w=1e-12, roulette_p=0.1, bias_max=1e300, bias_target=0.0, kappa=0.0, brems=0,
         max_steps=20000,
         n_nu=200, verlet_maxit=16, bias_mode=0, n_sc_max=4,
         n_bins=200, n_incl=1, k2_mode=0, scatter=0,
