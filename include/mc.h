@@ -72,9 +72,9 @@ typedef struct mc_model_params {
   double lnu_lo, lnu_hi;   /* spectrum range, log10(nu/Hz) */
   double roulette_w, roulette_p;  /* Russian roulette when w < roulette_w * w_birth, survival roulette_p */
   double bias_max;     /* upper bound on the bias b (any b >= 1 leaves the estimate unbiased) */
-  double kappa;        /* 0: thermal (Maxwell-Juettner) electrons; > 3: synchrotron emission and absorption of
-                          kappa-distributed electrons of width w = Theta_e (kappa - 3) / kappa (Compton
-                          scattering stays thermal; not with the surrogate) */
+  double kappa;        /* 0: thermal (Maxwell-Juettner) electrons; in (3, 1e8]: kappa-distributed electrons of
+                          width w = Theta_e (kappa - 3) / kappa for synchrotron emission, absorption and
+                          Compton scattering (non-thermal electrons of section 6; not with the surrogate) */
   double bias_target;  /* > 0: tune the bias per scattering generation on the fly so that each
                           generation produces about bias_target scattered superphotons per
                           superphoton it carries (mc_run only); 0: the bias as configured */

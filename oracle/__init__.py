@@ -130,6 +130,10 @@ def lib():
         L.or_get_weights.argtypes = [C.c_void_p, PD]
         L.or_run.argtypes = [C.c_void_p, I64, I64, P(I64), I64, PD, P(Stats), C.c_void_p, I64, P(I64), C.c_int]
         L.or_get_bias_scales.argtypes = [C.c_void_p, PD, C.c_int]
+        L.or_sigma_hot_kappa.argtypes = [D, D, D]
+        L.or_sigma_hot_kappa.restype = D
+        L.or_sample_kappa.argtypes = [D, D, U64, U64, I64, PD]
+        L.or_compton_kappa.argtypes = [D, D, D, U64, U64, I64, PD, PD]
         L.or_F_sync.argtypes = [D]
         L.or_F_sync.restype = D
         L.or_jnu_kappa.argtypes = [P(Params), D, D, D, D, D]
@@ -240,6 +244,23 @@ def Fang(K):
 def jnu_angint(cfg, nu, ne, thetae, B):
     p = params_from(cfg)
     return lib().or_jnu_angint(C.byref(p), nu, ne, thetae, B)
+
+
+def sigma_hot_kappa(kappa, w, eps):
+    return lib().or_sigma_hot_kappa(kappa, w, eps)
+
+
+def sample_kappa(kappa, w, n, seed=1, stream=0):
+    out = np.empty(n)
+    lib().or_sample_kappa(kappa, w, seed, stream, n, _pd(out))
+    return out
+
+
+def compton_kappa(kappa, thetae, eps, n, seed=1, stream0=0):
+    e = np.empty(n)
+    mu = np.empty(n)
+    lib().or_compton_kappa(kappa, thetae, eps, seed, stream0, n, _pd(e), _pd(mu))
+    return e, mu
 
 
 def F_sync(x):

@@ -803,6 +803,128 @@ HotTable &hot_table() {
 //  Theta <  0.25: with t = gamma - 1, f(t) <= sqrt(2) sqrt(t) (1 + 5t/4 + t^2/4) e^{-t/Theta}; draw from
 //                 that Gamma(3/2, 5/2, 7/2) mixture, accept with (1+t) sqrt(t+2) / (sqrt 2 (1 + 5t/4 + t^2/4)).
 const int MAXTRY = 10000;
+
+// ---------------------------------------------------------------- kappa electrons: scattering
+// Hot cross-section of the kappa population, sigma_h(w, eps) = <(1 - mu beta) sigma_KN(eps gamma (1 - mu beta))>,
+// tabulated as ln(sigma_h / sigma_T) on the kappa ln w grid x the thermal table's ln eps grid and
+// interpolated bilinearly (reading); the oracle's nodes by Gauss-Legendre panels in t = ln(gamma - 1)
+// (140 x 16) and, over mu, 24 Gauss-Legendre nodes in y = ln(1 - beta mu) (d mu = -e^y dy / beta), which
+// resolves the Klein-Nishina turnover that ultrarelativistic electrons confine to mu -> 1.
+struct KappaHot {
+  std::vector<double> v;   // [KAP_NW][HT_NE]
+  double lookup(double w, double eps) const {
+    double fw = (std::log(w) - KAP_LW0) / (KAP_LW1 - KAP_LW0) * (KAP_NW - 1);
+    double fe = (std::log(eps) - HT_LE0) / (HT_LE1 - HT_LE0) * (HT_NE - 1);
+    fw = std::min(std::max(fw, 0.0), (double)(KAP_NW - 1));
+    fe = std::min(std::max(fe, 0.0), (double)(HT_NE - 1));
+    int i = std::min((int)fw, KAP_NW - 2), j = std::min((int)fe, HT_NE - 2);
+    double a = fw - i, b = fe - j;
+    double l = (1 - a) * (1 - b) * v[(size_t)i * HT_NE + j] + (1 - a) * b * v[(size_t)i * HT_NE + j + 1] +
+               a * (1 - b) * v[(size_t)(i + 1) * HT_NE + j] + a * b * v[(size_t)(i + 1) * HT_NE + j + 1];
+    return SIGMA_T * std::exp(l);
+  }
+};
+
+const KappaHot &kappa_hot(double kappa) {
+  static std::mutex mu;
+  static std::map<double, KappaHot> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(kappa);
+  if (it != cache.end()) return it->second;
+  KappaHot T;
+  T.v.assign((size_t)KAP_NW * HT_NE, 0.0);
+  static const GL gp(16, 0.0, 1.0);
+  static const GL gm(24, -1.0, 1.0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < KAP_NW; ++i) {
+    const double w = std::exp(KAP_LW0 + (KAP_LW1 - KAP_LW0) * i / (KAP_NW - 1)), kw = kappa * w;
+    const double t0 = std::log(kw) - 25.0, h = 0.5;
+    std::vector<double> gam, bet, wt;
+    double norm = 0.0;
+    for (int k = 0; k < 140; ++k)
+      for (int q = 0; q < gp.n; ++q) {
+        const double t = t0 + (k + gp.x[q]) * h, e = std::exp(t), g = 1.0 + e, p = std::sqrt(e * (2.0 + e));
+        const double f = g * p * std::exp(t - (kappa + 1.0) * std::log1p(e / kw));
+        gam.push_back(g);
+        bet.push_back(p / g);
+        wt.push_back(gp.w[q] * h * f);
+        norm += gp.w[q] * h * f;
+      }
+    for (int j = 0; j < HT_NE; ++j) {
+      const double eps = std::exp(HT_LE0 + (HT_LE1 - HT_LE0) * j / (HT_NE - 1));
+      double acc = 0.0;
+      for (size_t q = 0; q < gam.size(); ++q) {
+        // (1/2) int (1 - beta mu) sigma_KN dmu = (1 / 2 beta) int_{ln(1-beta)}^{ln(1+beta)} e^{2y} sigma_KN(eps gamma e^y) dy,
+        // with ln(1 - beta) = -2 ln gamma - ln(1 + beta)
+        const double y1 = std::log1p(bet[q]), y0 = -2.0 * std::log(gam[q]) - y1;
+        double sm = 0.0;
+        for (int r = 0; r < gm.n; ++r) {
+          const double om = std::exp(0.5 * (y0 + y1) + 0.5 * (y1 - y0) * gm.x[r]);
+          sm += gm.w[r] * om * om * sigma_kn(eps * gam[q] * om);
+        }
+        acc += wt[q] * 0.5 * (0.5 * (y1 - y0)) * sm / bet[q];
+      }
+      T.v[(size_t)i * HT_NE + j] = std::log(acc / norm / SIGMA_T);
+    }
+  }
+  return cache.emplace(kappa, std::move(T)).first->second;
+}
+
+// Standard normal by the Box-Muller transform (two uniforms).
+double normal_bm(Stream &s) {
+  double u1 = 1.0 - uniform(s), u2 = uniform(s);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * PI * u2);
+}
+
+// Gamma(a) variate by the method of Marsaglia & Tsang (2000); for a < 1 from Gamma(a + 1) U^(1/a)
+// (the Gamma(a + 1) draws first, then U).
+double gamma_mt(double a, Stream &s) {
+  if (a < 1.0) {
+    const double g = gamma_mt(a + 1.0, s);
+    return g * std::pow(uniform(s), 1.0 / a);
+  }
+  const double d = a - 1.0 / 3.0, c = 1.0 / std::sqrt(9.0 * d);
+  for (int it = 0; it < MAXTRY; ++it) {
+    double x = normal_bm(s), v = 1.0 + c * x;
+    if (v <= 0.0) continue;
+    v = v * v * v;
+    double u = uniform(s);
+    if (u < 1.0 - 0.0331 * x * x * x * x) return d * v;
+    if (std::log(u) < 0.5 * x * x + d * (1.0 - v + std::log(v))) return d * v;
+  }
+  return d;
+}
+
+// Lorentz factor of a kappa electron (reading).  In u = gamma - 1 the density is
+// (1 + u) sqrt(u (2 + u)) (1 + u / (kappa w))^-(kappa+1).  It is bounded by an envelope whose terms are
+// u^(a-1) (1 + u / (kappa w))^-(kappa+1), each a scaled beta-prime(a, kappa + 1 - a) density (x = u / (kappa w)
+// = G_a / G_b, G ~ Gamma), mixed with weights from the beta-function integrals:
+//   w < 1:  sqrt2 u^1/2 (1 + u)^2, terms a = 3/2, 5/2, 7/2 (ratio to the density sqrt(1 + u/2) / (1 + u));
+//   w >= 1: (1 + u)^2,             terms a = 1, 2, 3       (ratio sqrt(1 - (1 + u)^-2)).
+// Draws: component, Gamma(a), Gamma(kappa + 1 - a), acceptance; repeated until accepted.
+double sample_kappa(double kappa, double w, Stream &s, int64_t *rejcap) {
+  const double kw = kappa * w;
+  const bool low = w < 1.0;
+  const double a1 = low ? 1.5 : 1.0;
+  // mass of each term: binomial coefficient x (kappa w)^a B(a, kappa + 1 - a), relative to the first;
+  // B(a + 1, b - 1) / B(a, b) = a / (b - 1)
+  const double b1 = kappa + 1.0 - a1;
+  const double r2 = 2.0 * kw * a1 / (b1 - 1.0);                     // term 2 / term 1
+  const double r3 = r2 * 0.5 * kw * (a1 + 1.0) / (b1 - 2.0);        // term 3 / term 1
+  const double tot = 1.0 + r2 + r3;
+  for (int it = 0; it < MAXTRY; ++it) {
+    const double uc = uniform(s) * tot;
+    const int k = uc < 1.0 ? 0 : (uc < 1.0 + r2 ? 1 : 2);
+    const double a = a1 + k;
+    const double ga = gamma_mt(a, s), gb = gamma_mt(kappa + 1.0 - a, s);
+    const double u = kw * (ga / gb);
+    const double acc = low ? std::sqrt(1.0 + 0.5 * u) / (1.0 + u) : std::sqrt(1.0 - 1.0 / ((1.0 + u) * (1.0 + u)));
+    if (uniform(s) < acc) return 1.0 + u;
+  }
+  if (rejcap) (*rejcap)++;
+  return 1.0 + kw;
+}
+
 double sample_mj(double thetae, Stream &s) {
   if (thetae >= 0.25) {
     for (int it = 0; it < MAXTRY; ++it) {
@@ -858,12 +980,12 @@ void boost(double E, const double p[3], double beta, const double v[3], double *
 // rest-frame angle from the Klein-Nishina differential cross-section (Thomson form below
 // eps_e = 1e-4), eps' = eps_e / (1 + eps_e (1 - cos)); boosted back.  Random draws in fixed order:
 // [gamma (MJ draws), mu_e, accept]*, phi_e, [cos, accept]*, phi.
-void compton_fluid(double thetae, double eps, const double n[3], Stream &s, double *eps_out, double dir_out[3],
-                   int64_t *rejcap) {
+void compton_fluid(double kappa, double thetae, double eps, const double n[3], Stream &s, double *eps_out,
+                   double dir_out[3], int64_t *rejcap) {
   double gam = 1.0, mue = 0.0, beta = 0.0;
   int it = 0;
   for (it = 0; it < MAXTRY; ++it) {
-    gam = sample_mj(thetae, s);
+    gam = kappa > 0.0 ? sample_kappa(kappa, thetae * (kappa - 3.0) / kappa, s, rejcap) : sample_mj(thetae, s);
     mue = 2.0 * uniform(s) - 1.0;
     beta = std::sqrt(1.0 - 1.0 / (gam * gam));
     double om = 1.0 - beta * mue;
@@ -1108,7 +1230,8 @@ void coefficients(const Model &M, const double X[4], const double K[4], bool wan
   c.ana += brems_nu_alpha(M.P, nu, c.F.ne, c.F.thetae);
   if (want_scatter) {
     double th = std::max(c.F.thetae, 1e-300);
-    c.ans = nu * c.F.ne * hot_table().lookup(th, eps);
+    c.ans = nu * c.F.ne * (M.P.kappa > 0.0 ? kappa_hot(M.P.kappa).lookup(th * (M.P.kappa - 3.0) / M.P.kappa, eps)
+                                           : hot_table().lookup(th, eps));
   }
 }
 
@@ -1223,7 +1346,7 @@ void scatter_child(const Model &M, const double Xe[4], const double Ke[4], doubl
   double ln = std::sqrt(kf[1] * kf[1] + kf[2] * kf[2] + kf[3] * kf[3]);
   double n[3] = {kf[1] / ln, kf[2] / ln, kf[3] / ln};
   double eo, dir[3];
-  compton_fluid(std::max(F.thetae, 1e-8), eps, n, s, &eo, dir, &acc.st.n_rej_cap);
+  compton_fluid(M.P.kappa, std::max(F.thetae, 1e-8), eps, n, s, &eo, dir, &acc.st.n_rej_cap);
   Child c;
   for (int m = 0; m < 4; ++m) c.K[m] = eo * e[0][m] + dir[0] * e[1][m] + dir[1] * e[2][m] + dir[2] * e[3][m];
   for (int m = 0; m < 4; ++m) c.X[m] = Xe[m];
@@ -1573,7 +1696,7 @@ void or_compton(double thetae, double eps, uint64_t seed, uint64_t id0, int64_t 
     Stream s{seed, id0 + (uint64_t)i, 0u};
     double nz[3] = {0.0, 0.0, 1.0};
     double eo, d[3];
-    compton_fluid(thetae, eps, nz, s, &eo, d, nullptr);
+    compton_fluid(0.0, thetae, eps, nz, s, &eo, d, nullptr);
     eps_out[i] = eo;
     for (int k = 0; k < 3; ++k) dir_out[3 * i + k] = d[k];
   }
@@ -1600,7 +1723,10 @@ void *or_create(const or_params *P, const or_grid *G) {
   M->prim.assign(G->prim, G->prim + (size_t)8 * M->nz);
   M->r_h = (P->mass > 0.0) ? 1.0 + std::sqrt(1.0 - P->a * P->a) : 0.0;
   if (P->scatter) hot_table();
-  if (P->kappa > 0.0) kappa_tables(P->kappa);
+  if (P->kappa > 0.0) {
+    kappa_tables(P->kappa);
+    if (P->scatter) kappa_hot(P->kappa);
+  }
   return M;
 }
 
@@ -1736,6 +1862,22 @@ int or_run(void *h, int64_t uid0, int64_t uid1, const int64_t *uids, int64_t nui
 
 double or_brems_q(double ne, double thetae) { return brems_q(ne, thetae); }
 double or_F_sync(double x) { return F_sync_direct(x); }
+double or_sigma_hot_kappa(double kappa, double w, double eps) { return kappa_hot(kappa).lookup(w, eps); }
+void or_sample_kappa(double kappa, double w, uint64_t seed, uint64_t stream, int64_t n, double *out) {
+  Stream s{seed, stream, 0u};
+  for (int64_t i = 0; i < n; ++i) out[i] = sample_kappa(kappa, w, s, nullptr);
+}
+void or_compton_kappa(double kappa, double thetae, double eps, uint64_t seed, uint64_t stream0, int64_t n,
+                      double *eps_out, double *mu_out) {
+  const double nz[3] = {0.0, 0.0, 1.0};
+  for (int64_t i = 0; i < n; ++i) {
+    Stream s{seed, stream0 + (uint64_t)i, 0u};
+    double eo, d[3];
+    compton_fluid(kappa, thetae, eps, nz, s, &eo, d, nullptr);
+    eps_out[i] = eo;
+    mu_out[i] = d[2] / std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  }
+}
 double or_jnu_kappa(const or_params *P, double nu, double ne, double thetae, double B, double costh) {
   return jnu(*P, nu, ne, thetae, B, costh);
 }

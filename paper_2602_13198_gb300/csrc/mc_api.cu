@@ -156,6 +156,7 @@ DevModel make_model(const mc_ctx *c) {
   m.kapJ = c->kapJ;
   m.kapA = c->kapA;
   m.kapI = c->kapI;
+  m.kapH = c->kapH;
   m.zlnw = c->zlnw;
   m.zbq = c->zbq;
   m.zbnt = c->zbnt;
@@ -288,11 +289,12 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
     c->kapJ = (double *)dev_alloc(c, sizeof(double) * kKapNX * kKapNW);
     c->kapA = (double *)dev_alloc(c, sizeof(double) * kKapNX * kKapNW);
     c->kapI = (double *)dev_alloc(c, sizeof(double) * kKapNX * kKapNW);
-    if (!c->kapF || !c->kapJ || !c->kapA || !c->kapI) {
+    c->kapH = (double *)dev_alloc(c, sizeof(double) * kKapNW * kHotNE);
+    if (!c->kapF || !c->kapJ || !c->kapA || !c->kapI || !c->kapH) {
       mc_free(c);
       return fail(nullptr, MC_ERR_OOM, "device allocation failed");
     }
-    launch_kappa_tables(p->kappa, c->kapF, c->kapJ, c->kapA, c->kapI, 0);
+    launch_kappa_tables(p->kappa, c->kapF, c->kapJ, c->kapA, c->kapI, c->kapH, c->gl + 256, 0);
   }
   DevModel m = make_model(c);
   launch_tables(m, c->lnF, c->lnK2, c->hot, c->gl, c->gl + 128, c->gl + 256, 0);

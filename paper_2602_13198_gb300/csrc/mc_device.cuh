@@ -72,6 +72,7 @@ struct DevModel {
   int brems;              // thermal bremsstrahlung on
   double kappa;           // > 0: kappa-distributed electrons for the synchrotron terms
   const double *kapJ, *kapA, *kapI;   // ln J, ln A, ln I on the kappa grid [kKapNX][kKapNW]
+  const double *kapH;     // ln(sigma_h / sigma_T) of the kappa population [kKapNW][kHotNE]
   const double *zlnw;     // per zone: ln w of the kappa population (kappa only)
   double *zbq, *zbnt;     // per zone: q / nu_T and nu_T = k T_e / h (bremsstrahlung only)
   const double *zlnuc;    // ln nu_c per zone
@@ -466,6 +467,22 @@ __device__ __forceinline__ double kappa_nu_alpha(const DevModel &m, double ne, d
   return kCa * ne * B * sth * kap_interp(m.kapA, lx, lw) / nu;
 }
 
+// Hot cross-section of the kappa population, bilinear in (ln w, ln eps) on the kappa w grid and the
+// thermal table's eps grid (clamped to both)
+__device__ __forceinline__ double kap_hot_lookup(const DevModel &m, double thetae, double eps) {
+  constexpr double sw = (kKapNW - 1) / (kKapLW1 - kKapLW0), se = (kHotNE - 1) / (kHotLE1 - kHotLE0);
+  double fw = (log(fmax(thetae, 1e-300) * (m.kappa - 3.0) / m.kappa) - kKapLW0) * sw;
+  double fe = (log(eps) - kHotLE0) * se;
+  fw = fmin(fmax(fw, 0.0), (double)(kKapNW - 1));
+  fe = fmin(fmax(fe, 0.0), (double)(kHotNE - 1));
+  int i = min((int)fw, kKapNW - 2), j = min((int)fe, kHotNE - 2);
+  double a = fw - i, b = fe - j;
+  const double *h = m.kapH;
+  double v00 = h[i * kHotNE + j], v01 = h[i * kHotNE + j + 1];
+  double v10 = h[(i + 1) * kHotNE + j], v11 = h[(i + 1) * kHotNE + j + 1];
+  return kSIGT * exp((1 - a) * (1 - b) * v00 + (1 - a) * b * v01 + a * (1 - b) * v10 + a * b * v11);
+}
+
 // ---------------------------------------------------------------- bremsstrahlung (future work in section 6)
 // Total thermal bremsstrahlung cooling rate of a hydrogen plasma [erg s^-1 cm^-3], electron-ion plus
 // electron-electron, from the fits of Stepney & Guilbert (1983) in the form of Narayan & Yi (1995);
@@ -745,7 +762,7 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
     }
   }
   if (m.brems) c.ana += brems_nu_alpha(P.ne, P.thetae, nu);
-  if (want_s) c.ans = nu * P.ne * hot_lookup_ln(m, lt, log(eps));
+  if (want_s) c.ans = nu * P.ne * (m.kappa > 0.0 ? kap_hot_lookup(m, P.thetae, eps) : hot_lookup_ln(m, lt, log(eps)));
 }
 
 // Mixed precision: the same quantities with FP32 plasma state and coefficient arithmetic.
@@ -798,8 +815,12 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, 
   // bremsstrahlung absorption in FP64 (n_e^2 leaves the FP32 range in dense plasma)
   if (m.brems) c.ana += brems_nu_alpha((double)P.ne, (double)P.thetae, (double)nu9 * 1e9);
   if (want_s) {
-    float sh = hot_lookup_f(m, fmaxf(P.thetae, 1e-30f), eps);
-    c.ans = (double)(nu9 * P.ne * (sh * 1e9f));
+    if (m.kappa > 0.0) {
+      c.ans = (double)nu9 * 1e9 * (double)P.ne * kap_hot_lookup(m, (double)P.thetae, (double)eps);
+    } else {
+      float sh = hot_lookup_f(m, fmaxf(P.thetae, 1e-30f), eps);
+      c.ans = (double)(nu9 * P.ne * (sh * 1e9f));
+    }
   }
 }
 
@@ -1009,6 +1030,57 @@ static __device__ double sample_mj(double th, Rng &s, uint64_t seed) {
   return 1.0 + t;
 }
 
+// Gamma(a) variate (Marsaglia & Tsang 2000), normals by Box-Muller from two uniforms; a < 1 through
+// Gamma(a + 1) U^(1/a), the Gamma(a + 1) drawn first.
+static __device__ double gamma_mt(double a, Rng &s, uint64_t seed) {
+  double boost = -1.0;
+  if (a < 1.0) {
+    boost = 1.0 / a;
+    a += 1.0;
+  }
+  const double d = a - 1.0 / 3.0, c = rsqrt(9.0 * d);
+  double g = d;
+  for (int it = 0; it < kMaxTry; ++it) {
+    const double u1 = rng_u(s, seed), u2 = rng_u(s, seed);
+    const double x = sqrt(-2.0 * log(1.0 - u1)) * cospi(2.0 * u2);
+    double v = 1.0 + c * x;
+    if (v <= 0.0) continue;
+    v = v * v * v;
+    const double u = rng_u(s, seed);
+    if (u < 1.0 - 0.0331 * (x * x) * (x * x) || log(u) < 0.5 * x * x + d * (1.0 - v + log(v))) {
+      g = d * v;
+      break;
+    }
+  }
+  if (boost > 0.0) g *= pow(rng_u(s, seed), boost);
+  return g;
+}
+
+// Lorentz factor of a kappa electron: u = gamma - 1 has density (1 + u) sqrt(u (2 + u)) (1 + u/kw)^-(kappa+1),
+// kw = kappa w.  Rejection from a three-term envelope, each term u^(a-1) (1 + u/kw)^-(kappa+1) drawn as
+// u = kw G_a / G_(kappa+1-a): for w < 1 the envelope sqrt2 u^1/2 (1 + u)^2 (a = 3/2, 5/2, 7/2; acceptance
+// sqrt(1 + u/2) / (1 + u)), otherwise (1 + u)^2 (a = 1, 2, 3; acceptance sqrt(1 - (1 + u)^-2)).  Term masses
+// follow from B(a + 1, b - 1) / B(a, b) = a / (b - 1).
+static __device__ double sample_kappa(double kappa, double w, Rng &s, uint64_t seed, int &rejcap) {
+  const double kw = kappa * w;
+  const bool low = w < 1.0;
+  const double a1 = low ? 1.5 : 1.0, b1 = kappa + 1.0 - a1;
+  const double r2 = 2.0 * kw * a1 / (b1 - 1.0);
+  const double r3 = r2 * (0.5 * kw * (a1 + 1.0) / (b1 - 2.0));
+  const double tot = 1.0 + r2 + r3;
+  for (int it = 0; it < kMaxTry; ++it) {
+    const double uc = rng_u(s, seed) * tot;
+    const double a = a1 + (uc < 1.0 ? 0.0 : (uc < 1.0 + r2 ? 1.0 : 2.0));
+    const double ga = gamma_mt(a, s, seed);
+    const double gb = gamma_mt(kappa + 1.0 - a, s, seed);
+    const double u = kw * (ga / gb);
+    const double acc = low ? sqrt(1.0 + 0.5 * u) / (1.0 + u) : sqrt(1.0 - 1.0 / ((1.0 + u) * (1.0 + u)));
+    if (rng_u(s, seed) < acc) return 1.0 + u;
+  }
+  rejcap++;
+  return 1.0 + kw;
+}
+
 __device__ __forceinline__ void perp_basis(const double n[3], double e1[3], double e2[3]) {
   double a0 = 1.0, a1 = 0.0;
   if (fabs(n[0]) >= 0.6) { a0 = 0.0; a1 = 1.0; }
@@ -1036,12 +1108,13 @@ __device__ __forceinline__ void boost3(double E, const double p[3], double beta,
 
 // Scattered photon in the plasma frame for incoming energy eps along unit n; draws in the order
 // [gamma (MJ), mu_e, accept]*, phi_e, [cos, accept]*, phi.
-static __device__ void compton_fluid(double th, double eps, const double n[3], Rng &s, uint64_t seed, double &eo,
-                              double dir[3], int &rejcap) {
+// kappa > 0: kappa-distributed electrons of temperature-like parameter w = th (kappa - 3) / kappa.
+static __device__ void compton_fluid(double kappa, double th, double eps, const double n[3], Rng &s, uint64_t seed,
+                                     double &eo, double dir[3], int &rejcap) {
   double gam = 1.0, mue = 0.0, beta = 0.0;
   int it;
   for (it = 0; it < kMaxTry; ++it) {
-    gam = sample_mj(th, s, seed);
+    gam = kappa > 0.0 ? sample_kappa(kappa, th * (kappa - 3.0) / kappa, s, seed, rejcap) : sample_mj(th, s, seed);
     mue = 2.0 * rng_u(s, seed) - 1.0;
     beta = sqrt(1.0 - 1.0 / (gam * gam));
     double om = 1.0 - beta * mue;

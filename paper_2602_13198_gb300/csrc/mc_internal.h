@@ -90,7 +90,8 @@ void launch_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, in
 // FMA-chain throughput of the FP64 or FP32 pipe in FLOP/s (mc_tables.cu)
 cudaError_t fma_peak(bool fp64, double *flops);
 cudaError_t selftest_math(int which, const double *x_dev, double *y_dev, double *ref_dev, int64_t n);
-void launch_kappa_tables(double kappa, double *lnF, double *lnJ, double *lnA, double *lnI, cudaStream_t st);
+void launch_kappa_tables(double kappa, double *lnF, double *lnJ, double *lnA, double *lnI, double *lnH,
+                         const double *gl_mu, cudaStream_t st);
 // transport (mc_transport.cu)
 int push_max_blocks_per_sm(int mixed, int phase, int block, int kerr);
 void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st);
@@ -122,6 +123,7 @@ struct mc_ctx {
   double *zbq = nullptr, *zbnt = nullptr;   // per-zone bremsstrahlung normalisation and k T_e / h
   double *zlnw = nullptr;                   // per-zone ln w of the kappa population
   double *kapF = nullptr, *kapJ = nullptr, *kapA = nullptr, *kapI = nullptr;   // kappa tables
+  double *kapH = nullptr;                   // kappa hot cross-section [kKapNW][kHotNE]
   int prim_f32 = 0;
   int n1 = 0, n2 = 0, n3 = 0;
   int64_t nz = 0;

@@ -177,7 +177,7 @@ static __device__ void child_kinematics(const DevModel &m, const double Xe[4], c
   rng_init(s, cid, 0u);
   double eo, dir[3];
   int rej = 0;
-  compton_fluid(fmax(P.thetae, 1e-8), eps, n, s, m.seed, eo, dir, rej);
+  compton_fluid(m.kappa, fmax(P.thetae, 1e-8), eps, n, s, m.seed, eo, dir, rej);
   ls.rejcap += rej;
 #pragma unroll
   for (int q = 0; q < 4; ++q) Kc[q] = eo * e[0][q] + dir[0] * e[1][q] + dir[1] * e[2][q] + dir[2] * e[3][q];

@@ -145,11 +145,51 @@ __global__ void k_kap_I(const double *lnJ, double *lnI) {
   lnI[node] = s > 0.0 ? fmax(kKapFloor, log(s)) : kKapFloor;
 }
 
-void launch_kappa_tables(double kappa, double *lnF, double *lnJ, double *lnA, double *lnI, cudaStream_t st) {
+// ln(sigma_h / sigma_T) of the kappa population at one (w, eps) node, one warp per node: the average of
+// (1 - beta mu) sigma_KN(eps gamma (1 - beta mu)) / sigma_T over the population (trapezoid rule in
+// t = ln(gamma - 1) over [ln(kappa w) - 25, ln(kappa w) + 45] with step 0.02, normalised by the same rule)
+// and over mu, as 32-point Gauss-Legendre in y = ln(1 - beta mu) on [ln(1 - beta), ln(1 + beta)]
+// (d mu = -e^y dy / beta; the Klein-Nishina turnover of fast electrons sits at mu -> 1, where y spreads
+// it out); lanes take every 32nd t, then a shuffle reduction.
+__global__ void k_kap_hot(double kappa, const double *gmx, const double *gmw, double *lnH) {
+  const int node = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (node >= kKapNW * kHotNE) return;   // whole warps leave together
+  const int iw = node / kHotNE, je = node % kHotNE;
+  const double w = exp(kKapLW0 + (kKapLW1 - kKapLW0) * iw / (kKapNW - 1));
+  const double e = exp(kHotLE0 + (kHotLE1 - kHotLE0) * je / (kHotNE - 1));
+  const double kw = kappa * w, t0 = log(kw) - 25.0, h = 0.02;
+  const int n = 3500;
+  double num = 0.0, den = 0.0;
+  for (int k = lane; k <= n; k += 32) {
+    const double t = t0 + k * h, x = exp(t), g = 1.0 + x, p = sqrt(x * (2.0 + x));
+    const double f = ((k == 0 || k == n) ? 0.5 : 1.0) * g * p * exp(t - (kappa + 1.0) * log1p(x / kw));
+    const double beta = p / g;
+    const double y1 = log1p(beta), y0 = -2.0 * log(g) - y1;   // 1 - beta = 1 / (gamma^2 (1 + beta))
+    const double ym = 0.5 * (y0 + y1), yh = 0.5 * (y1 - y0);
+    double q = 0.0;
+    for (int b = 0; b < 32; ++b) {
+      const double om = exp(ym + yh * gmx[b]);
+      q += gmw[b] * om * om * sigma_kn_ratio(e * g * om);
+    }
+    num += f * 0.5 * q * yh / beta;
+    den += f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if (lane == 0) lnH[node] = log(num / den);
+}
+
+void launch_kappa_tables(double kappa, double *lnF, double *lnJ, double *lnA, double *lnI, double *lnH,
+                         const double *gl_mu, cudaStream_t st) {
   k_kap_F<<<(kKapNF + 127) / 128, 128, 0, st>>>(lnF);
   const int nn = kKapNX * kKapNW;
   k_kap_JA<<<(nn + 127) / 128, 128, 0, st>>>(lnF, kappa, lnJ, lnA);
   k_kap_I<<<(nn + 127) / 128, 128, 0, st>>>(lnJ, lnI);
+  const int nh = kKapNW * kHotNE;   // one warp per node, four per block
+  k_kap_hot<<<(nh + 3) / 4, 128, 0, st>>>(kappa, gl_mu, gl_mu + 32, lnH);
 }
 
 // ---------------------------------------------------------------- grid layout
