@@ -88,7 +88,8 @@ __device__ __forceinline__ unsigned long long vload(const unsigned long long *p)
 }
 
 // Persistent loop of one phase over list_in[0, n_in); superphotons that change phase are appended
-// to list_out through out_cnt.  With the surrogate, the in-grid phase runs in CTA lockstep.
+// to list_out through out_cnt.  With the surrogate, the in-grid phase runs in lockstep per 128-thread
+// row group (the network's tile), each group on its own named barrier.
 template <bool MIXED, int PHASE, bool SUR>
 __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &io, const int32_t *list_in,
                             int64_t n_in, unsigned long long *cursor, int32_t *list_out, unsigned long long *out_cnt,
@@ -119,8 +120,10 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
       }
     }
     if (SUR && PHASE == 0) {
-      if (!__syncthreads_or(live ? 1 : 0)) {
-        if (!__syncthreads_or(exhausted ? 0 : 1)) break;
+      // the row group (128 threads) moves in lockstep; the two groups of a CTA do not
+      const int grp = threadIdx.x >> 7;
+      if (!group_or(grp, live)) {
+        if (!group_or(grp, !exhausted)) break;
         continue;
       }
       float in[3] = {0.0f, 0.0f, 0.0f}, out[3];

@@ -122,30 +122,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Named barrier of one 128-thread row group (ids 1 and 2; id 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int grp) {
+  if (grp == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
+  else asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
+// OR of a predicate over the 128 threads of a row group (every thread gets the result).
+__device__ __forceinline__ bool group_or(int grp, bool v) {
+  uint32_t r;
+  if (grp == 0)
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+  return r != 0;
+}
+
 // z sigmoid(z) with the fast reciprocal division (a few ulp; the BF16 split keeps ~16 bits)
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
-// Per-CTA state of the tensor-core MLP: shared-memory tiles, TMEM base, mbarrier and its phase.
-// A CTA of 128 x G threads evaluates G groups of 128 rows (G = 1 or 2); group g has its own A tiles
-// and accumulates in TMEM columns [64 g, 64 g + 64).  The tensor-memory kernels run one CTA per SM,
-// so two groups are how an SM gets eight warps of the surrogate transport.
+// Per-CTA state of the tensor-core MLP: shared-memory tiles, TMEM base, one mbarrier and phase per
+// row group.  A CTA of 128 x G threads evaluates G groups of 128 rows (G = 1 or 2); group g has its
+// own A tiles, accumulates in TMEM columns [64 g, 64 g + 64), and synchronises on its own named
+// barrier: the first thread of the group issues its MMAs and commits them to the group's mbarrier.
+// The groups run independently, so one group's FP64 transport overlaps the other's network wait.
+// The tensor-memory kernels run one CTA per SM, so two groups are how an SM gets eight warps.
 constexpr int kTcGroupsMax = 2;
 struct TcMlp {
   unsigned char *a1[kTcGroupsMax], *a2[kTcGroupsMax], *a2l[kTcGroupsMax];   // per-group A tiles
   unsigned char *b1, *b2, *b2l, *b3, *b3l;                                  // shared weight tiles
   const float *bias;                        // b1 b2 b3 in shared memory
-  uint32_t tmem, mbar, phase;
+  uint32_t tmem, mbar[kTcGroupsMax], phase[kTcGroupsMax];
   int groups;
   unsigned int *err;
 };
 
 // Shared memory needed by one CTA of `groups` row groups (tiles + biases + mbarrier + TMEM slot).
 __host__ __device__ constexpr int tc_smem_bytes(int groups) {
-  return groups * (kTileA1 + 2 * kTileA2) + kPackedBytes + 4 * (64 + 64 + 16) + 64;
+  return groups * (kTileA1 + 2 * kTileA2) + kPackedBytes + 4 * (64 + 64 + 16) + 8 * kTcGroupsMax + 64;
 }
 
 // Set-up by all threads of the CTA (blockDim.x = 128 or 256): carve shared memory, copy packed
-// weights and biases, initialise the mbarrier, warp 0 allocates kTmemCols TMEM columns.
+// weights and biases, initialise the groups' mbarriers, warp 0 allocates kTmemCols TMEM columns.
 __device__ __forceinline__ void tc_setup(TcMlp &T, unsigned char *smem, const SurrogateView &sv) {
   const int G = (int)(blockDim.x >> 7);
   T.groups = G;
@@ -161,7 +189,7 @@ __device__ __forceinline__ void tc_setup(TcMlp &T, unsigned char *smem, const Su
   T.b3l = T.b3 + kTileB3;
   float *bias = (float *)(T.b3l + kTileB3);
   uint64_t *mb = (uint64_t *)(bias + 64 + 64 + 16);
-  uint32_t *tslot = (uint32_t *)(mb + 1);
+  uint32_t *tslot = (uint32_t *)(mb + kTcGroupsMax);
   const int tid = threadIdx.x;
   const uint4 *src = (const uint4 *)sv.packed;
   uint4 *dst = (uint4 *)T.b1;
@@ -169,15 +197,18 @@ __device__ __forceinline__ void tc_setup(TcMlp &T, unsigned char *smem, const Su
   for (int i = tid; i < 64 + 64 + 16; i += blockDim.x) bias[i] = (i < 128 + 3) ? sv.bias[i] : 0.0f;
   T.bias = bias;
   T.err = sv.err;
-  T.mbar = smem_addr(mb);
-  if (tid == 0) mbar_init(T.mbar, 1);
+  for (int g = 0; g < kTcGroupsMax; ++g) {
+    T.mbar[g] = smem_addr(mb + g);
+    T.phase[g] = 0;
+  }
+  if (tid == 0)
+    for (int g = 0; g < G; ++g) mbar_init(T.mbar[g], 1);
   if ((tid >> 5) == 0) tmem_alloc(smem_addr(tslot), kTmemCols);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   T.tmem = *tslot;
-  T.phase = 0;
 }
 
 __device__ __forceinline__ void tc_teardown(TcMlp &T) {
@@ -187,33 +218,31 @@ __device__ __forceinline__ void tc_teardown(TcMlp &T) {
   if ((threadIdx.x >> 5) == 0) tmem_dealloc(T.tmem, kTmemCols);
 }
 
-// One layer: for every row group g, D_g[128 x N] = sum over the np (A, B) pairs of A_g[128 x K] B[N x K]^T
-// in TMEM columns [64 g, 64 g + N), issued by thread 0; returns after every thread has seen the
-// MMAs complete.
-__device__ __forceinline__ bool tc_layer(TcMlp &T, const unsigned char *const (*as)[3], const unsigned char *const *bs,
-                                         int np, int K, int N) {
+// One layer of row group g: D_g[128 x N] = sum over the np (A, B) pairs of A_g[128 x K] B[N x K]^T in
+// TMEM columns [64 g, 64 g + N), issued by the group's first thread; returns after every thread of
+// the group has seen the MMAs complete.
+__device__ __forceinline__ bool tc_layer(TcMlp &T, int g, const unsigned char *const *as,
+                                         const unsigned char *const *bs, int np, int K, int N) {
   fence_async_smem();
   tc_fence_before();
-  __syncthreads();
+  group_sync(g);
   tc_fence_after();
-  if (threadIdx.x == 0) {
+  if ((threadIdx.x & 127) == 0) {
     const uint32_t sbo = (K / 8) * 128;
     const uint32_t id = idesc_bf16(128, N);
-    for (int g = 0; g < T.groups; ++g) {
-      for (int p = 0; p < np; ++p) {
-        const uint32_t ab = smem_addr(as[g][p]), bb = smem_addr(bs[p]);
-        for (int k = 0; k < K / 16; ++k) {
-          // advancing 16 elements along K = two core matrices = 256 bytes
-          uint64_t da = umma_desc(ab + k * 256, 128, sbo);
-          uint64_t db = umma_desc(bb + k * 256, 128, sbo);
-          tc_mma(T.tmem + 64u * g, da, db, id, (p > 0 || k > 0) ? 1u : 0u);
-        }
+    for (int p = 0; p < np; ++p) {
+      const uint32_t ab = smem_addr(as[p]), bb = smem_addr(bs[p]);
+      for (int k = 0; k < K / 16; ++k) {
+        // advancing 16 elements along K = two core matrices = 256 bytes
+        uint64_t da = umma_desc(ab + k * 256, 128, sbo);
+        uint64_t db = umma_desc(bb + k * 256, 128, sbo);
+        tc_mma(T.tmem + 64u * g, da, db, id, (p > 0 || k > 0) ? 1u : 0u);
       }
     }
-    tc_commit(T.mbar);
+    tc_commit(T.mbar[g]);
   }
-  bool ok = mbar_wait_bounded(T.mbar, T.phase, T.err);
-  T.phase ^= 1u;
+  bool ok = mbar_wait_bounded(T.mbar[g], T.phase[g], T.err);
+  T.phase[g] ^= 1u;
   tc_fence_after();
   return ok;
 }
@@ -241,7 +270,7 @@ __device__ __forceinline__ void put_hidden(TcMlp &T, int grp, int row, const flo
   }
 }
 
-// Evaluates the network for this thread's row (all threads of the CTA must call it).
+// Evaluates the network for this thread's row (all 128 threads of the thread's row group must call it).
 // in[3]: normalised inputs; out[3]: raw outputs.  Returns false if a wait timed out.
 __device__ __forceinline__ bool tc_mlp_eval(TcMlp &T, const float in[3], float out[3]) {
   const int grp = threadIdx.x >> 7, row = threadIdx.x & 127;
@@ -263,32 +292,32 @@ __device__ __forceinline__ bool tc_mlp_eval(TcMlp &T, const float in[3], float o
     *(uint4 *)(T.a1[grp] + kmajor_off(row, 0, 16)) = *(uint4 *)v;
     *(uint4 *)(T.a1[grp] + kmajor_off(row, 8, 16)) = *(uint4 *)(v + 8);
   }
-  const unsigned char *a_l1[kTcGroupsMax][3] = {{T.a1[0], nullptr, nullptr}, {T.a1[1], nullptr, nullptr}};
+  const unsigned char *a_l1[1] = {T.a1[grp]};
   const unsigned char *b_l1[1] = {T.b1};
-  bool ok = tc_layer(T, a_l1, b_l1, 1, 16, 64);
+  bool ok = tc_layer(T, grp, a_l1, b_l1, 1, 16, 64);
   float h[64];
 #pragma unroll
   for (int c = 0; c < 64; c += 16) tmem_ld16(tbase + c, h + c);
 #pragma unroll
   for (int c = 0; c < 64; ++c) h[c] = silu_f(h[c] + T.bias[c]);
   put_hidden(T, grp, row, h);
-  const unsigned char *a_l2[kTcGroupsMax][3] = {{T.a2[0], T.a2l[0], T.a2[0]}, {T.a2[1], T.a2l[1], T.a2[1]}};
+  const unsigned char *a_l2[3] = {T.a2[grp], T.a2l[grp], T.a2[grp]};
   const unsigned char *b_l2[3] = {T.b2, T.b2, T.b2l};
-  ok = tc_layer(T, a_l2, b_l2, 3, 64, 64) && ok;
+  ok = tc_layer(T, grp, a_l2, b_l2, 3, 64, 64) && ok;
 #pragma unroll
   for (int c = 0; c < 64; c += 16) tmem_ld16(tbase + c, h + c);
 #pragma unroll
   for (int c = 0; c < 64; ++c) h[c] = silu_f(h[c] + T.bias[64 + c]);
   put_hidden(T, grp, row, h);   // the layer-2 MMAs have completed, so A2 may be overwritten
   const unsigned char *b_l3[3] = {T.b3, T.b3, T.b3l};
-  ok = tc_layer(T, a_l2, b_l3, 3, 64, 16) && ok;
+  ok = tc_layer(T, grp, a_l2, b_l3, 3, 64, 16) && ok;
   float y[16];
   tmem_ld16(tbase, y);
   out[0] = y[0] + T.bias[128];
   out[1] = y[1] + T.bias[129];
   out[2] = y[2] + T.bias[130];
   tc_fence_before();
-  __syncthreads();   // TMEM and A tiles free for the next evaluation
+  group_sync(grp);   // the group's TMEM columns and A tiles free for its next evaluation
   tc_fence_after();
   return ok;
 }

@@ -112,9 +112,9 @@ __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
   flush_stats(ls, io.cnt);
 }
 
-// Persistent in-grid push with the network; every thread of the CTA reaches the same tensor-core
-// evaluation once per iteration (idle lanes contribute a zero row), and the loop ends for the
-// whole CTA together.
+// Persistent in-grid push with the network.  Each 128-thread row group reaches its tensor-core
+// evaluation once per iteration (idle lanes contribute a zero row) and leaves the loop as a whole;
+// the CTA's two groups iterate independently and meet again only at the teardown.
 __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, PushIO io, SurrogateView sv) {
   extern __shared__ __align__(128) unsigned char smem_sur[];
   TcMlp T;
@@ -146,8 +146,9 @@ __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, Pus
         }
       }
     }
-    if (!__syncthreads_or(live ? 1 : 0)) {
-      if (!__syncthreads_or(exhausted ? 0 : 1)) break;
+    const int grp = threadIdx.x >> 7;   // each 128-thread row group moves in lockstep on its own
+    if (!group_or(grp, live)) {
+      if (!group_or(grp, !exhausted)) break;
       continue;
     }
     float in[3] = {0.0f, 0.0f, 0.0f}, out[3];

@@ -93,3 +93,29 @@ def test_batch_rejects_mixed_modes():
     with pytest.raises(mc.MCError) as e:
         mc.run_batch([a, b], [1e3, 1e3], [1, 2])
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_mixes_electron_models(precision):
+    # thermal, kappa (emission, absorption and scattering) and bremsstrahlung models share one launch;
+    # each model reads its own tables through its descriptor
+    from paper_2602_13198_gb300 import mc
+    models = [synth.torus(seed=201, a=0.5, n1=48, n2=24, kappa=4.0),
+              synth.scattering_sphere(0.1, n1=128, n2=32, kappa=5.0),
+              synth.torus(seed=202, a=0.0, n1=48, n2=24, brems=1),
+              synth.torus(seed=203, a=0.9, n1=48, n2=24)]
+    ns = [2e4, 1e4, 2e4, 1e4]
+    seeds = [31, 32, 33, 34]
+    ref = individual(models, ns, seeds, precision)
+    ctxs = []
+    for p, g in models:
+        m = mc.Model(p, precision=precision)
+        m.set_grid(g)
+        ctxs.append(m)
+    st = mc.run_batch(ctxs, ns, seeds, autotune=False, graph=False)
+    assert st["n_emit"] == sum(r[0]["n_emit"] for r in ref)
+    assert st["n_child"] == sum(r[0]["n_child"] for r in ref) and st["n_child"] > 0
+    for m, (rs, rspec) in zip(ctxs, ref):
+        s = m.spectrum_sums()
+        assert np.array_equal(s[..., 2], rspec[..., 2])
+        assert np.allclose(s[..., :2], rspec[..., :2], rtol=1e-11, atol=0)
