@@ -209,8 +209,11 @@ int mc_fma_peak(int device, int dtype, double *flops);
 /* Test hook: evaluates, on the current device, one of the library's own implementations of a
  * special function next to CUDA's for the same inputs.  which = 0: sine of |x| < 1/2 by the Taylor
  * series used in the metric (ref: CUDA sin); 1: its cosine (ref: CUDA cos); 2: x^(1/6) by the
- * FP32-seeded Newton iteration used in the synchrotron function (ref: cbrt(sqrt(x))).  x, y, ref
- * are n host doubles (caller-owned).  Errors: INVALID_ARG, NO_DEVICE, CUDA. */
+ * FP32-seeded Newton iteration used in the synchrotron function (ref: cbrt(sqrt(x))); 3: e^x in
+ * double-float arithmetic, as the mixed-precision geodesic evaluates r = e^x1 (ref: CUDA exp,
+ * |x| < 80); 4, 5: sin(pi x), cos(pi x) in double-float (ref: CUDA sincospi).  Inputs 3-5 are split
+ * to double-float first and results joined back to double.  x, y, ref are n host doubles
+ * (caller-owned).  Errors: INVALID_ARG, NO_DEVICE, CUDA. */
 int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t n);
 
 /* Zone superphoton counts for (N_s, seed) -- the same numbers mc_run computes and

@@ -157,6 +157,21 @@ DevModel make_model(const mc_ctx *c) {
   m.kapA = c->kapA;
   m.kapI = c->kapI;
   m.kapH = c->kapH;
+  m.dmass = df_const(m.mass);
+  m.da = df_const(m.a);
+  m.dx1_0 = df_const(m.x1_0);
+  m.dx1_hi = df_const(m.x1_hi);
+  m.dr_record = df_const(m.r_record);
+  m.dr_capture = df_const(m.r_capture);
+  m.dpi2hh = df_const(kPI * (1.0 - p.hslope));
+  m.dhh_pi = df_const((1.0 - p.hslope) / (2.0 * kPI));
+  m.dd2th = df_const(-2.0 * kPI * kPI * (1.0 - p.hslope));
+  m.dtab = c->dtab;
+  m.fidx1 = (float)m.idx1;
+  m.fidx2 = (float)m.idx2;
+  m.fidx3 = (float)m.idx3;
+  m.fx2_0 = (float)m.x2_0;
+  m.fx3_0 = (float)m.x3_0;
   m.zlnw = c->zlnw;
   m.zbq = c->zbq;
   m.zbnt = c->zbnt;
@@ -253,6 +268,7 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
   c->lnK2 = (double *)dev_alloc(c, sizeof(double) * c->nK2);
   c->hot = (double *)dev_alloc(c, sizeof(double) * kHotNT * kHotNE);
   c->gl = (double *)dev_alloc(c, sizeof(double) * (128 + 128 + 64));
+  c->dtab = (df *)dev_alloc(c, sizeof(df) * kDfTabN);
   c->cnt = (unsigned long long *)dev_alloc(c, sizeof(unsigned long long) * CNT_N);
   c->total_dev = (int64_t *)dev_alloc(c, sizeof(int64_t));
   size_t nspec = (size_t)p->n_incl * p->n_bins * 3;
@@ -280,6 +296,12 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
   gauss_legendre(64, 0.0, 0.5 * kPI, gl.data(), gl.data() + 64);      // angle integral
   gauss_legendre(64, 0.0, 8.0, gl.data() + 128, gl.data() + 192);     // hot cross-section, s
   gauss_legendre(32, -1.0, 1.0, gl.data() + 256, gl.data() + 288);    // hot cross-section, mu
+  df dft[kDfTabN];
+  df_table_host(dft);
+  if (!c->dtab || cudaMemcpy(c->dtab, dft, sizeof(dft), cudaMemcpyHostToDevice) != cudaSuccess) {
+    mc_free(c);
+    return fail(nullptr, MC_ERR_CUDA, "table upload failed");
+  }
   if (cudaMemcpy(c->gl, gl.data(), sizeof(double) * 320, cudaMemcpyHostToDevice) != cudaSuccess) {
     mc_free(c);
     return fail(nullptr, MC_ERR_CUDA, "table upload failed");
@@ -783,7 +805,7 @@ int mc_get_bias_scales(mc_ctx *c, double *scales, int n) {
 }
 
 int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t n) {
-  if (which < 0 || which > 2 || n < 0 || (n > 0 && (!x || !y || !ref))) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
+  if (which < 0 || which > 5 || n < 0 || (n > 0 && (!x || !y || !ref))) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();

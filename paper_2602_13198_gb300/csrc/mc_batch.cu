@@ -95,10 +95,10 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
                             int64_t n_in, unsigned long long *cursor, int32_t *list_out, unsigned long long *out_cnt,
                             TcMlp &T, LocalStats &ls) {
   const int lane = threadIdx.x & 31;
-  Ph p;
+  PhT<GeoScalar<MIXED>> p;   // double-float geodesic in the mixed-precision form
   int64_t slot = -1;
   bool live = false, exhausted = (n_in == 0);
-  SurCarry sc;
+  SurCarry<GeoScalar<MIXED>> sc;
   while (true) {
     if (!exhausted) {
       unsigned idle = __ballot_sync(0xffffffffu, !live);

@@ -9,8 +9,10 @@
 // per superphoton, tetrads, and the thermal Compton kinematics (section 2.7).
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
+#include "mc_df.cuh"
 #include "mc_mlp.cuh"
 
 namespace mcgb {
@@ -70,6 +72,10 @@ struct DevModel {
   const int64_t *start;   // exclusive scan of zone counts
   const double *zpref;    // 4 pi A nu_c per zone (int dOmega j_nu = zpref F(nu/nu_c))
   int brems;              // thermal bremsstrahlung on
+  df dmass, da, dx1_0, dx1_hi, dr_record, dr_capture;   // double-float splits for the mixed geodesic
+  df dpi2hh, dhh_pi, dd2th;   // pi (1 - h), (1 - h) / (2 pi), -2 pi^2 (1 - h): the theta map in double-float
+  const df *dtab;             // double-float function table (kDfTabN entries)
+  float fidx1, fidx2, fidx3, fx2_0, fx3_0;   // FP32 grid constants for the double-float zone lookup
   double kappa;           // > 0: kappa-distributed electrons for the synchrotron terms
   const double *kapJ, *kapA, *kapI;   // ln J, ln A, ln I on the kappa grid [kKapNX][kKapNW]
   const double *kapH;     // ln(sigma_h / sigma_T) of the kappa population [kKapNW][kHotNE]
@@ -138,14 +144,17 @@ constexpr uint64_t kZoneTag = 0xC000000000000000ull;
 
 // ---------------------------------------------------------------- metric (section 2.4)
 // Nonzero components of the MKS Kerr-Schild metric (symmetric): 00 01 03 11 13 22 33; its
-// inverse has 00 01 11 13 22 33.  d1 / d2: derivatives with respect to x1 and x2.
-struct Geo {
-  double g00, g01, g03, g11, g13, g22, g33;
-  double G00, G01, G11, G13, G22, G33;
-  double d100, d101, d103, d111, d113, d122, d133;
-  double d200, d201, d203, d211, d213, d222, d233;
-  double r, sth, cth;
+// inverse has 00 01 11 13 22 33.  d1 / d2: derivatives with respect to x1 and x2.  S is the
+// scalar of the geodesic arithmetic: double (plain FP64) or df (double-float, mixed precision).
+template <typename S>
+struct GeoT {
+  S g00, g01, g03, g11, g13, g22, g33;
+  S G00, G01, G11, G13, G22, G33;
+  S d100, d101, d103, d111, d113, d122, d133;
+  S d200, d201, d203, d211, d213, d222, d233;
+  S r, sth, cth;
 };
+using Geo = GeoT<double>;
 
 // theta(x2) = pi x2 + (1-h)/2 sin(2 pi x2) and its first two derivatives.
 __device__ __forceinline__ void theta_map(double h, double x2, double &th, double &dth, double &d2th) {
@@ -177,41 +186,61 @@ __device__ __forceinline__ void sincos_small(double d, double &s, double &c) {
 // delta = (1-h)/2 sin(2 pi x2): sin and cos of theta come from sincospi(x2) and the series of the
 // small angle delta (|delta| < 1/2 for h in (0, 1]) by angle addition.
 // KERR = false: the a = 0 (Schwarzschild) form, with the terms that vanish at a = 0 left out.
-template <bool DERIV, bool KERR = true>
-__device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double x2, Geo &G) {
-  const double a = KERR ? m.a : 0.0, M = m.mass, a2 = a * a;
-  double r = exp(x1);
-  double sp, cp;
-  sincospi(x2, &sp, &cp);
-  double dth, d2th, s, c;
-  if (m.hslope == 1.0) {
-    dth = kPI;
-    d2th = 0.0;
-    s = sp;
-    c = cp;
+// For S = df, r = e^x1 and the angular functions come from the double-float exp and sincospi, and
+// sin, cos of theta = pi (x2 + delta/pi) from a second sincospi in place of the series.
+template <bool DERIV, bool KERR = true, typename S = double>
+__device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, GeoT<S> &G) {
+  const S a = KERR ? pick<S>(m.a, m.da) : cst<S>(0.0), M = pick<S>(m.mass, m.dmass), a2 = a * a;
+  S r, dth, d2th, s, c;
+  if constexpr (std::is_same<S, df>::value) {
+    r = df_exp(x1s, m.dtab);
+    df sp, cp;
+    df_sincospi(x2s, m.dtab, sp, cp);
+    if (m.hslope == 1.0) {
+      dth = cst<S>(kPI);
+      d2th = cst<S>(0.0);
+      s = sp;
+      c = cp;
+    } else {
+      const df s2x = (sp * cp) * 2.0f, c2x = (cp - sp) * (cp + sp);   // sin, cos of 2 pi x2
+      dth = m.dpi2hh * c2x + cst<S>(kPI);
+      d2th = m.dd2th * s2x;
+      df_sincospi(x2s + m.dhh_pi * s2x, m.dtab, s, c);
+    }
   } else {
-    const double hh = 0.5 * (1.0 - m.hslope);
-    const double s2x = 2.0 * sp * cp, c2x = (cp - sp) * (cp + sp);   // sin, cos of 2 pi x2
-    dth = kPI * (1.0 + 2.0 * hh * c2x);
-    d2th = -4.0 * kPI * kPI * hh * s2x;
-    double sd, cd;
-    sincos_small(hh * s2x, sd, cd);
-    s = sp * cd + cp * sd;
-    c = cp * cd - sp * sd;
+    const double x1 = x1s, x2 = x2s;
+    r = exp(x1);
+    double sp, cp;
+    sincospi(x2, &sp, &cp);
+    if (m.hslope == 1.0) {
+      dth = kPI;
+      d2th = 0.0;
+      s = sp;
+      c = cp;
+    } else {
+      const double hh = 0.5 * (1.0 - m.hslope);
+      const double s2x = 2.0 * sp * cp, c2x = (cp - sp) * (cp + sp);   // sin, cos of 2 pi x2
+      dth = kPI * (1.0 + 2.0 * hh * c2x);
+      d2th = -4.0 * kPI * kPI * hh * s2x;
+      double sd, cd;
+      sincos_small(hh * s2x, sd, cd);
+      s = sp * cd + cp * sd;
+      c = cp * cd - sp * sd;
+    }
   }
-  double s2 = s * s, c2 = c * c;
-  double sig = KERR ? r * r + a2 * c2 : r * r;
+  S s2 = s * s, c2 = c * c;
+  S sig = KERR ? r * r + a2 * c2 : r * r;
   // one division for 1/Sigma, 1/r, 1/sin^2 and 1/(dtheta/dx2)
-  const double rs = r * s2;
-  double Q = 1.0 / (sig * rs * dth);
-  double Qd = Q * dth;
-  double isig = Qd * rs, ir = Qd * sig * s2, is2 = Qd * sig * r, idth = Q * sig * rs;
-  double f = 2.0 * M * r * isig;
-  double opf = 1.0 + f;
+  const S rs = r * s2;
+  S Q = srcp(sig * rs * dth);
+  S Qd = Q * dth;
+  S isig = Qd * rs, ir = Qd * sig * s2, is2 = Qd * sig * r, idth = Q * sig * rs;
+  S f = 2.0f * M * r * isig;
+  S opf = 1.0f + f;
   // Kerr-Schild components (t, r, theta, phi)
-  double Gtt = f - 1.0, Gtr = f, Grr = opf, Ghh = sig;
-  double Gtp = KERR ? -a * f * s2 : 0.0, Grp = KERR ? -a * s2 * opf : 0.0;
-  double Gpp = KERR ? s2 * (sig + a2 * s2 * opf) : s2 * sig;
+  S Gtt = f - 1.0f, Gtr = f, Grr = opf, Ghh = sig;
+  S Gtp = KERR ? -a * f * s2 : from_d<S>(0.0), Grp = KERR ? -a * s2 * opf : from_d<S>(0.0);
+  S Gpp = KERR ? s2 * (sig + a2 * s2 * opf) : s2 * sig;
   G.r = r;
   G.sth = s;
   G.cth = c;
@@ -226,38 +255,39 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
   // g^thth = 1/Sigma, g^phph = 1/(Sigma sin^2); divided by the Jacobian factors
   G.G00 = -opf;
   G.G01 = f * ir;
-  G.G11 = (KERR ? r * r - 2.0 * M * r + a2 : r * r - 2.0 * M * r) * isig * ir * ir;
-  G.G13 = KERR ? a * isig * ir : 0.0;
+  G.G11 = (KERR ? r * r - 2.0f * M * r + a2 : r * r - 2.0f * M * r) * isig * ir * ir;
+  G.G13 = KERR ? a * isig * ir : from_d<S>(0.0);
   G.G22 = isig * idth * idth;
   G.G33 = isig * is2;
   if (!DERIV) return;
   // derivatives of the KS components with respect to r and theta
-  double dfr = 2.0 * M * (sig - 2.0 * r * r) * isig * isig;
+  S dfr = 2.0f * M * (sig - 2.0f * r * r) * isig * isig;
   if constexpr (!KERR) {
     // a = 0: f, g_tr, g_rr depend on r only; g_thth = r^2, g_phph = r^2 sin^2
+    const S zero = from_d<S>(0.0);
     G.d100 = r * dfr;
     G.d101 = r * (r * dfr + Gtr);
-    G.d103 = 0.0;
-    G.d111 = r * r * (r * dfr + 2.0 * Grr);
-    G.d113 = 0.0;
-    G.d122 = r * (2.0 * r) * dth * dth;
-    G.d133 = r * (2.0 * r * s2);
-    G.d200 = G.d201 = G.d203 = G.d211 = G.d213 = 0.0;
-    G.d222 = Ghh * 2.0 * dth * d2th;
-    G.d233 = dth * (2.0 * s * c * sig);
+    G.d103 = zero;
+    G.d111 = r * r * (r * dfr + 2.0f * Grr);
+    G.d113 = zero;
+    G.d122 = r * (2.0f * r) * dth * dth;
+    G.d133 = r * (2.0f * r * s2);
+    G.d200 = G.d201 = G.d203 = G.d211 = G.d213 = zero;
+    G.d222 = Ghh * 2.0f * dth * d2th;
+    G.d233 = dth * (2.0f * s * c * sig);
     return;
   }
-  double dft = 4.0 * M * r * a2 * s * c * isig * isig;
-  double dGtp_r = -a * s2 * dfr, dGtp_t = -a * (dft * s2 + 2.0 * f * s * c);
-  double dGrp_r = -a * s2 * dfr, dGrp_t = -a * (2.0 * s * c * opf + s2 * dft);
-  double dGhh_r = 2.0 * r, dGhh_t = -2.0 * a2 * s * c;
-  double dGpp_r = 2.0 * r * s2 + a2 * s2 * s2 * dfr;
-  double dGpp_t = 2.0 * s * c * sig + s2 * (-2.0 * a2 * s * c) + a2 * (4.0 * s2 * s * c * opf + s2 * s2 * dft);
+  S dft = 4.0f * M * r * a2 * s * c * isig * isig;
+  S dGtp_r = -a * s2 * dfr, dGtp_t = -a * (dft * s2 + 2.0f * f * s * c);
+  S dGrp_r = -a * s2 * dfr, dGrp_t = -a * (2.0f * s * c * opf + s2 * dft);
+  S dGhh_r = 2.0f * r, dGhh_t = -2.0f * a2 * s * c;
+  S dGpp_r = 2.0f * r * s2 + a2 * s2 * s2 * dfr;
+  S dGpp_t = 2.0f * s * c * sig + s2 * (-2.0f * a2 * s * c) + a2 * (4.0f * s2 * s * c * opf + s2 * s2 * dft);
   // d/dx1 = r d/dr (Jacobian factor r also varies with x1)
   G.d100 = r * dfr;
   G.d101 = r * (r * dfr + Gtr);
   G.d103 = r * dGtp_r;
-  G.d111 = r * r * (r * dfr + 2.0 * Grr);
+  G.d111 = r * r * (r * dfr + 2.0f * Grr);
   G.d113 = r * (r * dGrp_r + Grp);
   G.d122 = r * dGhh_r * dth * dth;
   G.d133 = r * dGpp_r;
@@ -267,7 +297,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, double x1, double
   G.d203 = dth * dGtp_t;
   G.d211 = dth * dft * r * r;
   G.d213 = dth * dGrp_t * r;
-  G.d222 = dth * dGhh_t * dth * dth + Ghh * 2.0 * dth * d2th;
+  G.d222 = dth * dGhh_t * dth * dth + Ghh * 2.0f * dth * d2th;
   G.d233 = dth * dGpp_t;
 }
 
@@ -285,42 +315,42 @@ __device__ __forceinline__ double dot(const Geo &G, const double a[4], const dou
 }
 
 // dk^mu/dlambda = -Gamma^mu_ab k^a k^b = -g^{mu nu} (k^1 (d1 g k)_nu + k^2 (d2 g k)_nu - 1/2 d_nu g_ab k^a k^b)
-template <bool KERR = true>
-__device__ __forceinline__ void accel(const Geo &G, const double k[4], double A[4]) {
+template <bool KERR = true, typename S = double>
+__device__ __forceinline__ void accel(const GeoT<S> &G, const S k[4], S A[4]) {
   if constexpr (!KERR) {
     // a = 0: d103 = d113 = d2(0,1,3) = G13 = 0
-    double p0 = G.d100 * k[0] + G.d101 * k[1];
-    double p1 = G.d101 * k[0] + G.d111 * k[1];
-    double p2 = G.d122 * k[2];
-    double p3 = G.d133 * k[3];
-    double q2 = G.d222 * k[2];
-    double q3 = G.d233 * k[3];
-    double kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
-    double kDk2 = k[2] * q2 + k[3] * q3;
-    double w0 = k[1] * p0;
-    double w1 = k[1] * p1 - 0.5 * kDk1;
-    double w2 = k[1] * p2 + k[2] * q2 - 0.5 * kDk2;
-    double w3 = k[1] * p3 + k[2] * q3;
+    S p0 = G.d100 * k[0] + G.d101 * k[1];
+    S p1 = G.d101 * k[0] + G.d111 * k[1];
+    S p2 = G.d122 * k[2];
+    S p3 = G.d133 * k[3];
+    S q2 = G.d222 * k[2];
+    S q3 = G.d233 * k[3];
+    S kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
+    S kDk2 = k[2] * q2 + k[3] * q3;
+    S w0 = k[1] * p0;
+    S w1 = k[1] * p1 - 0.5f * kDk1;
+    S w2 = k[1] * p2 + k[2] * q2 - 0.5f * kDk2;
+    S w3 = k[1] * p3 + k[2] * q3;
     A[0] = -(G.G00 * w0 + G.G01 * w1);
     A[1] = -(G.G01 * w0 + G.G11 * w1);
     A[2] = -(G.G22 * w2);
     A[3] = -(G.G33 * w3);
     return;
   }
-  double p0 = G.d100 * k[0] + G.d101 * k[1] + G.d103 * k[3];
-  double p1 = G.d101 * k[0] + G.d111 * k[1] + G.d113 * k[3];
-  double p2 = G.d122 * k[2];
-  double p3 = G.d103 * k[0] + G.d113 * k[1] + G.d133 * k[3];
-  double q0 = G.d200 * k[0] + G.d201 * k[1] + G.d203 * k[3];
-  double q1 = G.d201 * k[0] + G.d211 * k[1] + G.d213 * k[3];
-  double q2 = G.d222 * k[2];
-  double q3 = G.d203 * k[0] + G.d213 * k[1] + G.d233 * k[3];
-  double kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
-  double kDk2 = k[0] * q0 + k[1] * q1 + k[2] * q2 + k[3] * q3;
-  double w0 = k[1] * p0 + k[2] * q0;
-  double w1 = k[1] * p1 + k[2] * q1 - 0.5 * kDk1;
-  double w2 = k[1] * p2 + k[2] * q2 - 0.5 * kDk2;
-  double w3 = k[1] * p3 + k[2] * q3;
+  S p0 = G.d100 * k[0] + G.d101 * k[1] + G.d103 * k[3];
+  S p1 = G.d101 * k[0] + G.d111 * k[1] + G.d113 * k[3];
+  S p2 = G.d122 * k[2];
+  S p3 = G.d103 * k[0] + G.d113 * k[1] + G.d133 * k[3];
+  S q0 = G.d200 * k[0] + G.d201 * k[1] + G.d203 * k[3];
+  S q1 = G.d201 * k[0] + G.d211 * k[1] + G.d213 * k[3];
+  S q2 = G.d222 * k[2];
+  S q3 = G.d203 * k[0] + G.d213 * k[1] + G.d233 * k[3];
+  S kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
+  S kDk2 = k[0] * q0 + k[1] * q1 + k[2] * q2 + k[3] * q3;
+  S w0 = k[1] * p0 + k[2] * q0;
+  S w1 = k[1] * p1 + k[2] * q1 - 0.5f * kDk1;
+  S w2 = k[1] * p2 + k[2] * q2 - 0.5f * kDk2;
+  S w3 = k[1] * p3 + k[2] * q3;
   A[0] = -(G.G00 * w0 + G.G01 * w1);
   A[1] = -(G.G01 * w0 + G.G11 * w1 + G.G13 * w3);
   A[2] = -(G.G22 * w2);
@@ -329,13 +359,23 @@ __device__ __forceinline__ void accel(const Geo &G, const double k[4], double A[
 
 // Step size (reading; the paper gives none): each internal coordinate moves at most eps_geo of
 // its scale (1 for ln r and phi, the distance to the nearer pole for x2).
-__device__ __forceinline__ double stepsize(const DevModel &m, const double X[4], const double K[4]) {
+template <typename S = double>
+__device__ __forceinline__ S stepsize(const DevModel &m, const S X[4], const S K[4]) {
   // 1 / (1/d1 + 1/d2 + 1/d3) with d1 = eps/(|k1|+S), d2 = eps x2n/(|k2|+S), d3 = eps/(|k3|+S)
   // = eps x2n / ((|k1| + |k3|) x2n + |k2|): one division
   const double SMALL = 1e-40;
   double x2n = fmin(fabs(X[2]), fabs(1.0 - X[2]));
   double den = ((fabs(K[1]) + SMALL) + (fabs(K[3]) + SMALL)) * x2n + (fabs(K[2]) + SMALL);
   return m.eps_geo * x2n / den;
+}
+
+// Double-float step size: the same rule, evaluated in FP32 (a step length needs no more).
+template <>
+__device__ __forceinline__ df stepsize<df>(const DevModel &m, const df X[4], const df K[4]) {
+  const float x2 = to_f(X[2]);
+  const float x2n = fminf(fabsf(x2), fabsf(1.0f - x2));
+  const float den = (fabsf(K[1].hi) + fabsf(K[3].hi)) * x2n + fabsf(K[2].hi) + 1e-30f;
+  return df{(float)m.eps_geo * x2n / den, 0.0f};
 }
 
 // ---------------------------------------------------------------- tables
@@ -531,6 +571,12 @@ __device__ __forceinline__ double Gsyn(double X) {
 }
 
 // ---------------------------------------------------------------- fluid (sections 2.5-2.7)
+// metric component of scalar GS as the plasma arithmetic's type T
+template <typename T> __device__ __forceinline__ T cvt(double x) { return (T)x; }
+template <typename T> __device__ __forceinline__ T cvt(df x);
+template <> __device__ __forceinline__ float cvt<float>(df x) { return to_f(x); }
+template <> __device__ __forceinline__ double cvt<double>(df x) { return to_d(x); }
+
 template <typename T>
 struct Plasma {
   T ne, thetae, B;
@@ -543,33 +589,50 @@ struct Plasma {
 
 // Primitives interpolated linearly in internal coordinates between zone centres (reading):
 // clamped to the edge zones in x1 and x2, periodic in x3, no plasma outside the radial range.
-template <typename T>
-__device__ __forceinline__ bool interp_prims(const DevModel &m, const double X[4], T pr[8]) {
-  if (X[1] < m.x1_0 || X[1] > m.x1_hi) return false;
+// Zone-centred fractional indices of a point: FP64 for a double position, FP32 for a double-float one
+// (the offset from the grid origin in double-float, then FP32).
+__device__ __forceinline__ double zone_coord(const DevModel &m, const double X[4], int d) {
+  return d == 1 ? (X[1] - m.x1_0) * m.idx1 - 0.5 : d == 2 ? (X[2] - m.x2_0) * m.idx2 - 0.5 : (X[3] - m.x3_0) * m.idx3 - 0.5;
+}
+__device__ __forceinline__ float zone_coord(const DevModel &m, const df X[4], int d) {
+  return d == 1 ? to_f(X[1] - m.dx1_0) * m.fidx1 - 0.5f
+                : d == 2 ? (to_f(X[2]) - m.fx2_0) * m.fidx2 - 0.5f : (to_f(X[3]) - m.fx3_0) * m.fidx3 - 0.5f;
+}
+__device__ __forceinline__ bool outside_radially(const DevModel &m, const double X[4]) {
+  return X[1] < m.x1_0 || X[1] > m.x1_hi;
+}
+__device__ __forceinline__ bool outside_radially(const DevModel &m, const df X[4]) {
+  return !(df_ge(X[1], m.dx1_0) && df_le(X[1], m.dx1_hi));
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T pr[8]) {
+  if (outside_radially(m, X)) return false;
+  using R = decltype(vmag(X[0]));   // index arithmetic: double, or float for double-float positions
   int i, j;
-  double di, dj;
+  R di, dj;
   {
-    double f = (X[1] - m.x1_0) * m.idx1 - 0.5;
-    i = (int)floor(f);
-    di = f - i;
-    if (m.n1 == 1) { i = 0; di = 0.0; }
-    else if (i < 0) { i = 0; di = 0.0; }
-    else if (i > m.n1 - 2) { i = m.n1 - 2; di = 1.0; }
+    const R f1 = zone_coord(m, X, 1);
+    i = (int)floor(f1);
+    di = f1 - i;
+    if (m.n1 == 1) { i = 0; di = 0; }
+    else if (i < 0) { i = 0; di = 0; }
+    else if (i > m.n1 - 2) { i = m.n1 - 2; di = 1; }
   }
   {
-    double f = (X[2] - m.x2_0) * m.idx2 - 0.5;
-    j = (int)floor(f);
-    dj = f - j;
-    if (m.n2 == 1) { j = 0; dj = 0.0; }
-    else if (j < 0) { j = 0; dj = 0.0; }
-    else if (j > m.n2 - 2) { j = m.n2 - 2; dj = 1.0; }
+    const R f2 = zone_coord(m, X, 2);
+    j = (int)floor(f2);
+    dj = f2 - j;
+    if (m.n2 == 1) { j = 0; dj = 0; }
+    else if (j < 0) { j = 0; dj = 0; }
+    else if (j > m.n2 - 2) { j = m.n2 - 2; dj = 1; }
   }
   int k0 = 0, k1 = 0;
-  double dk = 0.0;
+  R dk = 0;
   if (m.n3 > 1) {
-    double f = (X[3] - m.x3_0) * m.idx3 - 0.5;
-    double fl = floor(f);
-    dk = f - fl;
+    const R f3 = zone_coord(m, X, 3);
+    R fl = floor(f3);
+    dk = f3 - fl;
     long long kk = (long long)fl;
     k0 = (int)(((kk % m.n3) + m.n3) % m.n3);
     k1 = (k0 + 1) % m.n3;
@@ -636,19 +699,20 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const double X[4
 
 // Fluid-frame quantities from primitives with metric G: 4-velocity from the normal-observer
 // velocity, magnetic 4-vector b, n_e, |B| [G] and Theta_e from the R_high/R_low model.
-template <typename T>
-__device__ __forceinline__ void plasma_from_prims(const DevModel &m, const Geo &G, const T pr[8], Plasma<T> &P,
+template <typename T, typename GS = double>
+__device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<GS> &G, const T pr[8], Plasma<T> &P,
                                                   T ucon_out[4], T bcon_out[4]) {
-  T g00 = (T)G.g00, g01 = (T)G.g01, g03 = (T)G.g03, g11 = (T)G.g11, g13 = (T)G.g13, g22 = (T)G.g22, g33 = (T)G.g33;
+  T g00 = cvt<T>(G.g00), g01 = cvt<T>(G.g01), g03 = cvt<T>(G.g03), g11 = cvt<T>(G.g11), g13 = cvt<T>(G.g13),
+    g22 = cvt<T>(G.g22), g33 = cvt<T>(G.g33);
   T rho = pr[0], uu = pr[1];
   T U1 = pr[5], U2 = pr[6], U3 = pr[7];
   constexpr bool kF64 = sizeof(T) == 8;
-  T alpha = rsqrt(-(T)G.G00);
+  T alpha = rsqrt(-cvt<T>(G.G00));
   T q = g11 * U1 * U1 + g22 * U2 * U2 + g33 * U3 * U3 + (T)2 * g13 * U1 * U3;
   T rg = rsqrt((T)1 + q);                   // 1 / gamma
   T gamma = kF64 ? ((T)1 + q) * rg : sqrt((T)1 + q);
-  T u0 = gamma * (-(T)G.G00) * alpha;   // gamma / alpha, alpha = (-g^tt)^(-1/2)
-  T u1 = U1 - gamma * alpha * (T)G.G01;
+  T u0 = gamma * (-cvt<T>(G.G00)) * alpha;   // gamma / alpha, alpha = (-g^tt)^(-1/2)
+  T u1 = U1 - gamma * alpha * cvt<T>(G.G01);
   T u2 = U2, u3 = U3;
   T uc0 = g00 * u0 + g01 * u1 + g03 * u3;
   T uc1 = g01 * u0 + g11 * u1 + g13 * u3;
@@ -766,7 +830,8 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
 }
 
 // Mixed precision: the same quantities with FP32 plasma state and coefficient arithmetic.
-__device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, const double X[4], const double K[4],
+template <typename S>
+__device__ __forceinline__ void coefficients32(const DevModel &m, const GeoT<S> &G, const S X[4], const S K[4],
                                                bool want_s, Coef &c) {
   c.ana = c.ans = c.thetae = 0.0;
   float pr[8];
@@ -775,7 +840,7 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, 
   plasma_from_prims<float>(m, G, pr, P, nullptr, nullptr);
   c.thetae = P.thetae;
   if (!P.on) return;
-  float kf[4] = {(float)K[0], (float)K[1], (float)K[2], (float)K[3]};
+  float kf[4] = {to_f(K[0]), to_f(K[1]), to_f(K[2]), to_f(K[3])};
   float eps = -(kf[0] * P.ucov[0] + kf[1] * P.ucov[1] + kf[2] * P.ucov[2] + kf[3] * P.ucov[3]);
   if (!(eps > 0.0f)) return;
   // frequencies and emissivities span ~1e-40..1e40: keep the products in ranges float holds
@@ -806,7 +871,7 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const Geo &G, 
     // kappa population: its absorption integral (FP64 tables) in place of the thermal fit
     c.ana = 0.0;
     if (P.thetae >= (float)m.thetae_min && P.B > 0.0f && P.bsq > 0.0f) {
-      double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
+      double kb = to_d(K[0]) * P.bcov[0] + to_d(K[1]) * P.bcov[1] + to_d(K[2]) * P.bcov[2] + to_d(K[3]) * P.bcov[3];
       double cth = fmin(1.0, fmax(-1.0, kb / ((double)eps * sqrt((double)P.bsq))));
       double s2 = 1.0 - cth * cth;
       if (s2 > 0.0) c.ana = kappa_nu_alpha(m, (double)P.ne, (double)P.thetae, (double)P.B, sqrt(s2), (double)nu9 * 1e9);
@@ -833,7 +898,8 @@ struct CoefA {
   float in[3];
 };
 
-__device__ __forceinline__ void coefficients32_a(const DevModel &m, const Geo &G, const double X[4], const double K[4],
+template <typename S>
+__device__ __forceinline__ void coefficients32_a(const DevModel &m, const GeoT<S> &G, const S X[4], const S K[4],
                                                  CoefA &a) {
   a.on = a.emit = false;
   a.thetae = a.ne = a.eps = a.nu9 = a.ana_k2 = 0.0f;
@@ -844,7 +910,7 @@ __device__ __forceinline__ void coefficients32_a(const DevModel &m, const Geo &G
   plasma_from_prims<float>(m, G, pr, P, nullptr, nullptr);
   a.thetae = P.thetae;
   if (!P.on) return;
-  float kf[4] = {(float)K[0], (float)K[1], (float)K[2], (float)K[3]};
+  float kf[4] = {to_f(K[0]), to_f(K[1]), to_f(K[2]), to_f(K[3])};
   float eps = -(kf[0] * P.ucov[0] + kf[1] * P.ucov[1] + kf[2] * P.ucov[2] + kf[3] * P.ucov[3]);
   if (!(eps > 0.0f)) return;
   a.on = true;

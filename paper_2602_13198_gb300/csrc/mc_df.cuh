@@ -1,0 +1,179 @@
+// mc_df.cuh -- double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32 numbers
+// (|lo| <= ulp(hi)/2), which carries a 48-bit significand on the FP32 pipes.  GB300 issues FP32 at
+// ~74x its FP64 rate, so the mixed-precision transport keeps the geodesic at near-FP64 accuracy
+// (~1e-14 relative) in this form instead of in FP64.
+//
+// Error-free transformations: two-sum (Knuth, TAOCP vol. 2, 4.2.2), the fast two-sum for |a| >= |b|
+// (Dekker 1971), and the FMA form of the exact product (a b = p + e with e = fma(a, b, -p)).  The
+// addition is the accurate variant (both components summed with two-sum, two renormalisations),
+// which keeps a relative error of a few 2^-48 also under cancellation; the product adds the cross
+// terms to the exact product of the high parts.  The exponent range is FP32's.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mcgb {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df operator+(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  const df t = df_two_sum(a.lo, b.lo);
+  s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+// by an FP32 number (exact constants such as 2 or 0.5 and FP32 data)
+__device__ __forceinline__ df operator*(df a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df operator*(float b, df a) { return a * b; }
+
+__device__ __forceinline__ df operator+(df a, float b) {
+  df s = df_two_sum(a.hi, b);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ df operator+(float b, df a) { return a + b; }
+__device__ __forceinline__ df operator-(df a, float b) { return a + (-b); }
+__device__ __forceinline__ df operator-(float b, df a) { return (-a) + b; }
+
+__device__ __forceinline__ df &operator+=(df &a, df b) { return a = a + b; }
+
+// 1 / a: FP32 reciprocal refined by one Newton step in double-float (error ~2^-47)
+__device__ __forceinline__ df df_rcp(df a) {
+  const float q0 = __frcp_rn(a.hi);
+  const df r = 1.0f - a * q0;   // residual 1 - a q0, of order 2^-24
+  return df_fast_two_sum(q0, __fmul_rn(q0, r.hi));
+}
+
+__device__ __forceinline__ df df_abs(df a) { return a.hi < 0.0f ? -a : a; }
+
+// conversions: split a double into its nearest FP32 and the FP32 remainder; join exactly
+__device__ __forceinline__ df df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+// Compile-time split of a double constant (for constants that are not FP32 numbers, like pi)
+__host__ __device__ constexpr df df_const(double x) {
+  return {(float)x, (float)(x - (double)(float)x)};
+}
+
+// ---- scalar-generic helpers: the geodesic code is written once for S = double (plain FP64) and
+// S = df (mixed precision); for double every helper is the identity or the plain operation.
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(df x) { return df_to(x); }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(df x) { return __fadd_rn(x.hi, x.lo); }
+__device__ __forceinline__ double sabs(double x) { return fabs(x); }
+__device__ __forceinline__ df sabs(df x) { return df_abs(x); }
+__device__ __forceinline__ double srcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ df srcp(df x) { return df_rcp(x); }
+// ordering of normalised double-float values
+__device__ __forceinline__ bool df_ge(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+__device__ __forceinline__ bool df_le(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
+// a model constant held in both forms: the double for S = double, its df split for S = df
+template <typename S> __device__ __forceinline__ S pick(double d, df f);
+template <> __device__ __forceinline__ double pick<double>(double d, df) { return d; }
+template <> __device__ __forceinline__ df pick<df>(double, df f) { return f; }
+// a compile-time constant
+template <typename S> __host__ __device__ constexpr S cst(double x);
+template <> __host__ __device__ constexpr double cst<double>(double x) { return x; }
+template <> __host__ __device__ constexpr df cst<df>(double x) { return df_const(x); }
+
+template <typename S> __device__ __forceinline__ S from_d(double x);
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ df from_d<df>(double x) { return df_from(x); }
+// Terms of the Verlet convergence test sum |k_new - k_old| < tol sum |k_new|: FP64 for double, FP32 for
+// df (the difference of two close df values is exact enough in FP32 once the high parts cancel).
+__device__ __forceinline__ double vdiff(double a, double b) { return fabs(a - b); }
+__device__ __forceinline__ float vdiff(df a, df b) {
+  return fabsf(__fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ double vmag(double a) { return fabs(a); }
+__device__ __forceinline__ float vmag(df a) { return fabsf(a.hi); }
+__device__ __forceinline__ bool below_tol(double a, double tol, double b) { return a < tol * b; }
+__device__ __forceinline__ bool below_tol(float a, double tol, float b) { return a < (float)tol * b; }
+
+// ---- elementary functions in double-float (own range reductions and Taylor polynomials; the
+// high-order terms, below 2^-24 of the leading one, in FP32).  Both use a table of double-float
+// constants built on the host in FP64: entries [0, 32) hold 2^(j/32), entries [32, 96) sin(pi j/32).
+constexpr int kDfTabExp = 0, kDfTabSin = 32, kDfTabN = 96;
+
+__device__ __forceinline__ df df_tab(const df *T, int i) {
+  const float2 v = __ldg(reinterpret_cast<const float2 *>(T) + i);
+  return {v.x, v.y};
+}
+
+// e^x for |x| < 80: x = (32 e + j) ln2/32 + t with |t| <= ln2/64; e^x = 2^e 2^(j/32) e^t, and e^t by its
+// Taylor series to t^6 (truncation below 2^-56 for |t| <= ln2/64).
+__device__ __forceinline__ df df_exp(df x, const df *T) {
+  constexpr df kLn2_32 = df_const(0.6931471805599453094172321 / 32.0);
+  const float kf = rintf(x.hi * 46.16624130844683f);   // 32 / ln 2
+  const df t = x - kLn2_32 * kf;
+  const int k = (int)kf, j = k & 31, e = (k - j) / 32;
+  const float q = t.hi;
+  const float tail = q * q * q * q * (1.0f / 24.0f + q * (1.0f / 120.0f + q * (1.0f / 720.0f)));
+  const df t2 = t * t;
+  constexpr df kSixth = df_const(1.0 / 6.0);
+  df em1 = (t2 * t) * kSixth + tail;
+  em1 = em1 + t2 * 0.5f;
+  em1 = em1 + t;
+  const df r = df_tab(T, kDfTabExp + j) * (em1 + 1.0f);
+  return {ldexpf(r.hi, e), ldexpf(r.lo, e)};
+}
+
+// sin(pi x) and cos(pi x): x = j/32 + z with |z| <= 1/64, w = pi z, angle addition with the tabulated
+// sin and cos of pi j/32 (cos(pi j/32) = sin(pi (j + 16)/32)); sin w and cos w by their Taylor series
+// to w^7 and w^8 (truncation below 2^-57 for |w| <= pi/64).
+__device__ __forceinline__ void df_sincospi(df x, const df *T, df &s, df &c) {
+  constexpr df kPi = df_const(3.14159265358979323846264338);
+  const float jf = rintf(x.hi * 32.0f);
+  const df z = x - jf * 0.03125f;   // exact: j/32 is an FP32 number
+  const int j = (int)jf;
+  const df w = z * kPi;
+  const float q = w.hi, q2 = q * q;
+  const df w2 = w * w;
+  constexpr df kM6 = df_const(-1.0 / 6.0), k24 = df_const(1.0 / 24.0);
+  // sin w = w - w^3/6 + w^5/120 - w^7/5040
+  df sw = (w2 * w) * kM6 + q2 * q2 * q * (1.0f / 120.0f - q2 * (1.0f / 5040.0f));
+  sw = sw + w;
+  // cos w = 1 - w^2/2 + w^4/24 - w^6/720 + w^8/40320
+  df cw = (w2 * w2) * k24 + q2 * q2 * q2 * (-1.0f / 720.0f + q2 * (1.0f / 40320.0f));
+  cw = cw + w2 * -0.5f;
+  cw = cw + 1.0f;
+  const df sa = df_tab(T, kDfTabSin + (j & 63)), ca = df_tab(T, kDfTabSin + ((j + 16) & 63));
+  s = sa * cw + ca * sw;
+  c = ca * cw - sa * sw;
+}
+
+}  // namespace mcgb

@@ -252,11 +252,12 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16(v - __bfloat162float(hi));
 }
 
-// Writes 64 activations of this thread's row as hi/lo BF16 rows of its group's A2 / A2lo (two
-// values per conversion: element 2q in the low half of each packed pair, as in memory order).
-__device__ __forceinline__ void put_hidden(TcMlp &T, int grp, int row, const float *h) {
+// Writes 16 activations (columns c0 .. c0+15) of this thread's row as hi/lo BF16 rows of its group's
+// A2 / A2lo (two values per conversion: element 2q in the low half of each packed pair, as in
+// memory order).
+__device__ __forceinline__ void put_hidden16(TcMlp &T, int grp, int row, int c0, const float *h) {
 #pragma unroll
-  for (int c = 0; c < 64; c += 8) {
+  for (int c = 0; c < 16; c += 8) {
     __nv_bfloat162 hi[4], lo[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -265,8 +266,21 @@ __device__ __forceinline__ void put_hidden(TcMlp &T, int grp, int row, const flo
       const float2 back = __bfloat1622float2(hi[q]);
       lo[q] = __floats2bfloat162_rn(a - back.x, b - back.y);
     }
-    *(uint4 *)(T.a2[grp] + kmajor_off(row, c, 64)) = *(uint4 *)hi;
-    *(uint4 *)(T.a2l[grp] + kmajor_off(row, c, 64)) = *(uint4 *)lo;
+    *(uint4 *)(T.a2[grp] + kmajor_off(row, c0 + c, 64)) = *(uint4 *)hi;
+    *(uint4 *)(T.a2l[grp] + kmajor_off(row, c0 + c, 64)) = *(uint4 *)lo;
+  }
+}
+
+// Hidden layer epilogue in 16-column chunks (16 live activations instead of 64): TMEM accumulators
+// + bias, SiLU, BF16 hi/lo split into the next layer's A tiles.
+__device__ __forceinline__ void hidden_epilogue(TcMlp &T, int grp, int row, uint32_t tbase, const float *bias) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < 64; c0 += 16) {
+    float h[16];
+    tmem_ld16(tbase + c0, h);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) h[c] = silu_f(h[c] + bias[c0 + c]);
+    put_hidden16(T, grp, row, c0, h);
   }
 }
 
@@ -295,20 +309,11 @@ __device__ __forceinline__ bool tc_mlp_eval(TcMlp &T, const float in[3], float o
   const unsigned char *a_l1[1] = {T.a1[grp]};
   const unsigned char *b_l1[1] = {T.b1};
   bool ok = tc_layer(T, grp, a_l1, b_l1, 1, 16, 64);
-  float h[64];
-#pragma unroll
-  for (int c = 0; c < 64; c += 16) tmem_ld16(tbase + c, h + c);
-#pragma unroll
-  for (int c = 0; c < 64; ++c) h[c] = silu_f(h[c] + T.bias[c]);
-  put_hidden(T, grp, row, h);
+  hidden_epilogue(T, grp, row, tbase, T.bias);
   const unsigned char *a_l2[3] = {T.a2[grp], T.a2l[grp], T.a2[grp]};
   const unsigned char *b_l2[3] = {T.b2, T.b2, T.b2l};
   ok = tc_layer(T, grp, a_l2, b_l2, 3, 64, 64) && ok;
-#pragma unroll
-  for (int c = 0; c < 64; c += 16) tmem_ld16(tbase + c, h + c);
-#pragma unroll
-  for (int c = 0; c < 64; ++c) h[c] = silu_f(h[c] + T.bias[64 + c]);
-  put_hidden(T, grp, row, h);   // the layer-2 MMAs have completed, so A2 may be overwritten
+  hidden_epilogue(T, grp, row, tbase, T.bias + 64);   // the layer-2 MMAs have completed: A2 may be overwritten
   const unsigned char *b_l3[3] = {T.b3, T.b3, T.b3l};
   ok = tc_layer(T, grp, a_l2, b_l3, 3, 64, 16) && ok;
   float y[16];

@@ -3,13 +3,18 @@
 // initialisation, the in-grid step (sections 2.4-2.7), the free-streaming step, recording and the
 // Compton child (section 2.7), and the surrogate-split in-grid step.
 #pragma once
+#include <type_traits>
+
 #include "mc_internal.h"
 
 namespace mcgb {
 
 
-struct Ph {
-  double X[4], K[4], A[4];
+// Superphoton state; S is the geodesic scalar (double, or df in the mixed-precision transport
+// kernels, which convert at load and save: the pool holds FP64).
+template <typename S>
+struct PhT {
+  S X[4], K[4], A[4];
   double w, wb, ana, ans, acc, x1t;
   Rng s;
   int nsc;
@@ -17,15 +22,19 @@ struct Ph {
   int nsteps;
   int model;   // index of the superphoton's model in a batched run (0 otherwise)
 };
+using Ph = PhT<double>;
+// geodesic scalar of the transport kernels of each precision
+template <bool MIXED>
+using GeoScalar = typename std::conditional<MIXED, df, double>::type;
 
 struct LocalStats {
   unsigned long long emit, child, rec, abs, capt, maxst, steps, iters, nonconv, roul, rejcap, events, gsteps, giters;
 };
 
-template <bool MIXED>
-__device__ __forceinline__ void coefs(const DevModel &m, const Geo &G, const double X[4], const double K[4], bool ws,
+template <bool MIXED, typename S>
+__device__ __forceinline__ void coefs(const DevModel &m, const GeoT<S> &G, const S X[4], const S K[4], bool ws,
                                       Coef &c) {
-  if (MIXED) coefficients32(m, G, X, K, ws, c);
+  if constexpr (MIXED) coefficients32(m, G, X, K, ws, c);
   else coefficients64(m, G, X, K, ws, c);
 }
 
@@ -227,18 +236,26 @@ static __device__ void load_child(const DevModel &m, const ChildBuf &q, int64_t 
   p.nsc = q.nsc[idx];
 }
 
-__device__ __forceinline__ bool in_grid(const DevModel &m, const double X[4]) {
-  return X[1] >= m.x1_0 && X[1] <= m.x1_hi;
+template <typename S>
+__device__ __forceinline__ bool in_grid(const DevModel &m, const S X[4]) {
+  if constexpr (std::is_same<S, df>::value) return df_ge(X[1], m.dx1_0) && df_le(X[1], m.dx1_hi);
+  else return X[1] >= m.x1_0 && X[1] <= m.x1_hi;
 }
+// termination radii (recording sphere, capture near the horizon) in the geodesic's scalar
+__device__ __forceinline__ bool at_record(const DevModel &m, double r) { return r >= m.r_record; }
+__device__ __forceinline__ bool at_record(const DevModel &m, df r) { return df_ge(r, m.dr_record); }
+__device__ __forceinline__ bool at_capture(const DevModel &m, double r) { return r <= m.r_capture; }
+__device__ __forceinline__ bool at_capture(const DevModel &m, df r) { return df_le(r, m.dr_capture); }
 
-static __device__ void record(const DevModel &m, const PushIO &io, const Geo &G, const Ph &p) {
-  double E = -(G.g00 * p.K[0] + G.g01 * p.K[1] + G.g03 * p.K[3]);
+template <typename GS, typename S>
+static __device__ void record(const DevModel &m, const PushIO &io, const GeoT<GS> &G, const PhT<S> &p) {
+  double E = -(to_d(G.g00) * to_d(p.K[0]) + to_d(G.g01) * to_d(p.K[1]) + to_d(G.g03) * to_d(p.K[3]));
   if (!(E > 0.0)) return;
   double nu = E * (kME * kCL * kCL / kHPL);
   double l = log10(nu);
   int ib = (int)floor((l - m.lnu_lo) / m.dlog_bin);
   if (ib < 0 || ib >= m.n_bins) return;
-  double thf = acos(fabs(G.cth));
+  double thf = acos(fabs(to_d(G.cth)));
   int ii = (int)floor(thf / (0.5 * kPI) * m.n_incl);
   ii = min(max(ii, 0), m.n_incl - 1);
   double we = p.w * E;
@@ -248,7 +265,8 @@ static __device__ void record(const DevModel &m, const PushIO &io, const Geo &G,
   atomicAdd(sp + 2, 1.0);
 }
 
-static __device__ void write_log(const PushIO &io, const Ph &p, int status) {
+template <typename S>
+static __device__ void write_log(const PushIO &io, const PhT<S> &p, int status) {
   if (!io.log) return;
   unsigned long long slot = atomicAdd(io.cnt + CNT_LOG, 1ull);
   if ((int64_t)slot >= io.log_cap) {
@@ -260,8 +278,8 @@ static __device__ void write_log(const PushIO &io, const Ph &p, int status) {
   L.gen = p.nsc;
   L.status = status;
   for (int q = 0; q < 4; ++q) {
-    L.X[q] = p.X[q];
-    L.K[q] = p.K[q];
+    L.X[q] = to_d(p.X[q]);
+    L.K[q] = to_d(p.K[q]);
   }
   L.w = p.w;
   L.nsteps = p.nsteps;
@@ -270,36 +288,36 @@ static __device__ void write_log(const PushIO &io, const Ph &p, int status) {
 }
 
 // One geodesic step with absorption, scattering and the termination tests; false when finished.
-template <bool MIXED, bool KERR = true>
-static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
+template <bool MIXED, bool KERR = true, typename S = double>
+static __device__ bool step(const DevModel &m, const PushIO &io, PhT<S> &p, LocalStats &ls) {
   const bool scat = m.scatter && p.nsc < m.n_sc_max;
-  double dl = stepsize(m, p.X, p.K);
-  double X0[4], K0[4], Kp[4], An[4];
+  S dl = stepsize(m, p.X, p.K);
+  S X0[4], K0[4], Kp[4], An[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     X0[q] = p.X[q];
     K0[q] = p.K[q];
-    p.X[q] = X0[q] + K0[q] * dl + 0.5 * p.A[q] * dl * dl;
+    p.X[q] = X0[q] + K0[q] * dl + 0.5f * p.A[q] * dl * dl;
     Kp[q] = K0[q] + p.A[q] * dl;
   }
-  Geo G;
+  GeoT<S> G;
   metric_eval<true, KERR>(m, p.X[1], p.X[2], G);
   int it = 0;
   bool conv = false;
-  double Kn[4];
+  S Kn[4];
   while (true) {
     accel<KERR>(G, Kp, An);
-    double num = 0.0, den = 0.0;
+    decltype(vmag(dl)) num = 0, den = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      Kn[q] = K0[q] + 0.5 * (p.A[q] + An[q]) * dl;
-      num += fabs(Kn[q] - Kp[q]);
-      den += fabs(Kn[q]);
+      Kn[q] = K0[q] + 0.5f * (p.A[q] + An[q]) * dl;
+      num += vdiff(Kn[q], Kp[q]);
+      den += vmag(Kn[q]);
     }
     ++it;
 #pragma unroll
     for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
-    if (num < m.verlet_tol * den) {
+    if (below_tol(num, m.verlet_tol, den)) {
       conv = true;
       break;
     }
@@ -318,12 +336,13 @@ static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalSta
   ls.steps++;
   Coef c;
   coefs<MIXED>(m, G, p.X, p.K, scat, c);
-  const double C = m.Ccoef;
-  double tau_a = 0.5 * (p.ana + c.ana) * C * dl;
+  const double C = m.Ccoef, dld = to_d(dl);
+  double tau_a = 0.5 * (p.ana + c.ana) * C * dld;
   double w0 = p.w;
-  double wn = w0 * exp(-tau_a);
+  // attenuation factor: FP32 in the mixed-precision form (its coefficients are FP32 already)
+  double wn = w0 * (MIXED ? (double)expf((float)-tau_a) : exp(-tau_a));
   if (scat) {
-    double tau_s = 0.5 * (p.ans + c.ans) * C * dl;
+    double tau_s = 0.5 * (p.ans + c.ans) * C * dld;
     if (tau_s > 0.0) {
       double b = bias_of(m, c.thetae, p.nsc);
       double d = b * tau_s;
@@ -332,8 +351,8 @@ static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalSta
         double Xe[4], Ke[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          Xe[q] = X0[q] + f * (p.X[q] - X0[q]);
-          Ke[q] = K0[q] + f * (p.K[q] - K0[q]);
+          Xe[q] = to_d(X0[q]) + f * (to_d(p.X[q]) - to_d(X0[q]));
+          Ke[q] = to_d(K0[q]) + f * (to_d(p.K[q]) - to_d(K0[q]));
         }
         double we = w0 * exp(-f * tau_a);
         uint64_t cid = child_id(p.s.id, p.nev);
@@ -351,13 +370,12 @@ static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalSta
   p.w = wn;
   p.ana = c.ana;
   p.ans = c.ans;
-  const double r = G.r;
   int status = 0;
-  if (r >= m.r_record) {
+  if (at_record(m, G.r)) {
     record(m, io, G, p);
     status = 1;
     ls.rec++;
-  } else if (r <= m.r_capture) {
+  } else if (at_capture(m, G.r)) {
     status = 3;
     ls.capt++;
   } else if (!(p.w > 0.0)) {
@@ -389,33 +407,33 @@ static __device__ bool step(const DevModel &m, const PushIO &io, Ph &p, LocalSta
 // weight is unchanged): the same Verlet arithmetic and termination tests as step().  If the new
 // point lies inside the grid the step is discarded (state untouched) and 2 is returned, so the
 // in-grid phase redoes it with the coefficients.  Returns 0 to continue, 1 when finished.
-template <bool KERR = true>
-static __device__ int step_free(const DevModel &m, const PushIO &io, Ph &p, LocalStats &ls) {
-  double dl = stepsize(m, p.X, p.K);
-  double Xn[4], Kp[4], An[4], Kn[4];
+template <bool KERR = true, typename S = double>
+static __device__ int step_free(const DevModel &m, const PushIO &io, PhT<S> &p, LocalStats &ls) {
+  S dl = stepsize(m, p.X, p.K);
+  S Xn[4], Kp[4], An[4], Kn[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    Xn[q] = p.X[q] + p.K[q] * dl + 0.5 * p.A[q] * dl * dl;
+    Xn[q] = p.X[q] + p.K[q] * dl + 0.5f * p.A[q] * dl * dl;
     Kp[q] = p.K[q] + p.A[q] * dl;
   }
   if (in_grid(m, Xn)) return 2;
-  Geo G;
+  GeoT<S> G;
   metric_eval<true, KERR>(m, Xn[1], Xn[2], G);
   int it = 0;
   bool conv = false;
   while (true) {
     accel<KERR>(G, Kp, An);
-    double num = 0.0, den = 0.0;
+    decltype(vmag(dl)) num = 0, den = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      Kn[q] = p.K[q] + 0.5 * (p.A[q] + An[q]) * dl;
-      num += fabs(Kn[q] - Kp[q]);
-      den += fabs(Kn[q]);
+      Kn[q] = p.K[q] + 0.5f * (p.A[q] + An[q]) * dl;
+      num += vdiff(Kn[q], Kp[q]);
+      den += vmag(Kn[q]);
     }
     ++it;
 #pragma unroll
     for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
-    if (num < m.verlet_tol * den) {
+    if (below_tol(num, m.verlet_tol, den)) {
       conv = true;
       break;
     }
@@ -433,13 +451,12 @@ static __device__ int step_free(const DevModel &m, const PushIO &io, Ph &p, Loca
   ls.steps++;
   p.ana = 0.0;
   p.ans = 0.0;
-  const double r = G.r;
   int status = 0;
-  if (r >= m.r_record) {
+  if (at_record(m, G.r)) {
     record(m, io, G, p);
     status = 1;
     ls.rec++;
-  } else if (r <= m.r_capture) {
+  } else if (at_capture(m, G.r)) {
     status = 3;
     ls.capt++;
   } else if (!(p.w > 0.0)) {
@@ -484,12 +501,13 @@ __device__ __forceinline__ void flush_stats(const LocalStats &ls, unsigned long 
   }
 }
 
-__device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const Ph &p) {
+template <typename S>
+__device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const PhT<S> &p) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    P.X[q][i] = p.X[q];
-    P.K[q][i] = p.K[q];
-    P.A[q][i] = p.A[q];
+    P.X[q][i] = to_d(p.X[q]);
+    P.K[q][i] = to_d(p.K[q]);
+    P.A[q][i] = to_d(p.A[q]);
   }
   P.w[i] = p.w;
   P.wb[i] = p.wb;
@@ -505,12 +523,13 @@ __device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const Ph &p) {
   if (P.model) P.model[i] = (int16_t)p.model;
 }
 
-__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, Ph &p) {
+template <typename S>
+__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S> &p) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    p.X[q] = P.X[q][i];
-    p.K[q] = P.K[q][i];
-    p.A[q] = P.A[q][i];
+    p.X[q] = from_d<S>(P.X[q][i]);
+    p.K[q] = from_d<S>(P.K[q][i]);
+    p.A[q] = from_d<S>(P.A[q][i]);
   }
   p.w = P.w[i];
   p.wb = P.wb[i];
@@ -530,39 +549,41 @@ __device__ __forceinline__ void load_ph(const Pool &P, int64_t i, Ph &p) {
 // network inputs), one tensor-core evaluation for the CTA's 128 superphotons, part B (optical
 // depths, scattering, termination).  Identical to step<true> except for where K2 and sigma_h
 // come from.
+template <typename S>
 struct SurCarry {
-  double X0[4], K0[4], dl;
-  double r, cth, g00, g01, g03;
+  S X0[4], K0[4];
+  double dl, r, cth, g00, g01, g03;
   CoefA a;
 };
 
-static __device__ void step_sur_a(const DevModel &m, Ph &p, SurCarry &sc, LocalStats &ls) {
-  double dl = stepsize(m, p.X, p.K);
-  double Kp[4], An[4], Kn[4];
+template <typename S>
+static __device__ void step_sur_a(const DevModel &m, PhT<S> &p, SurCarry<S> &sc, LocalStats &ls) {
+  S dl = stepsize(m, p.X, p.K);
+  S Kp[4], An[4], Kn[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     sc.X0[q] = p.X[q];
     sc.K0[q] = p.K[q];
-    p.X[q] = sc.X0[q] + sc.K0[q] * dl + 0.5 * p.A[q] * dl * dl;
+    p.X[q] = sc.X0[q] + sc.K0[q] * dl + 0.5f * p.A[q] * dl * dl;
     Kp[q] = sc.K0[q] + p.A[q] * dl;
   }
-  Geo G;
+  GeoT<S> G;
   metric_eval<true>(m, p.X[1], p.X[2], G);
   int it = 0;
   bool conv = false;
   while (true) {
     accel(G, Kp, An);
-    double num = 0.0, den = 0.0;
+    decltype(vmag(dl)) num = 0, den = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      Kn[q] = sc.K0[q] + 0.5 * (p.A[q] + An[q]) * dl;
-      num += fabs(Kn[q] - Kp[q]);
-      den += fabs(Kn[q]);
+      Kn[q] = sc.K0[q] + 0.5f * (p.A[q] + An[q]) * dl;
+      num += vdiff(Kn[q], Kp[q]);
+      den += vmag(Kn[q]);
     }
     ++it;
 #pragma unroll
     for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
-    if (num < m.verlet_tol * den) {
+    if (below_tol(num, m.verlet_tol, den)) {
       conv = true;
       break;
     }
@@ -579,24 +600,25 @@ static __device__ void step_sur_a(const DevModel &m, Ph &p, SurCarry &sc, LocalS
   if (!conv) ls.nonconv++;
   p.nsteps++;
   ls.steps++;
-  sc.dl = dl;
-  sc.r = G.r;
-  sc.cth = G.cth;
-  sc.g00 = G.g00;
-  sc.g01 = G.g01;
-  sc.g03 = G.g03;
+  sc.dl = to_d(dl);
+  sc.r = to_d(G.r);
+  sc.cth = to_d(G.cth);
+  sc.g00 = to_d(G.g00);
+  sc.g01 = to_d(G.g01);
+  sc.g03 = to_d(G.g03);
   coefficients32_a(m, G, p.X, p.K, sc.a);
 }
 
-static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, Ph &p, const SurCarry &sc, const float out[3],
-                           LocalStats &ls) {
+template <typename S>
+static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, PhT<S> &p, const SurCarry<S> &sc,
+                                  const float out[3], LocalStats &ls) {
   const bool scat = m.scatter && p.nsc < m.n_sc_max;
   Coef c;
   coefficients32_b(m, sc.a, out, scat, c);
   const double C = m.Ccoef, dl = sc.dl;
   double tau_a = 0.5 * (p.ana + c.ana) * C * dl;
   double w0 = p.w;
-  double wn = w0 * exp(-tau_a);
+  double wn = w0 * (double)expf((float)-tau_a);   // FP32 attenuation, as in step<true>
   if (scat) {
     double tau_s = 0.5 * (p.ans + c.ans) * C * dl;
     if (tau_s > 0.0) {
@@ -607,8 +629,8 @@ static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, Ph &p, co
         double Xe[4], Ke[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          Xe[q] = sc.X0[q] + f * (p.X[q] - sc.X0[q]);
-          Ke[q] = sc.K0[q] + f * (p.K[q] - sc.K0[q]);
+          Xe[q] = to_d(sc.X0[q]) + f * (to_d(p.X[q]) - to_d(sc.X0[q]));
+          Ke[q] = to_d(sc.K0[q]) + f * (to_d(p.K[q]) - to_d(sc.K0[q]));
         }
         double we = w0 * exp(-f * tau_a);
         uint64_t cid = child_id(p.s.id, p.nev);

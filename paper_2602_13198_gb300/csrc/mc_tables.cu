@@ -469,10 +469,38 @@ static cudaError_t fma_peak_t(double *flops) {
 cudaError_t fma_peak(bool fp64, double *flops) { return fp64 ? fma_peak_t<double>(flops) : fma_peak_t<float>(flops); }
 
 // ---------------------------------------------------------------- special-function self-test
-__global__ void k_selftest_math(int which, const double *x, double *y, double *ref, int64_t n) {
+// Double-float function table: 2^(j/32) for j < 32, then sin(pi j/32) for j < 64 (by quadrant from the
+// first-quadrant sine and cosine, so that 0 and +-1 are exact), split from FP64 values.
+void df_table_host(df *t) {
+  for (int j = 0; j < 32; ++j) t[kDfTabExp + j] = df_const(std::exp2(j / 32.0));
+  for (int j = 0; j < 64; ++j) {
+    const int q = j / 16, r = j % 16;
+    double v = (q % 2 == 0) ? std::sin(kPI * r / 32.0) : std::cos(kPI * r / 32.0);
+    if (q >= 2) v = -v;
+    t[kDfTabSin + j] = df_const(v);
+  }
+}
+
+__global__ void k_selftest_math(int which, const double *x, double *y, double *ref, int64_t n, const df *T) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = x[i];
+  // double-float functions: the reference takes the input as split to double-float
+  const df vd = df_from(v);
+  if (which == 3) {
+    y[i] = df_to(df_exp(vd, T));
+    ref[i] = exp(df_to(vd));
+    return;
+  }
+  if (which == 4 || which == 5) {
+    df s, c;
+    df_sincospi(vd, T, s, c);
+    y[i] = df_to(which == 4 ? s : c);
+    double rs, rc;
+    sincospi(df_to(vd), &rs, &rc);
+    ref[i] = which == 4 ? rs : rc;
+    return;
+  }
   if (which == 2) {
     y[i] = pow_sixth(v);
     ref[i] = cbrt(sqrt(v));
@@ -486,9 +514,19 @@ __global__ void k_selftest_math(int which, const double *x, double *y, double *r
 }
 
 cudaError_t selftest_math(int which, const double *x_dev, double *y_dev, double *ref_dev, int64_t n) {
-  if (n > 0) k_selftest_math<<<(unsigned)((n + 255) / 256), 256>>>(which, x_dev, y_dev, ref_dev, n);
-  cudaError_t e = cudaGetLastError();
-  return e != cudaSuccess ? e : cudaDeviceSynchronize();
+  df host[kDfTabN];
+  df_table_host(host);
+  df *tab = nullptr;
+  cudaError_t e = cudaMalloc(&tab, sizeof(host));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(tab, host, sizeof(host), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n > 0) {
+    k_selftest_math<<<(unsigned)((n + 255) / 256), 256>>>(which, x_dev, y_dev, ref_dev, n, tab);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(tab);
+  return e;
 }
 
 }  // namespace mcgb

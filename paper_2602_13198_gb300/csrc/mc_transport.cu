@@ -66,7 +66,7 @@ template <bool MIXED, int PHASE, bool KERR>
 __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  Ph p;
+  PhT<GeoScalar<MIXED>> p;   // double-float geodesic in the mixed-precision form
   int64_t slot = -1;
   bool live = false;
   bool exhausted = false;
@@ -121,11 +121,11 @@ __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, Pus
   tc_setup(T, smem_sur, sv);
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  Ph p;
+  PhT<df> p;
   int64_t slot = -1;
   bool live = false;
   bool exhausted = false;
-  SurCarry sc;
+  SurCarry<df> sc;
   while (true) {
     if (!exhausted) {
       unsigned idle = __ballot_sync(0xffffffffu, !live);

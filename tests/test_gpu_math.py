@@ -1,6 +1,6 @@
 """The library's own special-function implementations against CUDA's on the device: the Taylor
-sine/cosine of the small theta-map angle (metric evaluation) and the Newton x^(1/6) of the
-synchrotron function."""
+sine/cosine of the small theta-map angle (metric evaluation), the Newton x^(1/6) of the
+synchrotron function, and the double-float e^x and sin/cos(pi x) of the mixed-precision geodesic."""
 import numpy as np
 import pytest
 
@@ -37,3 +37,31 @@ def test_sixth_root_matches_cuda():
     # X z^5 takes four roundings after the Newton steps, cbrt(sqrt(x)) two: within 10 ulp
     assert rel.max() < 10 * 2.2e-16, rel.max()
     assert abs(y[-8] - 1.0) <= 2.3e-16 and abs(y[-7] - 2.0) <= 4.5e-16   # x = 1 and x = 64
+
+
+def test_double_float_exp_matches_cuda():
+    mc = _mc()
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(-20.0, 20.0, 200000), np.linspace(-0.02, 0.02, 4001),
+                        np.array([0.0, 1.0, np.log(2.0), 0.6931471805599453 / 64, 10.0, -10.0])])
+    y, ref = mc.selftest_math(3, x)
+    rel = np.abs(y / ref - 1.0)
+    # 48-bit arithmetic: the reduction x - k ln2/32 carries |x| 2^-48 of absolute error
+    bound = 4.0 * 2.0 ** -48 * np.maximum(1.0, np.abs(x))
+    assert np.all(rel <= bound), (rel / bound).max()
+    assert y[-6] == 1.0
+
+
+@pytest.mark.parametrize("which", [4, 5])
+def test_double_float_sincospi_matches_cuda(which):
+    mc = _mc()
+    rng = np.random.default_rng(6 + which)
+    x = np.concatenate([rng.uniform(-2.0, 3.0, 200000), np.arange(-64, 97) / 32.0,
+                        np.array([1e-9, 0.5 - 1e-12, 1.0 - 1e-15])])
+    y, ref = mc.selftest_math(which, x)
+    assert np.abs(y - ref).max() <= 4.0 * 2.0 ** -48
+    # exact at multiples of 1/2
+    k = np.arange(-64, 97) / 32.0
+    half = (np.abs(k * 2 - np.round(k * 2)) == 0)
+    yk = y[200000:200000 + len(k)]
+    assert np.all(np.isin(np.abs(yk[half]), [0.0, 1.0]))
