@@ -51,9 +51,9 @@ FLOP_EMIT = 2000.0
 FLOP_EVENT = 1500.0
 GEN_LAUNCHES = 7          # zone prep, weight partials, weight final, counts, 3 scan kernels
 # DRAM bytes (read + write) per superphoton of the first in-grid launch of a job, from one ncu capture
-# of k_push<in-grid> (FP64) at N_s = 1e6, tau_T = 1e-2 (224.5 MB for ~787k superphotons); traffic grows
+# of k_push<in-grid> (FP64) at N_s = 1e6, tau_T = 1e-2 (225.1 MB for ~787k superphotons); traffic grows
 # in proportion to the superphotons a launch carries.  Must be re-taken whenever that kernel changes.
-TRAFFIC_B_PER_PH_FP64 = 285.3
+TRAFFIC_B_PER_PH_FP64 = 286.2
 
 
 def log(*a):
@@ -133,6 +133,24 @@ SURVEY = ("batched parameter survey: 64 synthetic 2-D Fishbone-Moncrief tori dra
           "{-0.94,-0.5,0,0.5,0.94} x R_high {1,10,40,160} x accretion scale {0.5,1,2,4} (M_unit = 5e17 g x scale), "
           "grids 128x64 / 192x96 / 256x128, N_s log-uniform in [1e5, 1e7] per model, bias 96e4 Theta_e^2 (<= 1e5)")
 FLOP_SUR_EVAL = 2.0 * (3 * 64 + 64 * 64 + 64 * 3)   # one 3-64-64-3 network evaluation (algorithmic)
+# The mixed-precision forms run the geodesic in double-float on the FP32 pipes.  FP32 flops per
+# FP64-equivalent operation of the hand count, from the library's double-float arithmetic: an
+# addition is 20 (two two-sums, two fast two-sums, two additions), a product 10 (a product, three
+# FMAs at 2, a fast two-sum); the geodesic's mix of the two averages about 15.
+DF_FLOPS_PER_OP = 15.0
+
+
+def df_roofline(ops, seconds, fp32_peak, fp64_peak, kernel):
+    """Roofline of a double-float transport kernel against the measured FP32 peak (estimate: the hand
+    count's FP64-equivalent operations x DF_FLOPS_PER_OP), with the FP64-accurate operation rate beside
+    it and its ratio to what the FP64 pipe could sustain."""
+    eq = ops / seconds
+    fp32 = DF_FLOPS_PER_OP * eq
+    return {"bound": "alu", "kernel": kernel, "achieved": fp32 / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+            "frac": fp32 / fp32_peak, "peak_source": "measured FP32 FMA-chain (mc_fma_peak)",
+            "note": "geodesic in double-float on the FP32 pipes; achieved = hand-counted FP64-equivalent "
+                    "operations x %.0f FP32 flops each (estimate)" % DF_FLOPS_PER_OP,
+            "fp64_equivalent_tflops": eq / 1e12, "vs_fp64_peak": eq / fp64_peak}
 
 
 def spectrum_error(s_new, s_ref, min_count=16):
@@ -224,10 +242,8 @@ def survey_forms(args, dev, stream, flush, fp64_peak, bf16_peak):
              "autotune": {"min_blocks_per_sm": st["batch_min_blocks"], "ctas": st["batch_ctas"],
                           "graph": bool(st["batch_graph"]), "tune_and_capture_s": t_setup},
              "gpu_launches": 1 + GEN_LAUNCHES * len(specs) + 1,
-             "roofline": {"bound": "alu", "kernel": "k_batch (whole batched transport, one cooperative launch)",
-                          "achieved": fp64_flops / kern_s / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                          "frac": fp64_flops / kern_s / fp64_peak,
-                          "peak_source": "measured FP64 FMA-chain (mc_fma_peak); FP64 share of the mixed path only"}}
+             "roofline": df_roofline(fp64_flops, kern_s, fp32_peak, fp64_peak,
+                                     "k_batch (whole batched transport, one cooperative launch)")}
         if sur:
             tf = FLOP_SUR_EVAL * st["n_steps_grid"] / kern_s / 1e12
             r["surrogate"] = {"validation_loss": vloss, "tensor_achieved_tflops": tf, "bf16_peak_tflops": bf16_peak,
@@ -396,17 +412,20 @@ def main():
     achieved = flops_grid / t_grid / 1e12
     peak = fp64_peak / 1e12
     per_run = units / max(args.steps, 1)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": (TRAFFIC_B_PER_PH_FP64 * per_run
-                            if args.precision == "fp64" and TRAFFIC_B_PER_PH_FP64 else None),
-                "traffic_note": "bytes of the first in-grid launch of a run (it carries every primary): ncu DRAM "
-                                "read+write per superphoton at N_s=1e6 x superphotons per run",
-                "kernel": "k_push<in-grid> (%s): dominant kernel, %.0f%% of transport time"
-                          % (args.precision, 100 * t_grid / max(t_transport, 1e-30)),
-                "peak_source": "measured: project FP64 FMA-chain microbenchmark on this GPU (mc_fma_peak)",
-                "fp32_peak_tflops": fp32_peak / 1e12,
-                "phase_s": {"init": t_init, "in_grid": t_grid, "free": t_free},
-                "transport_achieved_tflops": flops / t_transport / 1e12}
+    if args.precision == "mixed":
+        roofline = df_roofline(flops_grid, t_grid, fp32_peak, fp64_peak, "k_push<in-grid> (mixed, double-float geodesic)")
+        roofline.update({"traffic": None, "phase_s": {"init": t_init, "in_grid": t_grid, "free": t_free}})
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": TRAFFIC_B_PER_PH_FP64 * per_run if TRAFFIC_B_PER_PH_FP64 else None,
+                    "traffic_note": "bytes of the first in-grid launch of a run (it carries every primary): ncu DRAM "
+                                    "read+write per superphoton at N_s=1e6 x superphotons per run",
+                    "kernel": "k_push<in-grid> (%s): dominant kernel, %.0f%% of transport time"
+                              % (args.precision, 100 * t_grid / max(t_transport, 1e-30)),
+                    "peak_source": "measured: project FP64 FMA-chain microbenchmark on this GPU (mc_fma_peak)",
+                    "fp32_peak_tflops": fp32_peak / 1e12,
+                    "phase_s": {"init": t_init, "in_grid": t_grid, "free": t_free},
+                    "transport_achieved_tflops": flops / t_transport / 1e12}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

@@ -172,6 +172,20 @@ DevModel make_model(const mc_ctx *c) {
   m.fidx3 = (float)m.idx3;
   m.fx2_0 = (float)m.x2_0;
   m.fx3_0 = (float)m.x3_0;
+  m.fNe_unit = (float)m.Ne_unit;
+  m.fB_unit = (float)m.B_unit;
+  m.fgam = (float)m.gam;
+  m.fR_low = (float)m.R_low;
+  m.fR_high = (float)m.R_high;
+  m.fthetae_max = (float)m.thetae_max;
+  m.fithetae_max = (float)m.ithetae_max;
+  m.fthetae_min = (float)m.thetae_min;
+  m.feps_geo = (float)m.eps_geo;
+  m.fverlet_tol = (float)m.verlet_tol;
+  m.hslope1 = m.hslope == 1.0;
+  m.kappa_on = m.kappa > 0.0;
+  m.lnK2f = c->lnK2f;
+  m.hotf = c->hotf;
   m.zlnw = c->zlnw;
   m.zbq = c->zbq;
   m.zbnt = c->zbnt;
@@ -266,6 +280,8 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
   c->nK2 = (int)std::floor((kK2LnT1 - kK2LnT0) / kK2Step + 0.5) + 1;
   c->lnF = (double *)dev_alloc(c, sizeof(double) * c->nF);
   c->lnK2 = (double *)dev_alloc(c, sizeof(double) * c->nK2);
+  c->lnK2f = (float *)dev_alloc(c, sizeof(float) * c->nK2);
+  c->hotf = (float *)dev_alloc(c, sizeof(float) * kHotNT * kHotNE);
   c->hot = (double *)dev_alloc(c, sizeof(double) * kHotNT * kHotNE);
   c->gl = (double *)dev_alloc(c, sizeof(double) * (128 + 128 + 64));
   c->dtab = (df *)dev_alloc(c, sizeof(df) * kDfTabN);
@@ -320,6 +336,12 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
   }
   DevModel m = make_model(c);
   launch_tables(m, c->lnF, c->lnK2, c->hot, c->gl, c->gl + 128, c->gl + 256, 0);
+  if (!c->lnK2f || !c->hotf) {
+    mc_free(c);
+    return fail(nullptr, MC_ERR_OOM, "device allocation failed");
+  }
+  launch_to_f32(c->lnK2, c->lnK2f, c->nK2, 0);
+  launch_to_f32(c->hot, c->hotf, kHotNT * kHotNE, 0);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     std::string msg = std::string("table build failed: ") + cudaGetErrorString(e);

@@ -114,6 +114,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
           if (k < (unsigned long long)n_in) {
             slot = list_in[k];
             load_ph(b.pool, slot, p);
+            p.wthr = sm[p.model].roulette_w * p.wb;
             live = true;
           }
         }
@@ -165,11 +166,15 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
   }
 }
 
+// Dynamic shared memory of a batch CTA: the model descriptors, then (surrogate) the network's tiles.
+constexpr int kModelsSmem = (int)((sizeof(DevModel) * kMaxBatch + 127) / 128 * 128);
+static int batch_smem_bytes(bool sur) { return kModelsSmem + (sur ? tc_smem_bytes(kTcGroupsMax) : 0); }
+
 template <bool MIXED, bool SUR, int MINB>
 __global__ void __launch_bounds__(SUR ? 256 : 128, MINB) k_batch(BatchIO b) {
-  __shared__ DevModel sm[kMaxBatch];
   __shared__ int64_t soff[kMaxBatch + 1];
   extern __shared__ __align__(128) unsigned char dyn[];
+  DevModel *sm = reinterpret_cast<DevModel *>(dyn);
   {
     const unsigned long long *src = (const unsigned long long *)b.models;
     unsigned long long *dst = (unsigned long long *)sm;
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(SUR ? 256 : 128, MINB) k_batch(BatchIO b) {
   }
   __syncthreads();
   TcMlp T;
-  if (SUR) tc_setup(T, dyn, b.sv);
+  if (SUR) tc_setup(T, dyn + kModelsSmem, b.sv);
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long *agrid = b.ph + kPhBase, *afree = agrid + kMaxPhases, *cgrid = afree + kMaxPhases,
                      *cfree = cgrid + kMaxPhases;
@@ -454,12 +459,10 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
   if (sur) b.sv = surrogate_view(c0);
   b.timeout_ns = 120e9;
   BatchKernel kern = pick_kernel(mixed, sur, minb);
-  int smem = sur ? tc_smem_bytes(kTcGroupsMax) : 0;
-  if (smem) {
-    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    // shared memory over L1: a CTA with two network row groups needs ~127 KB
-    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  }
+  const int smem = batch_smem_bytes(sur);
+  cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // shared memory over L1: the descriptors take ~50 KB, a CTA with two network row groups ~127 KB more
+  cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   void *args[] = {&b};
   if (timed) cudaEventRecord(bs->e0, st);
   e = cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(sur ? 128 * kTcGroupsMax : 128), args, smem, st);
@@ -470,12 +473,9 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
 static int max_ctas(mc_ctx *c0, int minb) {
   const bool mixed = c0->p.precision == MC_PREC_MIXED, sur = c0->p.surrogate == 1;
   BatchKernel kern = pick_kernel(mixed, sur, minb);
-  int smem = sur ? tc_smem_bytes(kTcGroupsMax) : 0;
-  if (smem) {
-    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    // shared memory over L1: a CTA with two network row groups needs ~127 KB
-    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  }
+  const int smem = batch_smem_bytes(sur);
+  cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)kern, sur ? 128 * kTcGroupsMax : 128, smem);
   if (sur) n = std::min(n, 4);   // at most four CTAs x 128 TMEM columns per SM

@@ -76,6 +76,10 @@ struct DevModel {
   df dpi2hh, dhh_pi, dd2th;   // pi (1 - h), (1 - h) / (2 pi), -2 pi^2 (1 - h): the theta map in double-float
   const df *dtab;             // double-float function table (kDfTabN entries)
   float fidx1, fidx2, fidx3, fx2_0, fx3_0;   // FP32 grid constants for the double-float zone lookup
+  // FP32 copies of model constants and tables read by the FP32 arithmetic (no FP64 conversions there)
+  float fNe_unit, fB_unit, fgam, fR_low, fR_high, fthetae_max, fithetae_max, fthetae_min, feps_geo, fverlet_tol;
+  int hslope1, kappa_on;
+  const float *lnK2f, *hotf;
   double kappa;           // > 0: kappa-distributed electrons for the synchrotron terms
   const double *kapJ, *kapA, *kapI;   // ln J, ln A, ln I on the kappa grid [kKapNX][kKapNW]
   const double *kapH;     // ln(sigma_h / sigma_T) of the kappa population [kKapNW][kHotNE]
@@ -196,7 +200,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
     r = df_exp(x1s, m.dtab);
     df sp, cp;
     df_sincospi(x2s, m.dtab, sp, cp);
-    if (m.hslope == 1.0) {
+    if (m.hslope1) {
       dth = cst<S>(kPI);
       d2th = cst<S>(0.0);
       s = sp;
@@ -239,7 +243,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
   S opf = 1.0f + f;
   // Kerr-Schild components (t, r, theta, phi)
   S Gtt = f - 1.0f, Gtr = f, Grr = opf, Ghh = sig;
-  S Gtp = KERR ? -a * f * s2 : from_d<S>(0.0), Grp = KERR ? -a * s2 * opf : from_d<S>(0.0);
+  S Gtp = KERR ? -a * f * s2 : cst<S>(0.0), Grp = KERR ? -a * s2 * opf : cst<S>(0.0);
   S Gpp = KERR ? s2 * (sig + a2 * s2 * opf) : s2 * sig;
   G.r = r;
   G.sth = s;
@@ -256,7 +260,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
   G.G00 = -opf;
   G.G01 = f * ir;
   G.G11 = (KERR ? r * r - 2.0f * M * r + a2 : r * r - 2.0f * M * r) * isig * ir * ir;
-  G.G13 = KERR ? a * isig * ir : from_d<S>(0.0);
+  G.G13 = KERR ? a * isig * ir : cst<S>(0.0);
   G.G22 = isig * idth * idth;
   G.G33 = isig * is2;
   if (!DERIV) return;
@@ -264,7 +268,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
   S dfr = 2.0f * M * (sig - 2.0f * r * r) * isig * isig;
   if constexpr (!KERR) {
     // a = 0: f, g_tr, g_rr depend on r only; g_thth = r^2, g_phph = r^2 sin^2
-    const S zero = from_d<S>(0.0);
+    const S zero = cst<S>(0.0);
     G.d100 = r * dfr;
     G.d101 = r * (r * dfr + Gtr);
     G.d103 = zero;
@@ -375,7 +379,7 @@ __device__ __forceinline__ df stepsize<df>(const DevModel &m, const df X[4], con
   const float x2 = to_f(X[2]);
   const float x2n = fminf(fabsf(x2), fabsf(1.0f - x2));
   const float den = (fabsf(K[1].hi) + fabsf(K[3].hi)) * x2n + fabsf(K[2].hi) + 1e-30f;
-  return df{(float)m.eps_geo * x2n / den, 0.0f};
+  return df{m.feps_geo * x2n / den, 0.0f};
 }
 
 // ---------------------------------------------------------------- tables
@@ -418,9 +422,9 @@ __device__ __forceinline__ double lnK2_of_ln(const DevModel &m, double lt) {
 __device__ __forceinline__ float K2_of_f(const DevModel &m, float thetae) {
   if (m.k2_mode == 1) return 2.0f * thetae * thetae;
   float f = (__logf(thetae) - (float)kK2LnT0) * (float)(1.0 / kK2Step);
-  int i = max(0, min((int)f, m.nK2 - 2));
+  int i = max(0, min(zone_floor(f), m.nK2 - 2));
   float u = f - i;
-  float l = (1.0f - u) * (float)m.lnK2[i] + u * (float)m.lnK2[i + 1];
+  float l = (1.0f - u) * m.lnK2f[i] + u * m.lnK2f[i + 1];
   return __expf(l);
 }
 
@@ -448,11 +452,11 @@ __device__ __forceinline__ float hot_lookup_f(const DevModel &m, float thetae, f
   float fe = (__logf(eps) - (float)kHotLE0) * (float)((kHotNE - 1) / (kHotLE1 - kHotLE0));
   ft = fminf(fmaxf(ft, 0.0f), (float)(kHotNT - 1));
   fe = fminf(fmaxf(fe, 0.0f), (float)(kHotNE - 1));
-  int i = min((int)ft, kHotNT - 2), j = min((int)fe, kHotNE - 2);
+  const int i = max(0, min(zone_floor(ft), kHotNT - 2)), j = max(0, min(zone_floor(fe), kHotNE - 2));
   float a = ft - i, b = fe - j;
-  const double *h = m.hot;
-  float v00 = (float)h[i * kHotNE + j], v01 = (float)h[i * kHotNE + j + 1];
-  float v10 = (float)h[(i + 1) * kHotNE + j], v11 = (float)h[(i + 1) * kHotNE + j + 1];
+  const float *h32 = m.hotf;
+  float v00 = h32[i * kHotNE + j], v01 = h32[i * kHotNE + j + 1];
+  float v10 = h32[(i + 1) * kHotNE + j], v11 = h32[(i + 1) * kHotNE + j + 1];
   float l = (1 - a) * (1 - b) * v00 + (1 - a) * b * v01 + a * (1 - b) * v10 + a * b * v11;
   return (float)kSIGT * __expf(l);
 }
@@ -571,6 +575,11 @@ __device__ __forceinline__ double Gsyn(double X) {
 }
 
 // ---------------------------------------------------------------- fluid (sections 2.5-2.7)
+// model constant in the plasma arithmetic's type: the double, or its FP32 copy
+template <typename T> __device__ __forceinline__ T mv(double d, float f);
+template <> __device__ __forceinline__ double mv<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float mv<float>(double, float f) { return f; }
+
 // metric component of scalar GS as the plasma arithmetic's type T
 template <typename T> __device__ __forceinline__ T cvt(double x) { return (T)x; }
 template <typename T> __device__ __forceinline__ T cvt(df x);
@@ -613,7 +622,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   R di, dj;
   {
     const R f1 = zone_coord(m, X, 1);
-    i = (int)floor(f1);
+    i = zone_floor(f1);
     di = f1 - i;
     if (m.n1 == 1) { i = 0; di = 0; }
     else if (i < 0) { i = 0; di = 0; }
@@ -621,7 +630,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   }
   {
     const R f2 = zone_coord(m, X, 2);
-    j = (int)floor(f2);
+    j = zone_floor(f2);
     dj = f2 - j;
     if (m.n2 == 1) { j = 0; dj = 0; }
     else if (j < 0) { j = 0; dj = 0; }
@@ -631,9 +640,9 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   R dk = 0;
   if (m.n3 > 1) {
     const R f3 = zone_coord(m, X, 3);
-    R fl = floor(f3);
-    dk = f3 - fl;
-    long long kk = (long long)fl;
+    const int ki = zone_floor(f3);
+    dk = f3 - (R)ki;
+    long long kk = ki;
     k0 = (int)(((kk % m.n3) + m.n3) % m.n3);
     k1 = (k0 + 1) % m.n3;
   }
@@ -730,32 +739,32 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<
   if (ucon_out) { ucon_out[0] = u0; ucon_out[1] = u1; ucon_out[2] = u2; ucon_out[3] = u3; }
   if (bcon_out) { bcon_out[0] = b0; bcon_out[1] = b1; bcon_out[2] = b2; bcon_out[3] = b3; }
   P.bsq = b0 * bc0 + b1 * bc1 + b2 * bc2 + b3 * bc3;
-  P.ne = (rho > (T)0) ? rho * (T)m.Ne_unit : (T)0;
+  P.ne = (rho > (T)0) ? rho * mv<T>(m.Ne_unit, m.fNe_unit) : (T)0;
   P.rb = (T)0;
   P.ith = (T)0;
   if (kF64) {
     // one reciprocal square root gives |b| (for B), 1/b^2 (for beta) and the 1/|b| of cos(theta_B)
     const T rb = (P.bsq > (T)0) ? rsqrt(P.bsq) : (T)0;
     P.rb = rb;
-    P.B = P.bsq * rb * (T)m.B_unit;
+    P.B = P.bsq * rb * mv<T>(m.B_unit, m.fB_unit);
   } else {
-    P.B = sqrt(fmax(P.bsq, (T)0)) * (T)m.B_unit;
+    P.B = sqrt(fmax(P.bsq, (T)0)) * mv<T>(m.B_unit, m.fB_unit);
   }
   if (rho > (T)0 && uu > (T)0) {
     // Theta_e = (m_p/m_e)(gam-1)(u/rho)/(1 + T_i/T_e), T_i/T_e = (R_high beta^2 + R_low)/(1 + beta^2)
     T num, den;
     if (P.bsq > (T)0) {
-      T beta = kF64 ? (T)2 * uu * ((T)m.gam - (T)1) * P.rb * P.rb : (T)2 * uu * ((T)m.gam - (T)1) / P.bsq;
+      T beta = kF64 ? (T)2 * uu * (mv<T>(m.gam, m.fgam) - (T)1) * P.rb * P.rb : (T)2 * uu * (mv<T>(m.gam, m.fgam) - (T)1) / P.bsq;
       T b2x = beta * beta;
-      num = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu * ((T)1 + b2x);
-      den = rho * ((T)1 + (T)m.R_low + ((T)1 + (T)m.R_high) * b2x);
+      num = (T)(kMP / kME) * (mv<T>(m.gam, m.fgam) - (T)1) * uu * ((T)1 + b2x);
+      den = rho * ((T)1 + mv<T>(m.R_low, m.fR_low) + ((T)1 + mv<T>(m.R_high, m.fR_high)) * b2x);
     } else {
-      num = (T)(kMP / kME) * ((T)m.gam - (T)1) * uu;
-      den = rho * ((T)1 + (T)m.R_high);
+      num = (T)(kMP / kME) * (mv<T>(m.gam, m.fgam) - (T)1) * uu;
+      den = rho * ((T)1 + mv<T>(m.R_high, m.fR_high));
     }
     T th, ith = (T)0;
     const T nd = num * den;
-    if (kF64 && nd > (T)1e-300 && nd < (T)1e300) {
+    if (kF64 && nd > (T)(kF64 ? 1e-300 : 1e-30) && nd < (T)(kF64 ? 1e300 : 1e30)) {
       // Theta_e and 1/Theta_e from one reciprocal
       const T inv = (T)1 / nd;
       th = num * (num * inv);
@@ -764,9 +773,9 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<
       th = num / den;
       if (kF64) ith = den / num;
     }
-    if (th > (T)m.thetae_max) {
-      th = (T)m.thetae_max;
-      ith = (T)m.ithetae_max;
+    if (th > mv<T>(m.thetae_max, m.fthetae_max)) {
+      th = mv<T>(m.thetae_max, m.fthetae_max);
+      ith = mv<T>(m.ithetae_max, m.fithetae_max);
     }
     P.thetae = th;
     P.ith = ith;
@@ -846,7 +855,7 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const GeoT<S> 
   // frequencies and emissivities span ~1e-40..1e40: keep the products in ranges float holds
   float nu9 = eps * (float)(kME * kCL * kCL / kHPL * 1e-9);   // nu / 1e9 Hz
   float ana = 0.0f;
-  if (P.thetae >= (float)m.thetae_min && P.B > 0.0f && P.bsq > 0.0f) {
+  if (P.thetae >= m.fthetae_min && P.B > 0.0f && P.bsq > 0.0f) {
     float kb = kf[0] * P.bcov[0] + kf[1] * P.bcov[1] + kf[2] * P.bcov[2] + kf[3] * P.bcov[3];
     float cth = fminf(1.0f, fmaxf(-1.0f, kb / (eps * sqrtf(P.bsq))));
     float s2 = 1.0f - cth * cth;
@@ -867,10 +876,10 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const GeoT<S> 
     }
   }
   c.ana = (double)ana;
-  if (m.kappa > 0.0) {
+  if (m.kappa_on) {
     // kappa population: its absorption integral (FP64 tables) in place of the thermal fit
     c.ana = 0.0;
-    if (P.thetae >= (float)m.thetae_min && P.B > 0.0f && P.bsq > 0.0f) {
+    if (P.thetae >= m.fthetae_min && P.B > 0.0f && P.bsq > 0.0f) {
       double kb = to_d(K[0]) * P.bcov[0] + to_d(K[1]) * P.bcov[1] + to_d(K[2]) * P.bcov[2] + to_d(K[3]) * P.bcov[3];
       double cth = fmin(1.0, fmax(-1.0, kb / ((double)eps * sqrt((double)P.bsq))));
       double s2 = 1.0 - cth * cth;
@@ -880,7 +889,7 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const GeoT<S> 
   // bremsstrahlung absorption in FP64 (n_e^2 leaves the FP32 range in dense plasma)
   if (m.brems) c.ana += brems_nu_alpha((double)P.ne, (double)P.thetae, (double)nu9 * 1e9);
   if (want_s) {
-    if (m.kappa > 0.0) {
+    if (m.kappa_on) {
       c.ans = (double)nu9 * 1e9 * (double)P.ne * kap_hot_lookup(m, (double)P.thetae, (double)eps);
     } else {
       float sh = hot_lookup_f(m, fmaxf(P.thetae, 1e-30f), eps);
@@ -919,7 +928,7 @@ __device__ __forceinline__ void coefficients32_a(const DevModel &m, const GeoT<S
   float nu9 = eps * (float)(kME * kCL * kCL / kHPL * 1e-9);
   a.nu9 = nu9;
   float lnK = 0.0f;
-  if (P.thetae >= (float)m.thetae_min && P.B > 0.0f && P.bsq > 0.0f) {
+  if (P.thetae >= m.fthetae_min && P.B > 0.0f && P.bsq > 0.0f) {
     float kb = kf[0] * P.bcov[0] + kf[1] * P.bcov[1] + kf[2] * P.bcov[2] + kf[3] * P.bcov[3];
     float cth = fminf(1.0f, fmaxf(-1.0f, kb / (eps * sqrtf(P.bsq))));
     float s2 = 1.0f - cth * cth;

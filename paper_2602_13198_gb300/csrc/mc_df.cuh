@@ -121,8 +121,29 @@ __device__ __forceinline__ float vdiff(df a, df b) {
 }
 __device__ __forceinline__ double vmag(double a) { return fabs(a); }
 __device__ __forceinline__ float vmag(df a) { return fabsf(a.hi); }
-__device__ __forceinline__ bool below_tol(double a, double tol, double b) { return a < tol * b; }
-__device__ __forceinline__ bool below_tol(float a, double tol, float b) { return a < (float)tol * b; }
+__device__ __forceinline__ bool below_tol(double a, double tol, float, double b) { return a < tol * b; }
+__device__ __forceinline__ bool below_tol(float a, double, float tolf, float b) { return a < tolf * b; }
+
+// Nearest integer of |x| < 2^22 with FP32 additions only: adding 1.5 * 2^23 leaves the integer in the
+// low mantissa bits (ties to even).  Returns it as a float and, in k, as an int; no conversion
+// instruction (those share the narrow FP64 pipe on this GPU).
+__device__ __forceinline__ float rint_shift(float x, int &k) {
+  const float t = __fadd_rn(x, 12582912.0f);
+  k = __float_as_int(t) - 0x4B400000;
+  return __fsub_rn(t, 12582912.0f);
+}
+// Cell index of a fractional table or zone coordinate: floor in FP64; in FP32 the shifted rounding of
+// f - 1/2, which at an exact integer may give the cell below with weight 1 on its upper corner (the
+// same linear blend).
+__device__ __forceinline__ int zone_floor(double f) { return (int)floor(f); }
+__device__ __forceinline__ int zone_floor(float f) {
+  int k;
+  rint_shift(__fsub_rn(f, 0.5f), k);
+  return k;
+}
+
+// 2^e for -126 <= e <= 127, from its bit pattern
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
 
 // ---- elementary functions in double-float (own range reductions and Taylor polynomials; the
 // high-order terms, below 2^-24 of the leading one, in FP32).  Both use a table of double-float
@@ -138,9 +159,10 @@ __device__ __forceinline__ df df_tab(const df *T, int i) {
 // Taylor series to t^6 (truncation below 2^-56 for |t| <= ln2/64).
 __device__ __forceinline__ df df_exp(df x, const df *T) {
   constexpr df kLn2_32 = df_const(0.6931471805599453094172321 / 32.0);
-  const float kf = rintf(x.hi * 46.16624130844683f);   // 32 / ln 2
+  int k;
+  const float kf = rint_shift(x.hi * 46.16624130844683f, k);   // 32 / ln 2
   const df t = x - kLn2_32 * kf;
-  const int k = (int)kf, j = k & 31, e = (k - j) / 32;
+  const int j = k & 31, e = (k - j) / 32;
   const float q = t.hi;
   const float tail = q * q * q * q * (1.0f / 24.0f + q * (1.0f / 120.0f + q * (1.0f / 720.0f)));
   const df t2 = t * t;
@@ -149,7 +171,8 @@ __device__ __forceinline__ df df_exp(df x, const df *T) {
   em1 = em1 + t2 * 0.5f;
   em1 = em1 + t;
   const df r = df_tab(T, kDfTabExp + j) * (em1 + 1.0f);
-  return {ldexpf(r.hi, e), ldexpf(r.lo, e)};
+  const float p2 = exp2i(e);
+  return {r.hi * p2, r.lo * p2};
 }
 
 // sin(pi x) and cos(pi x): x = j/32 + z with |z| <= 1/64, w = pi z, angle addition with the tabulated
@@ -157,9 +180,9 @@ __device__ __forceinline__ df df_exp(df x, const df *T) {
 // to w^7 and w^8 (truncation below 2^-57 for |w| <= pi/64).
 __device__ __forceinline__ void df_sincospi(df x, const df *T, df &s, df &c) {
   constexpr df kPi = df_const(3.14159265358979323846264338);
-  const float jf = rintf(x.hi * 32.0f);
+  int j;
+  const float jf = rint_shift(x.hi * 32.0f, j);
   const df z = x - jf * 0.03125f;   // exact: j/32 is an FP32 number
-  const int j = (int)jf;
   const df w = z * kPi;
   const float q = w.hi, q2 = q * q;
   const df w2 = w * w;

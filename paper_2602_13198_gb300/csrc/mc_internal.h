@@ -91,6 +91,7 @@ void launch_grid_to_aos(const void *src, int src_f32, void *dst, int dst_f32, in
 cudaError_t fma_peak(bool fp64, double *flops);
 cudaError_t selftest_math(int which, const double *x_dev, double *y_dev, double *ref_dev, int64_t n);
 void df_table_host(df *t);
+void launch_to_f32(const double *src, float *dst, int n, cudaStream_t st);
 void launch_kappa_tables(double kappa, double *lnF, double *lnJ, double *lnA, double *lnI, double *lnH,
                          const double *gl_mu, cudaStream_t st);
 // transport (mc_transport.cu)
@@ -126,6 +127,7 @@ struct mc_ctx {
   double *kapF = nullptr, *kapJ = nullptr, *kapA = nullptr, *kapI = nullptr;   // kappa tables
   double *kapH = nullptr;                   // kappa hot cross-section [kKapNW][kHotNE]
   mcgb::df *dtab = nullptr;                 // double-float function table (exp2, sin pi)
+  float *lnK2f = nullptr, *hotf = nullptr;  // FP32 copies of the K2 and hot cross-section tables
   int prim_f32 = 0;
   int n1 = 0, n2 = 0, n3 = 0;
   int64_t nz = 0;

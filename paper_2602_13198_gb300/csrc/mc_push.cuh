@@ -21,6 +21,7 @@ struct PhT {
   uint32_t nev;
   int nsteps;
   int model;   // index of the superphoton's model in a batched run (0 otherwise)
+  double wthr;   // roulette threshold roulette_w * wb (set at load; read by the double-float kernels)
 };
 using Ph = PhT<double>;
 // geodesic scalar of the transport kernels of each precision
@@ -241,6 +242,24 @@ __device__ __forceinline__ bool in_grid(const DevModel &m, const S X[4]) {
   if constexpr (std::is_same<S, df>::value) return df_ge(X[1], m.dx1_0) && df_le(X[1], m.dx1_hi);
   else return X[1] >= m.x1_0 && X[1] <= m.x1_hi;
 }
+// Weight tests of the termination logic.  The double-float transport compares the bit patterns of the
+// (non-negative) doubles as integers, which order them the same way, and so keeps FP64 instructions
+// out of its loop: w > 0 (NaN fails, as in FP64) and w < roulette_w * wb.
+template <typename S>
+__device__ __forceinline__ bool w_positive(const PhT<S> &p) {
+  if constexpr (std::is_same<S, df>::value) {
+    const long long b = __double_as_longlong(p.w);
+    return b > 0 && b <= 0x7FF0000000000000LL;
+  } else {
+    return p.w > 0.0;
+  }
+}
+template <typename S>
+__device__ __forceinline__ bool w_roulette(const DevModel &m, const PhT<S> &p) {
+  if constexpr (std::is_same<S, df>::value) return __double_as_longlong(p.w) < __double_as_longlong(p.wthr);
+  else return p.w < m.roulette_w * p.wb;
+}
+
 // termination radii (recording sphere, capture near the horizon) in the geodesic's scalar
 __device__ __forceinline__ bool at_record(const DevModel &m, double r) { return r >= m.r_record; }
 __device__ __forceinline__ bool at_record(const DevModel &m, df r) { return df_ge(r, m.dr_record); }
@@ -317,7 +336,7 @@ static __device__ bool step(const DevModel &m, const PushIO &io, PhT<S> &p, Loca
     ++it;
 #pragma unroll
     for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
-    if (below_tol(num, m.verlet_tol, den)) {
+    if (below_tol(num, m.verlet_tol, m.fverlet_tol, den)) {
       conv = true;
       break;
     }
@@ -378,11 +397,11 @@ static __device__ bool step(const DevModel &m, const PushIO &io, PhT<S> &p, Loca
   } else if (at_capture(m, G.r)) {
     status = 3;
     ls.capt++;
-  } else if (!(p.w > 0.0)) {
+  } else if (!w_positive(p)) {
     status = 2;
     ls.abs++;
   } else {
-    if (p.w < m.roulette_w * p.wb) {
+    if (w_roulette(m, p)) {
       if (rng_u(p.s, m.seed) < m.roulette_p) {
         p.w /= m.roulette_p;
         ls.roul++;
@@ -433,7 +452,7 @@ static __device__ int step_free(const DevModel &m, const PushIO &io, PhT<S> &p, 
     ++it;
 #pragma unroll
     for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
-    if (below_tol(num, m.verlet_tol, den)) {
+    if (below_tol(num, m.verlet_tol, m.fverlet_tol, den)) {
       conv = true;
       break;
     }
@@ -459,11 +478,11 @@ static __device__ int step_free(const DevModel &m, const PushIO &io, PhT<S> &p, 
   } else if (at_capture(m, G.r)) {
     status = 3;
     ls.capt++;
-  } else if (!(p.w > 0.0)) {
+  } else if (!w_positive(p)) {
     status = 2;
     ls.abs++;
   } else {
-    if (p.w < m.roulette_w * p.wb) {
+    if (w_roulette(m, p)) {
       if (rng_u(p.s, m.seed) < m.roulette_p) {
         p.w /= m.roulette_p;
         ls.roul++;
@@ -542,6 +561,14 @@ __device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S> &p) {
   p.nsc = P.nsc[i];
   p.nsteps = P.nsteps[i];
   p.model = P.model ? (int)P.model[i] : 0;
+  p.wthr = 0.0;
+}
+
+// load for a transport kernel of model m: also the roulette threshold
+template <typename S>
+__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S> &p, const DevModel &m) {
+  load_ph(P, i, p);
+  p.wthr = m.roulette_w * p.wb;
 }
 
 // ---------------------------------------------------------------- surrogate in-grid push
@@ -583,7 +610,7 @@ static __device__ void step_sur_a(const DevModel &m, PhT<S> &p, SurCarry<S> &sc,
     ++it;
 #pragma unroll
     for (int q = 0; q < 4; ++q) Kp[q] = Kn[q];
-    if (below_tol(num, m.verlet_tol, den)) {
+    if (below_tol(num, m.verlet_tol, m.fverlet_tol, den)) {
       conv = true;
       break;
     }
@@ -662,11 +689,11 @@ static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, PhT<S> &p
   } else if (r <= m.r_capture) {
     status = 3;
     ls.capt++;
-  } else if (!(p.w > 0.0)) {
+  } else if (!w_positive(p)) {
     status = 2;
     ls.abs++;
   } else {
-    if (p.w < m.roulette_w * p.wb) {
+    if (w_roulette(m, p)) {
       if (rng_u(p.s, m.seed) < m.roulette_p) {
         p.w /= m.roulette_p;
         ls.roul++;

@@ -469,6 +469,15 @@ static cudaError_t fma_peak_t(double *flops) {
 cudaError_t fma_peak(bool fp64, double *flops) { return fp64 ? fma_peak_t<double>(flops) : fma_peak_t<float>(flops); }
 
 // ---------------------------------------------------------------- special-function self-test
+__global__ void k_to_f32(const double *src, float *dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
+void launch_to_f32(const double *src, float *dst, int n, cudaStream_t st) {
+  if (n > 0) k_to_f32<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n);
+}
+
 // Double-float function table: 2^(j/32) for j < 32, then sin(pi j/32) for j < 64 (by quadrant from the
 // first-quadrant sine and cosine, so that 0 and +-1 are exact), split from FP64 values.
 void df_table_host(df *t) {

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
           unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
           if (k < (unsigned long long)io.n_in) {
             slot = io.list_in[k];
-            load_ph(io.pool, slot, p);
+            load_ph(io.pool, slot, p, m);
             live = true;
           }
         }
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, Pus
           unsigned long long k = base + __popc(idle & ((1u << lane) - 1u));
           if (k < (unsigned long long)io.n_in) {
             slot = io.list_in[k];
-            load_ph(io.pool, slot, p);
+            load_ph(io.pool, slot, p, m);
             live = true;
           }
         }
