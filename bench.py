@@ -167,7 +167,7 @@ def spectrum_error(s_new, s_ref, min_count=16):
     return lum, int(sel.sum()), int((sel & ok).sum())
 
 
-def survey_forms(args, dev, stream, flush, fp64_peak, bf16_peak):
+def survey_forms(args, dev, stream, flush, fp64_peak, fp32_peak, bf16_peak):
     """The metric's second form on the survey workload: the same 64 models and seeds run (1) as plain
     FP64, one mc_run per model, and (2) batched into one persistent launch (autotuned, replayed from
     a captured CUDA graph) in mixed precision, with and without the coefficient surrogate.  Each
@@ -443,7 +443,7 @@ def main():
                 bf16 = json.load(f).get("bf16_tflops")
         except Exception:
             bf16 = None
-        survey = survey_forms(args, dev, stream, flush, fp64_peak, bf16)
+        survey = survey_forms(args, dev, stream, flush, fp64_peak, fp32_peak, bf16)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
