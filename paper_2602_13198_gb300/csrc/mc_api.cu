@@ -570,7 +570,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
   if (use_sur && !c->sur_ready) return fail(c, MC_ERR_STATE, "surrogate requested but no trained weights");
   SurrogateView sv;
   std::memset(&sv, 0, sizeof(sv));
-  // two 128-row groups of the network per CTA (tensor-memory kernels run one CTA per SM)
+  // four 128-row groups of the network per CTA (tensor-memory kernels run one CTA per SM)
   const int sur_block = 128 * kTcGroupsMax;
   const int sur_smem = tc_smem_bytes(kTcGroupsMax);
   int occ_sur = 1;

@@ -121,7 +121,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
       }
     }
     if (SUR && PHASE == 0) {
-      // the row group (128 threads) moves in lockstep; the two groups of a CTA do not
+      // the row group (128 threads) moves in lockstep; the groups of a CTA do not
       const int grp = threadIdx.x >> 7;
       if (!group_or(grp, live)) {
         if (!group_or(grp, !exhausted)) break;
@@ -171,7 +171,7 @@ constexpr int kModelsSmem = (int)((sizeof(DevModel) * kMaxBatch + 127) / 128 * 1
 static int batch_smem_bytes(bool sur) { return kModelsSmem + (sur ? tc_smem_bytes(kTcGroupsMax) : 0); }
 
 template <bool MIXED, bool SUR, int MINB>
-__global__ void __launch_bounds__(SUR ? 256 : 128, MINB) k_batch(BatchIO b) {
+__global__ void __launch_bounds__(SUR ? 128 * kTcGroupsMax : 128, MINB) k_batch(BatchIO b) {
   __shared__ int64_t soff[kMaxBatch + 1];
   extern __shared__ __align__(128) unsigned char dyn[];
   DevModel *sm = reinterpret_cast<DevModel *>(dyn);
@@ -461,7 +461,7 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
   BatchKernel kern = pick_kernel(mixed, sur, minb);
   const int smem = batch_smem_bytes(sur);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  // shared memory over L1: the descriptors take ~50 KB, a CTA with two network row groups ~127 KB more
+  // shared memory over L1: the descriptors take ~48 KB, a CTA with four network row groups ~163 KB more
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   void *args[] = {&b};
   if (timed) cudaEventRecord(bs->e0, st);
@@ -478,7 +478,7 @@ static int max_ctas(mc_ctx *c0, int minb) {
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void *)kern, sur ? 128 * kTcGroupsMax : 128, smem);
-  if (sur) n = std::min(n, 4);   // at most four CTAs x 128 TMEM columns per SM
+  if (sur) n = std::min(n, 512 / kTmemCols);   // TMEM: 512 columns per SM
   return std::max(n, 0);
 }
 

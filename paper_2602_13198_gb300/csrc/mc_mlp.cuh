@@ -31,7 +31,7 @@ constexpr double kSurThetaK2Min = 0.3;   // o1 trained for Theta_e >= 0.3 only
 constexpr int kTileA1 = 128 * 16 * 2, kTileA2 = 128 * 64 * 2;
 constexpr int kTileB1 = 64 * 16 * 2, kTileB2 = 64 * 64 * 2, kTileB3 = 16 * 64 * 2;
 constexpr int kPackedBytes = kTileB1 + 2 * kTileB2 + 2 * kTileB3;   // B1, B2hi, B2lo, B3hi, B3lo
-constexpr int kTmemCols = 128;
+constexpr int kTmemCols = 256;   // 64 columns per row group, up to three groups
 
 // Byte offset of element (row, k) of a rows x K bf16 matrix in the canonical K-major layout without
 // swizzle: 8x8 core matrices of 128 contiguous bytes, core (row/8, k/8) at ((row/8)*(K/8) + k/8)*128.
@@ -122,10 +122,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Named barrier of one 128-thread row group (ids 1 and 2; id 0 is __syncthreads).
+// Named barrier of one 128-thread row group (ids 1 to 3; id 0 is __syncthreads).
 __device__ __forceinline__ void group_sync(int grp) {
   if (grp == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
-  else asm volatile("bar.sync 2, 128;" ::: "memory");
+  else if (grp == 1) asm volatile("bar.sync 2, 128;" ::: "memory");
+  else if (grp == 2) asm volatile("bar.sync 3, 128;" ::: "memory");
+  else asm volatile("bar.sync 4, 128;" ::: "memory");
 }
 
 // OR of a predicate over the 128 threads of a row group (every thread gets the result).
@@ -138,9 +140,23 @@ __device__ __forceinline__ bool group_or(int grp, bool v) {
         : "=r"(r)
         : "r"((uint32_t)v)
         : "memory");
-  else
+  else if (grp == 1)
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+  else if (grp == 2)
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 3, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 4, 128, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(r)
         : "r"((uint32_t)v)
@@ -152,12 +168,13 @@ __device__ __forceinline__ bool group_or(int grp, bool v) {
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // Per-CTA state of the tensor-core MLP: shared-memory tiles, TMEM base, one mbarrier and phase per
-// row group.  A CTA of 128 x G threads evaluates G groups of 128 rows (G = 1 or 2); group g has its
+// row group.  A CTA of 128 x G threads evaluates G groups of 128 rows (G = 1 .. 4); group g has its
 // own A tiles, accumulates in TMEM columns [64 g, 64 g + 64), and synchronises on its own named
 // barrier: the first thread of the group issues its MMAs and commits them to the group's mbarrier.
-// The groups run independently, so one group's FP64 transport overlaps the other's network wait.
-// The tensor-memory kernels run one CTA per SM, so two groups are how an SM gets eight warps.
-constexpr int kTcGroupsMax = 2;
+// The groups run independently, so one group's transport overlaps another's network wait.  The
+// tensor-memory kernels run one CTA per SM, so four groups are how an SM gets sixteen warps (at a
+// 128-register cap, which measured faster than eight warps at 255).
+constexpr int kTcGroupsMax = 4;
 struct TcMlp {
   unsigned char *a1[kTcGroupsMax], *a2[kTcGroupsMax], *a2l[kTcGroupsMax];   // per-group A tiles
   unsigned char *b1, *b2, *b2l, *b3, *b3l;                                  // shared weight tiles

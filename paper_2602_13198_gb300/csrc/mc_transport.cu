@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
 
 // Persistent in-grid push with the network.  Each 128-thread row group reaches its tensor-core
 // evaluation once per iteration (idle lanes contribute a zero row) and leaves the loop as a whole;
-// the CTA's two groups iterate independently and meet again only at the teardown.
+// the CTA's groups iterate independently and meet again only at the teardown.
 __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, PushIO io, SurrogateView sv) {
   extern __shared__ __align__(128) unsigned char smem_sur[];
   TcMlp T;
