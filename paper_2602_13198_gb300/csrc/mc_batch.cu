@@ -288,8 +288,8 @@ typedef void (*BatchKernel)(BatchIO);
 
 static BatchKernel pick_kernel(bool mixed, bool sur, int minb) {
   if (sur) return k_batch<true, true, 1>;   // tensor-memory kernels run one CTA per SM
-  if (mixed) return minb == 1 ? k_batch<true, false, 1> : k_batch<true, false, 3>;
-  return minb == 1 ? k_batch<false, false, 1> : k_batch<false, false, 3>;
+  if (mixed) return minb == 1 ? k_batch<true, false, 1> : minb == 3 ? k_batch<true, false, 3> : k_batch<true, false, 4>;
+  return minb == 1 ? k_batch<false, false, 1> : minb == 3 ? k_batch<false, false, 3> : k_batch<false, false, 4>;
 }
 
 }  // namespace mcgb
@@ -531,7 +531,7 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
     const double frac = std::min(1.0, std::max(0.05, 5e6 / ns_tot));
     for (int i = 0; i < n; ++i) ns_small[i] = std::max(1.0, frac * n_s[i]);
     double best = 1e300;
-    const int minbs[2] = {1, 3};
+    const int minbs[3] = {1, 3, 4};   // register caps 255, 168, 128
     for (int mb : minbs) {
       if (mb != 1 && c0->p.surrogate == 1) continue;   // one launch-bounds variant with the network
       int mx = max_ctas(c0, mb);

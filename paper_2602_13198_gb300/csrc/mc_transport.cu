@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
 // the grid, PHASE 1 while they are outside it.  A lane whose superphoton ends or changes phase is
 // refilled from the list (one atomic per warp).
 template <bool MIXED, int PHASE, bool KERR>
-__global__ void __launch_bounds__(128) k_push(DevModel m, PushIO io) {
+__global__ void __launch_bounds__(128, MIXED ? 4 : 1) k_push(DevModel m, PushIO io) {
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   PhT<GeoScalar<MIXED>> p;   // double-float geodesic in the mixed-precision form
