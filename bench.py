@@ -51,9 +51,9 @@ FLOP_EMIT = 2000.0
 FLOP_EVENT = 1500.0
 GEN_LAUNCHES = 7          # zone prep, weight partials, weight final, counts, 3 scan kernels
 # DRAM bytes (read + write) per superphoton of the first in-grid launch of a job, from one ncu capture
-# of k_push<in-grid> (FP64) at N_s = 1e6, tau_T = 1e-2 (225.1 MB for ~787k superphotons); traffic grows
+# of k_push_fp64<in-grid> at N_s = 1e6, tau_T = 1e-2 (224.9 MB for ~787k superphotons); traffic grows
 # in proportion to the superphotons a launch carries.  Must be re-taken whenever that kernel changes.
-TRAFFIC_B_PER_PH_FP64 = 286.2
+TRAFFIC_B_PER_PH_FP64 = 285.9
 
 
 def log(*a):
