@@ -87,7 +87,9 @@ typedef struct mc_model_params {
   int32_t k2_mode;     /* 0: exact K2(1/Theta_e); 1: K2 ~ 2 Theta_e^2 (section 2.2) */
   int32_t scatter;     /* 0: Compton scattering off */
   /* --- execution (not part of the physics) --- */
-  int32_t precision;   /* MC_PREC_FP64: everything FP64; MC_PREC_MIXED: FP64 geodesics, FP32 plasma coefficients */
+  int32_t precision;   /* MC_PREC_FP64: everything FP64; MC_PREC_MIXED: geodesics at FP64-level accuracy in
+                          double-float (FP32 pairs, 48-bit significand), plasma coefficients in FP32;
+                          emission, Compton kinematics, optical depths and weights stay FP64 */
   int32_t surrogate;   /* 0: closed forms and tables; 1: MLP surrogate for the coefficients (needs weights) */
   int32_t block;       /* threads per CTA of the transport kernel (0: default 128) */
   int32_t ctas_per_sm; /* resident CTAs per SM for the persistent launch (0: occupancy maximum) */

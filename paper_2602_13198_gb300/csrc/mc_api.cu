@@ -180,7 +180,7 @@ DevModel make_model(const mc_ctx *c) {
   m.fthetae_max = (float)m.thetae_max;
   m.fithetae_max = (float)m.ithetae_max;
   m.fthetae_min = (float)m.thetae_min;
-  m.feps_geo = (float)m.eps_geo;
+  m.deps_geo = df_const(m.eps_geo);
   m.fverlet_tol = (float)m.verlet_tol;
   m.hslope1 = m.hslope == 1.0;
   m.kappa_on = m.kappa > 0.0;

@@ -77,7 +77,8 @@ struct DevModel {
   const df *dtab;             // double-float function table (kDfTabN entries)
   float fidx1, fidx2, fidx3, fx2_0, fx3_0;   // FP32 grid constants for the double-float zone lookup
   // FP32 copies of model constants and tables read by the FP32 arithmetic (no FP64 conversions there)
-  float fNe_unit, fB_unit, fgam, fR_low, fR_high, fthetae_max, fithetae_max, fthetae_min, feps_geo, fverlet_tol;
+  float fNe_unit, fB_unit, fgam, fR_low, fR_high, fthetae_max, fithetae_max, fthetae_min, fverlet_tol;
+  df deps_geo;
   int hslope1, kappa_on;
   const float *lnK2f, *hotf;
   double kappa;           // > 0: kappa-distributed electrons for the synchrotron terms
@@ -194,20 +195,21 @@ __device__ __forceinline__ void sincos_small(double d, double &s, double &c) {
 // sin, cos of theta = pi (x2 + delta/pi) from a second sincospi in place of the series.
 template <bool DERIV, bool KERR = true, typename S = double>
 __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, GeoT<S> &G) {
-  const S a = KERR ? pick<S>(m.a, m.da) : cst<S>(0.0), M = pick<S>(m.mass, m.dmass), a2 = a * a;
+  constexpr S kZeroS = cst<S>(0.0), kPiS = cst<S>(kPI);   // compile-time constants (no conversions)
+  const S a = KERR ? pick<S>(m.a, m.da) : kZeroS, M = pick<S>(m.mass, m.dmass), a2 = a * a;
   S r, dth, d2th, s, c;
   if constexpr (std::is_same<S, df>::value) {
     r = df_exp(x1s, m.dtab);
     df sp, cp;
     df_sincospi(x2s, m.dtab, sp, cp);
     if (m.hslope1) {
-      dth = cst<S>(kPI);
-      d2th = cst<S>(0.0);
+      dth = kPiS;
+      d2th = kZeroS;
       s = sp;
       c = cp;
     } else {
       const df s2x = (sp * cp) * 2.0f, c2x = (cp - sp) * (cp + sp);   // sin, cos of 2 pi x2
-      dth = m.dpi2hh * c2x + cst<S>(kPI);
+      dth = m.dpi2hh * c2x + kPiS;
       d2th = m.dd2th * s2x;
       df_sincospi(x2s + m.dhh_pi * s2x, m.dtab, s, c);
     }
@@ -243,7 +245,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
   S opf = 1.0f + f;
   // Kerr-Schild components (t, r, theta, phi)
   S Gtt = f - 1.0f, Gtr = f, Grr = opf, Ghh = sig;
-  S Gtp = KERR ? -a * f * s2 : cst<S>(0.0), Grp = KERR ? -a * s2 * opf : cst<S>(0.0);
+  S Gtp = KERR ? -a * f * s2 : kZeroS, Grp = KERR ? -a * s2 * opf : kZeroS;
   S Gpp = KERR ? s2 * (sig + a2 * s2 * opf) : s2 * sig;
   G.r = r;
   G.sth = s;
@@ -260,7 +262,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
   G.G00 = -opf;
   G.G01 = f * ir;
   G.G11 = (KERR ? r * r - 2.0f * M * r + a2 : r * r - 2.0f * M * r) * isig * ir * ir;
-  G.G13 = KERR ? a * isig * ir : cst<S>(0.0);
+  G.G13 = KERR ? a * isig * ir : kZeroS;
   G.G22 = isig * idth * idth;
   G.G33 = isig * is2;
   if (!DERIV) return;
@@ -268,7 +270,7 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
   S dfr = 2.0f * M * (sig - 2.0f * r * r) * isig * isig;
   if constexpr (!KERR) {
     // a = 0: f, g_tr, g_rr depend on r only; g_thth = r^2, g_phph = r^2 sin^2
-    const S zero = cst<S>(0.0);
+    const S zero = kZeroS;
     G.d100 = r * dfr;
     G.d101 = r * (r * dfr + Gtr);
     G.d103 = zero;
@@ -373,13 +375,14 @@ __device__ __forceinline__ S stepsize(const DevModel &m, const S X[4], const S K
   return m.eps_geo * x2n / den;
 }
 
-// Double-float step size: the same rule, evaluated in FP32 (a step length needs no more).
+// Double-float step size: the same rule in double-float, so that the steps land where the FP64
+// path's do (an FP32 step length would move every step end along the path by ~1e-7).
 template <>
 __device__ __forceinline__ df stepsize<df>(const DevModel &m, const df X[4], const df K[4]) {
-  const float x2 = to_f(X[2]);
-  const float x2n = fminf(fabsf(x2), fabsf(1.0f - x2));
-  const float den = (fabsf(K[1].hi) + fabsf(K[3].hi)) * x2n + fabsf(K[2].hi) + 1e-30f;
-  return df{m.feps_geo * x2n / den, 0.0f};
+  const df a = df_abs(X[2]), b = df_abs(1.0f - X[2]);
+  const df x2n = df_le(a, b) ? a : b;
+  const df den = ((df_abs(K[1]) + df_abs(K[3])) * x2n + df_abs(K[2])) + 1e-30f;
+  return (m.deps_geo * x2n) * df_rcp(den);
 }
 
 // ---------------------------------------------------------------- tables

@@ -237,3 +237,30 @@ def test_scattering_sphere_full_size_sampled():
     assert r["n"] >= 0.99 * len(uids)
     assert len(r["flips"]) <= 2
     assert r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9
+
+
+@pytest.mark.parametrize("kind,n_s,seed", [("ks_sphere", 1e5, 21), ("kerr_torus", 3e4, 22)])
+def test_mixed_precision_geodesics_match_fp64_oracle(kind, n_s, seed):
+    # Without scattering, a superphoton's positions and wavevectors depend on the geodesic alone, so
+    # the mixed form's double-float geodesic (48-bit significand, own e^x and sin/cos(pi x)) must
+    # follow the oracle's FP64 paths closely; an FP32 geodesic would be off by ~1e-5.  Weights carry
+    # the FP32 coefficients and are compared loosely.  The Kerr torus (a = 0.9375, h = 0.3)
+    # exercises the spin terms and the theta map.
+    if kind == "ks_sphere":
+        p, g = synth.sphere("ks")
+    else:
+        p, g = synth.torus(seed=7, a=0.9375, n1=96, n2=48, scatter=0)
+    assert not p["scatter"]
+    gm = gpu_model(p, g, precision="mixed")
+    om = oracle_model(p, g)
+    tot = om.prepare(n_s, seed)
+    rng = np.random.default_rng(seed)
+    uids = np.sort(rng.choice(tot, size=min(400, tot), replace=False))
+    lg, lo = gm.trace(n_s, seed, uids), om.run(uids=uids, log=True)["log"]
+    r = compare_logs(lg, lo)
+    assert r["n"] >= 0.99 * len(uids)
+    assert len(r["flips"]) <= max(2, 0.01 * r["n"]), len(r["flips"])
+    assert r["worst"]["X"] < 1e-8 and r["worst"]["K"] < 1e-8, r["worst"]
+    # weights of recorded superphotons (an absorbed one may end at an FP32 underflow to 0 on one side)
+    rec = compare_logs([x for x in lg if x["status"] == 1], [x for x in lo if x["status"] == 1])
+    assert rec["n"] > 0 and rec["worst"]["w"] < 1e-3, rec["worst"]
