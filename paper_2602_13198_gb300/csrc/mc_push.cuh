@@ -579,7 +579,8 @@ __device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S> &p, con
 template <typename S>
 struct SurCarry {
   S X0[4], K0[4];
-  double dl, r, cth, g00, g01, g03;
+  double dl;
+  int term;   // radius test at the step end: 1 recording sphere reached, 3 captured, 0 neither
   CoefA a;
 };
 
@@ -628,11 +629,8 @@ static __device__ void step_sur_a(const DevModel &m, PhT<S> &p, SurCarry<S> &sc,
   p.nsteps++;
   ls.steps++;
   sc.dl = to_d(dl);
-  sc.r = to_d(G.r);
-  sc.cth = to_d(G.cth);
-  sc.g00 = to_d(G.g00);
-  sc.g01 = to_d(G.g01);
-  sc.g03 = to_d(G.g03);
+  // only the radius tests cross the network evaluation (the metric is re-evaluated to record)
+  sc.term = at_record(m, G.r) ? 1 : (at_capture(m, G.r) ? 3 : 0);
   coefficients32_a(m, G, p.X, p.K, sc.a);
 }
 
@@ -675,18 +673,14 @@ static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, PhT<S> &p
   p.w = wn;
   p.ana = c.ana;
   p.ans = c.ans;
-  const double r = sc.r;
   int status = 0;
-  if (r >= m.r_record) {
-    Geo G;
-    G.g00 = sc.g00;
-    G.g01 = sc.g01;
-    G.g03 = sc.g03;
-    G.cth = sc.cth;
+  if (sc.term == 1) {
+    GeoT<S> G;
+    metric_eval<false>(m, p.X[1], p.X[2], G);
     record(m, io, G, p);
     status = 1;
     ls.rec++;
-  } else if (r <= m.r_capture) {
+  } else if (sc.term == 3) {
     status = 3;
     ls.capt++;
   } else if (!w_positive(p)) {
