@@ -148,7 +148,12 @@ def _torch_allocator():
 
 
 class Model:
-    """One model context: ``Model(params, device=0)`` then ``set_grid`` and ``run``."""
+    """One model context: ``Model(params, device=0)`` then ``set_grid`` and ``run``.
+
+    ``precision="fp64"`` runs every step in FP64.  ``precision="mixed"`` runs the geodesic in
+    double-float on the FP32 pipes (FP64-level accuracy) and the plasma coefficients in FP32
+    (see ``precision`` in include/mc.h); ``surrogate=True`` (mixed only) takes K2, sigma_h and
+    the emissivity shape from the tensor-core network."""
 
     def __init__(self, params: dict, device: int = 0, precision: str = "fp64", use_torch_allocator: bool = True,
                  block: int = 0, ctas_per_sm: int = 0, surrogate: bool = False):
