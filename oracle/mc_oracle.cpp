@@ -10,8 +10,11 @@
 // libstdc++/scipy Bessel functions, numerical Klein-Nishina integrals, geodesic
 // invariants (null condition, E, L, Carter Q), the Schwarzschild orbit equation,
 // sampler histograms against their densities, the thermal Thomson-limit energy gain,
-// and the analytic synchrotron sphere.  "parity unpinned" items are listed in the
-// design notes (GRMHD-like torus spectra have no independent reference).
+// and the analytic synchrotron sphere; for the later additions, the bremsstrahlung fits'
+// continuity and classical limit, the kappa tables against scipy quadratures and their thermal
+// limits, and the kappa sampler against its density.  No function is "parity unpinned".  One
+// composite result has no independent reference: the spectra of the GRMHD-like tori, built
+// from the pinned parts above.
 //
 // Build: g++ -O2 -std=c++17 -fopenmp -shared -fPIC mc_oracle.cpp -o libmc_oracle.so
 
