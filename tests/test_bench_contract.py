@@ -43,3 +43,22 @@ def test_reference_line_describes_its_own_cpu_run(reference_line):
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.gpu
+def test_device_line_carries_roofline_clocks_and_e2e():
+    from helpers import cuda_available
+    if not cuda_available():
+        pytest.skip("needs a CUDA device")
+    r = subprocess.run([sys.executable, "bench.py", "--steps", "1", "--warmup", "3", "--n-s", "1e5",
+                        "--no-cpu-baseline", "--no-survey"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")][-1])
+    assert d["value"] > 0 and d["unit"] == "superphotons/s" and d["gpu_launches"] > 0
+    rl = d["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in rl, k
+    assert rl["bound"] == "alu" and 0.0 < rl["frac"] < 1.5
+    assert set(("sm_mhz", "sm_max_mhz", "reasons")) <= set(d["clocks"])
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
