@@ -226,13 +226,19 @@ int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t
  *   counts: device int64[n1*n2*n3], written; start: device int64[n1*n2*n3], the exclusive scan
  *   (first uid of each zone), written; total: device int64[1], the job's primary count, written.
  *   All three are caller-owned device pointers; the call is asynchronous on `stream`.
- * Scratch lives in one static device array of fixed size (5.3 MiB) that every GPU loading the
- * library keeps until the process exits; grids above 131072 zones or weight tables above 512 nodes
- * are rejected with MC_ERR_SIZE.  The first call on a device looks up that array's device address
- * (once per device, with the device current); make that first call before any stream capture.
+ *   A zone state that turns non-finite (mc_run fails with MC_ERR_NAN_INPUT on it) makes *total
+ *   -1; counts and start are then meaningless.  The call itself cannot see this without waiting
+ *   for the GPU, so it still returns MC_OK: read *total after the stream's work is done.
+ * Scratch lives in one static device array of fixed size (8.3 MiB: eight per-zone arrays, the
+ * weight-table partial sums and the scan's block sums) that every GPU loading the library keeps
+ * until the process exits; grids above 131072 zones or weight tables above 512 nodes are rejected
+ * with MC_ERR_SIZE.  The first call on a device looks up that array's device address (once per
+ * device, with the device current) and keeps it for the life of the process (a cudaDeviceReset
+ * in between is not supported); make that first call before any stream capture.
  * All calls share the array and it keeps the last call's contents: calls whose work overlaps on
  * the GPU (different streams, or different contexts on the same device) race and must be ordered
- * by the caller.  The context's tables and grid are read, not modified.
+ * by the caller.  The context's tables, grid and per-zone arrays are read, not modified (the
+ * kappa and bremsstrahlung zone arrays are rebuilt in the scratch).
  * Errors: INVALID_ARG, STATE (no grid), SIZE, CUDA. */
 int mc_zone_counts_noalloc(mc_ctx *c, double n_s, uint64_t seed, int64_t *counts, int64_t *start, int64_t *total,
                            void *stream);
@@ -285,6 +291,15 @@ int mc_surrogate_infer(mc_ctx *c, const float *x, float *y, int64_t n, int tenso
 #define MC_BATCH_GRAPH 2
 int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint64_t *seeds, int flags, void *stream,
                  mc_run_stats *stats);
+
+/* Limit, in seconds, on each device-side wait of the grid barrier between the phases of a batched
+ * run led by c (ctxs[0] of mc_run_batch); default 120.  A wait that runs out raises an error bit on
+ * the device; every CTA then leaves the kernel at its next barrier, and mc_run_batch returns
+ * MC_ERR_TIMEOUT with the context still usable (the next call starts from reset counters).  The
+ * limit is part of a captured batch graph's key, so changing it re-captures.  Not in the paper: a
+ * guard of this library's persistent launch (section 3 launches one kernel per stage).
+ * Errors: INVALID_ARG (c NULL, or seconds outside [1e-9, 3600]). */
+int mc_set_wait_limit(mc_ctx *c, double seconds);
 
 /* Releases the context and all its device memory.  NULL is a no-op. */
 void mc_free(mc_ctx *c);

@@ -323,6 +323,7 @@ struct BatchState {
   DevModel *h_models = nullptr;
   const int64_t **h_totals = nullptr;
   int g_minb = 0, g_ctas = 0;
+  double g_wait = 0.0;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -457,7 +458,7 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
   b.ph = bs->ph;
   b.bar = bs->bar;
   if (sur) b.sv = surrogate_view(c0);
-  b.timeout_ns = 120e9;
+  b.timeout_ns = c0->wait_ns;
   BatchKernel kern = pick_kernel(mixed, sur, minb);
   const int smem = batch_smem_bytes(sur);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -569,7 +570,7 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
     std::vector<uint64_t> vep(n);
     for (int i = 0; i < n; ++i) vep[i] = ctxs[i]->grid_epoch;
     bool same = bs->gexec && bs->g_ns == vns && bs->g_seed == vseed && bs->g_ctx == vctx && bs->g_epoch == vep &&
-                bs->g_minb == minb && bs->g_ctas == ctas;
+                bs->g_minb == minb && bs->g_ctas == ctas && bs->g_wait == c0->wait_ns;
     if (!same) {
       if (bs->gexec) {
         cudaGraphExecDestroy(bs->gexec);
@@ -594,6 +595,7 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
         bs->g_epoch = vep;
         bs->g_minb = minb;
         bs->g_ctas = ctas;
+        bs->g_wait = c0->wait_ns;
       }
     }
     if (bs->gexec) {
@@ -650,5 +652,12 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
     stats->batch_ctas = ctas;
     stats->batch_graph = used_graph ? 1 : 0;
   }
+  return MC_OK;
+}
+
+extern "C" int mc_set_wait_limit(mc_ctx *c, double seconds) {
+  if (!c) return set_err(nullptr, MC_ERR_INVALID_ARG, "null context");
+  if (!(seconds >= 1e-9 && seconds <= 3600.0)) return set_err(c, MC_ERR_INVALID_ARG, "wait limit must be in [1e-9, 3600] s");
+  c->wait_ns = seconds * 1e9;
   return MC_OK;
 }

@@ -163,6 +163,7 @@ struct mc_ctx {
   bool sur_ready = false;
   // batched runs led by this context (mc_batch.cu)
   void *batch = nullptr;
+  double wait_ns = 120e9;   // limit on each device-side grid-barrier wait of a batch led by this context
 };
 
 // Tensor-core view of the context's trained network (mc_mlp.cu).

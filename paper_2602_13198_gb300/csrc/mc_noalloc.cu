@@ -19,13 +19,17 @@ constexpr int64_t kMaxZones = 131072;   // largest grid accepted: n1*n2*n3 <= 2^
 constexpr int kMaxNu = 512;             // largest weight table accepted
 constexpr int64_t kMaxChunks = (kMaxZones + 2047) / 2048;
 constexpr int64_t kMaxScanBlocks = (kMaxZones + 1023) / 1024 + 1;
-// layout (bytes, each region 256-aligned): 5 per-zone double arrays, partial sums, ln w, 1/w,
-// scan block sums, the non-finite flag
+// layout (bytes, each region 256-aligned): 8 per-zone double arrays (volume, emission prefactor,
+// ln nu_c, rejection bound, expected count, and the kappa ln w and bremsstrahlung q / nu_T, k T_e / h
+// that the zone preparation writes for those models), partial sums, ln w, 1/w, scan block sums, the
+// non-finite flag
+constexpr int kZoneArrays = 8;
 constexpr size_t kZoneBytes = (size_t)kMaxZones * 8;
 constexpr size_t kPartialBytes = (size_t)kMaxNu * kMaxChunks * 8;
 constexpr size_t kNuBytes = (size_t)kMaxNu * 8;
 constexpr size_t kScanBytes = ((size_t)kMaxScanBlocks * 8 + 255) / 256 * 256;
-constexpr size_t kScratchBytes = 5 * kZoneBytes + kPartialBytes + 2 * kNuBytes + kScanBytes + 256;
+constexpr size_t kScratchBytes = kZoneArrays * kZoneBytes + kPartialBytes + 2 * kNuBytes + kScanBytes + 256;
+static_assert(kScratchBytes == 8660480, "scratch size stated in mc.h (8.3 MiB)");
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -33,6 +37,12 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 void *g_addr[kMaxDevices] = {nullptr};
 std::mutex g_mu;
+
+// A zone state that the preparation flagged non-finite makes the job's total -1 (mc_run fails with
+// MC_ERR_NAN_INPUT on the same state), so the caller can tell without a host synchronisation here.
+__global__ void k_flag_total(const int *bad, int64_t *total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *bad) *total = -1;
+}
 
 }  // namespace
 
@@ -85,11 +95,15 @@ extern "C" int mc_zone_counts_noalloc(mc_ctx *c, double n_s, uint64_t seed, int6
   double *zlnuc = (double *)(p + 2 * kZoneBytes);
   double *zgmax = (double *)(p + 3 * kZoneBytes);
   double *znbar = (double *)(p + 4 * kZoneBytes);
-  double *partial = (double *)(p + 5 * kZoneBytes);
-  double *lnw = (double *)(p + 5 * kZoneBytes + kPartialBytes);
-  double *winv = (double *)(p + 5 * kZoneBytes + kPartialBytes + kNuBytes);
-  int64_t *bsum = (int64_t *)(p + 5 * kZoneBytes + kPartialBytes + 2 * kNuBytes);
-  int *bad = (int *)(p + 5 * kZoneBytes + kPartialBytes + 2 * kNuBytes + kScanBytes);
+  double *zlnw = (double *)(p + 5 * kZoneBytes);
+  double *zbq = (double *)(p + 6 * kZoneBytes);
+  double *zbnt = (double *)(p + 7 * kZoneBytes);
+  unsigned char *tail = p + kZoneArrays * kZoneBytes;
+  double *partial = (double *)tail;
+  double *lnw = (double *)(tail + kPartialBytes);
+  double *winv = (double *)(tail + kPartialBytes + kNuBytes);
+  int64_t *bsum = (int64_t *)(tail + kPartialBytes + 2 * kNuBytes);
+  int *bad = (int *)(tail + kPartialBytes + 2 * kNuBytes + kScanBytes);
   cudaStream_t st = (cudaStream_t)stream;
   int nchunks = (int)((c->nz + 2047) / 2048);
   DevModel m = make_model(c);
@@ -99,6 +113,11 @@ extern "C" int mc_zone_counts_noalloc(mc_ctx *c, double n_s, uint64_t seed, int6
   m.zgmax = zgmax;
   m.lnw = lnw;
   m.winv = winv;
+  // the zone preparation writes these per-zone arrays for kappa and bremsstrahlung models: they go
+  // to the scratch too, so the context's own arrays (and a run on them) are left alone
+  m.zlnw = zlnw;
+  m.zbq = zbq;
+  m.zbnt = zbnt;
   // the scratch keeps the previous call's contents: every array below is fully rewritten by its
   // kernel; only the non-finite flag must start at zero
   e = cudaMemsetAsync(bad, 0, sizeof(int), st);
@@ -107,6 +126,7 @@ extern "C" int mc_zone_counts_noalloc(mc_ctx *c, double n_s, uint64_t seed, int6
     launch_weights(m, zvol, zpref, zlnuc, partial, nchunks, n_s, c->p.w_min, lnw, winv, st);
     launch_counts(m, zvol, zpref, zlnuc, zgmax, znbar, counts, st);
     launch_scan(counts, start, bsum, c->nz, total, st);
+    k_flag_total<<<1, 32, 0, st>>>(bad, total);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -117,6 +117,8 @@ def lib():
         L.mc_run_batch.restype = C.c_int
         L.mc_zone_counts_noalloc.argtypes = [vp, C.c_double, u64, vp, vp, vp, vp]
         L.mc_zone_counts_noalloc.restype = C.c_int
+        L.mc_set_wait_limit.argtypes = [vp, C.c_double]
+        L.mc_set_wait_limit.restype = C.c_int
         fp = C.POINTER(C.c_float)
         L.mc_surrogate_train.argtypes = [vp, i64, i64, i64, C.c_double, u64, dp]
         L.mc_surrogate_set_weights.argtypes = [vp, fp]
@@ -257,6 +259,10 @@ class Model:
         out = np.zeros(self.nz, dtype=np.int64)
         self._check(lib().mc_get_zone_counts(self._h, out.ctypes.data_as(C.POINTER(C.c_int64)), self.nz))
         return out
+
+    def set_wait_limit(self, seconds: float):
+        """Limit on each grid-barrier wait of a batch this model leads (mc_set_wait_limit)."""
+        self._check(lib().mc_set_wait_limit(self._h, float(seconds)))
 
     def zone_counts_noalloc(self, n_s: float, seed: int, counts, start, total, stream=None):
         """Zone counts into caller-owned CUDA tensors (int64 [nz], [nz], [1]) with no device

@@ -119,3 +119,34 @@ def test_batch_mixes_electron_models(precision):
         s = m.spectrum_sums()
         assert np.array_equal(s[..., 2], rspec[..., 2])
         assert np.allclose(s[..., :2], rspec[..., :2], rtol=1e-11, atol=0)
+
+
+def test_batch_barrier_wait_limit_times_out_and_context_recovers():
+    # a 1 microsecond limit makes the first CTAs at the first grid barrier give up while every CTA is
+    # still present: the launch must end with MC_ERR_TIMEOUT, and the same contexts must then run the
+    # batch to the individual results once the default limit is back (direct launch and graph)
+    from paper_2602_13198_gb300 import mc
+    models = survey_models(3)
+    ns = [2e4, 1e4, 2e4]
+    seeds = [41, 42, 43]
+    ref = individual(models, ns, seeds, "fp64")
+    ctxs = []
+    for p, g in models:
+        m = mc.Model(p, precision="fp64")
+        m.set_grid(g)
+        ctxs.append(m)
+    with pytest.raises(mc.MCError) as e:
+        ctxs[0].set_wait_limit(0.0)
+    assert e.value.code == -1
+    for graph in (False, True):
+        ctxs[0].set_wait_limit(1e-6)
+        with pytest.raises(mc.MCError) as e:
+            mc.run_batch(ctxs, ns, seeds, autotune=False, graph=graph)
+        assert e.value.code == -4                  # MC_ERR_TIMEOUT
+        ctxs[0].set_wait_limit(120.0)
+        st = mc.run_batch(ctxs, ns, seeds, autotune=False, graph=graph)
+        assert st["n_emit"] == sum(r[0]["n_emit"] for r in ref)
+        for m, (rs, rspec) in zip(ctxs, ref):
+            s = m.spectrum_sums()
+            assert np.array_equal(s[..., 2], rspec[..., 2])
+            assert np.allclose(s[..., :2], rspec[..., :2], rtol=1e-11, atol=0)
