@@ -118,6 +118,8 @@ def lib():
         L.or_sample_mj.argtypes = [D, U64, U64, I64, PD]
         L.or_compton.argtypes = [D, D, U64, U64, I64, PD, PD]
         L.or_fluid.argtypes = [C.c_void_p, PD, PD]
+        L.or_fluid_from_prims.argtypes = [P(Params), PD, PD, PD]
+        L.or_tetrad.argtypes = [P(Params), PD, PD, C.c_int, PD]
         L.or_create.argtypes = [P(Params), P(Grid)]
         L.or_create.restype = C.c_void_p
         L.or_destroy.argtypes = [C.c_void_p]
@@ -221,6 +223,28 @@ def geodesic(cfg, X0, K0, r_in, r_out, max_steps=100000):
     its = C.c_int64(0)
     n = lib().or_geodesic(C.byref(p), _pd(X0), _pd(K0), r_in, r_out, max_steps, _pd(Xe), _pd(Ke), _pd(mn), C.byref(its))
     return {"X": Xe, "K": Ke, "nsteps": int(n), "max_null": float(mn[0]), "iters": int(its.value)}
+
+
+def fluid_from_prims(cfg, X, prim):
+    """Fluid state at X from the primitives (rho, u, B^1..3, U^1..3): dict with ne, thetae, B [G],
+    bsq, ucon, ucov, bcon, bcov."""
+    p = params_from(cfg)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    pr = np.ascontiguousarray(prim, dtype=np.float64)
+    out = np.empty(20)
+    lib().or_fluid_from_prims(C.byref(p), _pd(X), _pd(pr), _pd(out))
+    return {"ne": out[0], "thetae": out[1], "B": out[2], "bsq": out[3], "ucon": out[4:8].copy(),
+            "ucov": out[8:12].copy(), "bcon": out[12:16].copy(), "bcov": out[16:20].copy()}
+
+
+def tetrad(cfg, X, prim, kind):
+    """Plasma-frame tetrad e[a, mu] at X for the primitives: kind "emission" or "scatter"."""
+    p = params_from(cfg)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    pr = np.ascontiguousarray(prim, dtype=np.float64)
+    e = np.empty(16)
+    lib().or_tetrad(C.byref(p), _pd(X), _pd(pr), 0 if kind == "emission" else 1, _pd(e))
+    return e.reshape(4, 4)
 
 
 def jnu(cfg, nu, ne, thetae, B, costh):

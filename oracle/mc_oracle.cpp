@@ -12,9 +12,14 @@
 // sampler histograms against their densities, the thermal Thomson-limit energy gain,
 // and the analytic synchrotron sphere; for the later additions, the bremsstrahlung fits'
 // continuity and classical limit, the kappa tables against scipy quadratures and their thermal
-// limits, and the kappa sampler against its density.  No function is "parity unpinned".  One
-// composite result has no independent reference: the spectra of the GRMHD-like tori, built
-// from the pinned parts above.
+// limits, and the kappa sampler against its density.  The fluid state, the tetrads and the fluid
+// interpolation are pinned at random points of spinning tori (both signs of the spin): u.u = -1
+// and u's projection orthogonal to the normal observer equal to U^i; b^mu against an independent
+// linear solve of b.u = 0, b^i u^t - b^t u^i = B^i; Theta_e at the beta -> infinity, beta = 1 and
+// beta -> 0 points of the temperature model; e_a.e_b = eta_ab with e_0 = u and e_3 = b/|b|; and a
+// primitive field linear in (x1, x2, x3) reproduced exactly, clamped and periodic as read.  No
+// function is "parity unpinned".  One composite result has no independent reference: the spectra
+// of the GRMHD-like tori, built from the pinned parts above.
 //
 // Build: g++ -O2 -std=c++17 -fopenmp -shared -fPIC mc_oracle.cpp -o libmc_oracle.so
 
@@ -1714,6 +1719,36 @@ void or_fluid(void *h, const double *X, double *out) {
   fluid_at(M, X, g, F);
   out[0] = F.ne; out[1] = F.thetae; out[2] = F.B; out[3] = F.plasma ? 1.0 : 0.0;
   for (int m = 0; m < 4; ++m) { out[4 + m] = F.ucon[m]; out[8 + m] = F.bcon[m]; }
+}
+
+// Fluid state from primitives at a point (fluid_from_prims, sections 2.2 and 2.5), for the pins of
+// the fluid frame: out = ne, thetae, |B| [G], b^2, u^mu[4], u_mu[4], b^mu[4], b_mu[4] (20 doubles).
+void or_fluid_from_prims(const or_params *P, const double *X, const double *pr, double *out) {
+  double g[4][4];
+  gcov_at(*P, X, g);
+  Fluid F;
+  fluid_from_prims(*P, make_units(*P), pr, g, F);
+  out[0] = F.ne; out[1] = F.thetae; out[2] = F.B; out[3] = F.bsq;
+  for (int m = 0; m < 4; ++m) {
+    out[4 + m] = F.ucon[m];
+    out[8 + m] = F.ucov[m];
+    out[12 + m] = F.bcon[m];
+    out[16 + m] = F.bcov[m];
+  }
+}
+
+// Plasma-frame tetrad at a point with the given primitives (sections 2.1 and 2.7): kind 0 the
+// emission tetrad, 1 the scattering tetrad; e16[4 a + mu] = e_(a)^mu.
+void or_tetrad(const or_params *P, const double *X, const double *pr, int kind, double *e16) {
+  double g[4][4];
+  gcov_at(*P, X, g);
+  Fluid F;
+  fluid_from_prims(*P, make_units(*P), pr, g, F);
+  double e[4][4];
+  if (kind == 0) tetrad_emission(g, F, e);
+  else tetrad_scatter(g, F, e);
+  for (int a = 0; a < 4; ++a)
+    for (int m = 0; m < 4; ++m) e16[4 * a + m] = e[a][m];
 }
 
 void *or_create(const or_params *P, const or_grid *G) {
