@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 @pytest.fixture(scope="module")
 def reference_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                        "--grid", "36x16x16", "--n-s", "1e6"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
@@ -50,8 +51,9 @@ def test_device_line_carries_roofline_clocks_and_e2e():
     from helpers import cuda_available
     if not cuda_available():
         pytest.skip("needs a CUDA device")
-    r = subprocess.run([sys.executable, "bench.py", "--steps", "1", "--warmup", "3", "--n-s", "1e5",
-                        "--no-cpu-baseline", "--no-survey"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    r = subprocess.run([sys.executable, "bench.py", "--steps", "2", "--warmup", "3", "--n-s", "1e6", "--shards", "2",
+                        "--grid", "72x32x32", "--no-cpu-baseline", "--no-forms"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads([ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")][-1])
     assert d["value"] > 0 and d["unit"] == "superphotons/s" and d["gpu_launches"] > 0
