@@ -96,6 +96,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
                             TcMlp &T, LocalStats &ls) {
   const int lane = threadIdx.x & 31;
   PhT<GeoScalar<MIXED>> p;   // double-float geodesic in the mixed-precision form
+  p.raddr = nullptr;
   int64_t slot = -1;
   bool live = false, exhausted = (n_in == 0);
   SurCarry<GeoScalar<MIXED>> sc;
@@ -143,6 +144,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
           live = false;
         }
       }
+      flush_record(p);
     } else {
       if (!__any_sync(0xffffffffu, live)) break;
       if (live) {
@@ -162,6 +164,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
           live = false;
         }
       }
+      flush_record(p);
     }
   }
 }

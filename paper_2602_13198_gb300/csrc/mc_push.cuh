@@ -22,6 +22,8 @@ struct PhT {
   int nsteps;
   int model;   // index of the superphoton's model in a batched run (0 otherwise)
   double wthr;   // roulette threshold roulette_w * wb (set at load; read by the double-float kernels)
+  double *raddr; // spectrum bin of a record made in this loop iteration (NULL: none), flushed per warp
+  double rwe;    // its w E
 };
 using Ph = PhT<double>;
 // geodesic scalar of the transport kernels of each precision
@@ -266,8 +268,11 @@ __device__ __forceinline__ bool at_record(const DevModel &m, df r) { return df_g
 __device__ __forceinline__ bool at_capture(const DevModel &m, double r) { return r <= m.r_capture; }
 __device__ __forceinline__ bool at_capture(const DevModel &m, df r) { return df_le(r, m.dr_capture); }
 
+// Binning of a superphoton at the recording sphere (section 3): E_inf = -k_t, log-frequency bin x
+// inclination bin.  The sums are not added here: the bin and w E wait in the state until the warp's
+// flush_record, which adds each bin's share of the warp once.
 template <typename GS, typename S>
-static __device__ void record(const DevModel &m, const PushIO &io, const GeoT<GS> &G, const PhT<S> &p) {
+static __device__ void record(const DevModel &m, const PushIO &io, const GeoT<GS> &G, PhT<S> &p) {
   double E = -(to_d(G.g00) * to_d(p.K[0]) + to_d(G.g01) * to_d(p.K[1]) + to_d(G.g03) * to_d(p.K[3]));
   if (!(E > 0.0)) return;
   double nu = E * (kME * kCL * kCL / kHPL);
@@ -277,11 +282,35 @@ static __device__ void record(const DevModel &m, const PushIO &io, const GeoT<GS
   double thf = acos(fabs(to_d(G.cth)));
   int ii = (int)floor(thf / (0.5 * kPI) * m.n_incl);
   ii = min(max(ii, 0), m.n_incl - 1);
-  double we = p.w * E;
-  double *sp = m.spec + ((int64_t)ii * m.n_bins + ib) * 3;
-  atomicAdd(sp, we);
-  atomicAdd(sp + 1, we * we);
-  atomicAdd(sp + 2, 1.0);
+  p.raddr = m.spec + ((int64_t)ii * m.n_bins + ib) * 3;
+  p.rwe = p.w * E;
+}
+
+// Warp-aggregated spectrum accumulation.  All 32 lanes call it at a converged point of their
+// persistent loop (the loop's exit is warp-uniform); lanes whose superphoton was recorded in this
+// iteration and that hit the same bin (of the same model) add sum w E, sum (w E)^2 and the count
+// through their lowest lane, so a bin takes one set of FP64 atomics per warp and iteration.
+template <typename S>
+__device__ __forceinline__ void flush_record(PhT<S> &p) {
+  const unsigned pend = __ballot_sync(0xffffffffu, p.raddr != nullptr);
+  if (pend == 0u) return;
+  const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)p.raddr);
+  double s1 = 0.0, s2 = 0.0, n = 0.0;
+  for (unsigned rem = pend; rem; rem &= rem - 1u) {   // pend is the same on every lane
+    const int src = __ffs(rem) - 1;
+    const double v = __shfl_sync(0xffffffffu, p.rwe, src);
+    if ((peers >> src) & 1u) {
+      s1 += v;
+      s2 += v * v;
+      n += 1.0;
+    }
+  }
+  if (p.raddr && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+    atomicAdd(p.raddr, s1);
+    atomicAdd(p.raddr + 1, s2);
+    atomicAdd(p.raddr + 2, n);
+  }
+  p.raddr = nullptr;
 }
 
 template <typename S>
@@ -562,6 +591,7 @@ __device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S> &p) {
   p.nsteps = P.nsteps[i];
   p.model = P.model ? (int)P.model[i] : 0;
   p.wthr = 0.0;
+  p.raddr = nullptr;
 }
 
 // load for a transport kernel of model m: also the roulette threshold

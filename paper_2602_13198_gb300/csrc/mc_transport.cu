@@ -68,6 +68,7 @@ __device__ __forceinline__ void push_body(const DevModel &m, const PushIO &io) {
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   PhT<GeoScalar<MIXED>> p;   // double-float geodesic in the mixed-precision form
+  p.raddr = nullptr;
   int64_t slot = -1;
   bool live = false;
   bool exhausted = false;
@@ -109,6 +110,7 @@ __device__ __forceinline__ void push_body(const DevModel &m, const PushIO &io) {
         live = false;
       }
     }
+    flush_record(p);
   }
   flush_stats(ls, io.cnt);
 }
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, Pus
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   PhT<df> p;
+  p.raddr = nullptr;
   int64_t slot = -1;
   bool live = false;
   bool exhausted = false;
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, Pus
         live = false;
       }
     }
+    flush_record(p);
   }
   tc_teardown(T);
   flush_stats(ls, io.cnt);
