@@ -35,6 +35,45 @@ constexpr double kFLnK0 = -23.025850929940457, kFLnK1 = 18.420680743952367, kFSt
 // K2(1/Theta) table: ln K2 on ln Theta in [ln 0.01, ln 1e4], spacing 0.002
 constexpr double kK2LnT0 = -4.605170185988091, kK2LnT1 = 9.210340371976184, kK2Step = 0.002;
 
+// ---------------------------------------------------------------- FP64 work on the integer pipes
+// GB300's FP64 pipe (~1.7 lanes per SM per clock) bounds the FP64 transport kernels, and it also
+// executes FP64 compares, min/max and conversions.  Where the outcome is the same bit for bit, these
+// helpers do that work with integer instructions instead.
+//
+// Exact float -> double widening: a finite normal float's sign, exponent (re-biased by 1023 - 127)
+// and mantissa are re-packed as a double; zeros keep their sign; subnormal floats (below 1.2e-38)
+// take the conversion instruction.  The value is the conversion's (widening is exact).  Not for
+// infinities or NaNs (grid values are checked finite when the grid is set).
+__device__ __forceinline__ double widen_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t mag = u & 0x7fffffffu;
+  if (mag < 0x00800000u) return mag == 0u ? __hiloint2double((int)(u & 0x80000000u), 0) : (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(u << 29));
+}
+// Order key of a double: keys compare as signed 64-bit integers in the order of the values
+// (-0 < +0; not for NaN).  For non-negative values the key is the bit pattern itself.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+// a >= b, a <= b for doubles known to be non-negative (or b negative in dle_nn: then false)
+__device__ __forceinline__ bool dge_nn(double a, double b) { return __double_as_longlong(a) >= __double_as_longlong(b); }
+__device__ __forceinline__ bool dle_nn(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+// max(x, 0) for any non-NaN x (a negative x has a negative bit pattern), and min / max of
+// non-negative doubles
+__device__ __forceinline__ double dmax0(double x) {
+  const long long b = __double_as_longlong(x);
+  return __longlong_as_double(b > 0 ? b : 0);
+}
+__device__ __forceinline__ double dmin_nn(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x < y ? x : y);
+}
+__device__ __forceinline__ double dmax_nn(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+
 // ---------------------------------------------------------------- model view passed to kernels
 struct DevModel {
   // metric and units
@@ -370,7 +409,7 @@ __device__ __forceinline__ S stepsize(const DevModel &m, const S X[4], const S K
   // 1 / (1/d1 + 1/d2 + 1/d3) with d1 = eps/(|k1|+S), d2 = eps x2n/(|k2|+S), d3 = eps/(|k3|+S)
   // = eps x2n / ((|k1| + |k3|) x2n + |k2|): one division
   const double SMALL = 1e-40;
-  double x2n = fmin(fabs(X[2]), fabs(1.0 - X[2]));
+  double x2n = dmin_nn(fabs(X[2]), fabs(1.0 - X[2]));
   double den = ((fabs(K[1]) + SMALL) + (fabs(K[3]) + SMALL)) * x2n + (fabs(K[2]) + SMALL);
   return m.eps_geo * x2n / den;
 }
@@ -435,8 +474,8 @@ __device__ __forceinline__ double hot_lookup_ln(const DevModel &m, double lt, do
   constexpr double st = (kHotNT - 1) / (kHotLT1 - kHotLT0), se = (kHotNE - 1) / (kHotLE1 - kHotLE0);
   double ft = (lt - kHotLT0) * st;
   double fe = (le - kHotLE0) * se;
-  ft = fmin(fmax(ft, 0.0), (double)(kHotNT - 1));
-  fe = fmin(fmax(fe, 0.0), (double)(kHotNE - 1));
+  ft = dmin_nn(dmax0(ft), (double)(kHotNT - 1));
+  fe = dmin_nn(dmax0(fe), (double)(kHotNE - 1));
   int i = min((int)ft, kHotNT - 2), j = min((int)fe, kHotNE - 2);
   double a = ft - i, b = fe - j;
   const double *h = m.hot;
@@ -611,7 +650,8 @@ __device__ __forceinline__ float zone_coord(const DevModel &m, const df X[4], in
                 : d == 2 ? (to_f(X[2]) - m.fx2_0) * m.fidx2 - 0.5f : (to_f(X[3]) - m.fx3_0) * m.fidx3 - 0.5f;
 }
 __device__ __forceinline__ bool outside_radially(const DevModel &m, const double X[4]) {
-  return X[1] < m.x1_0 || X[1] > m.x1_hi;
+  const long long k = dkey(X[1]);
+  return k < dkey(m.x1_0) || k > dkey(m.x1_hi);
 }
 __device__ __forceinline__ bool outside_radially(const DevModel &m, const df X[4]) {
   return !(df_ge(X[1], m.dx1_0) && df_le(X[1], m.dx1_hi));
@@ -666,19 +706,24 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   T wk0 = (T)(1 - dk), wk1 = (T)dk;
 #pragma unroll
   for (int f = 0; f < 8; ++f) pr[f] = (T)0;
+  // FP32 fields into FP64 sums: widened on the integer pipes (the same values as the conversion)
+  auto wide = [](float v) -> T {
+    if constexpr (kF32) return v;
+    else return widen_exact(v);
+  };
   auto acc = [&](int64_t zb, T w) {
     if (rd32) {
       const float4 *p0 = reinterpret_cast<const float4 *>(p32 + (zb + k0) * 8);
       float4 a0 = __ldg(p0), a1 = __ldg(p0 + 1);
       T ww = w * wk0;
-      pr[0] += ww * (T)a0.x; pr[1] += ww * (T)a0.y; pr[2] += ww * (T)a0.z; pr[3] += ww * (T)a0.w;
-      pr[4] += ww * (T)a1.x; pr[5] += ww * (T)a1.y; pr[6] += ww * (T)a1.z; pr[7] += ww * (T)a1.w;
+      pr[0] += ww * wide(a0.x); pr[1] += ww * wide(a0.y); pr[2] += ww * wide(a0.z); pr[3] += ww * wide(a0.w);
+      pr[4] += ww * wide(a1.x); pr[5] += ww * wide(a1.y); pr[6] += ww * wide(a1.z); pr[7] += ww * wide(a1.w);
       if (m.n3 > 1) {
         const float4 *p1 = reinterpret_cast<const float4 *>(p32 + (zb + k1) * 8);
         float4 b0 = __ldg(p1), b1 = __ldg(p1 + 1);
         ww = w * wk1;
-        pr[0] += ww * (T)b0.x; pr[1] += ww * (T)b0.y; pr[2] += ww * (T)b0.z; pr[3] += ww * (T)b0.w;
-        pr[4] += ww * (T)b1.x; pr[5] += ww * (T)b1.y; pr[6] += ww * (T)b1.z; pr[7] += ww * (T)b1.w;
+        pr[0] += ww * wide(b0.x); pr[1] += ww * wide(b0.y); pr[2] += ww * wide(b0.z); pr[3] += ww * wide(b0.w);
+        pr[4] += ww * wide(b1.x); pr[5] += ww * wide(b1.y); pr[6] += ww * wide(b1.z); pr[7] += ww * wide(b1.w);
       }
     } else {
       const double2 *p0 = reinterpret_cast<const double2 *>(m.prim64 + (zb + k0) * 8);
@@ -742,21 +787,27 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<
   if (ucon_out) { ucon_out[0] = u0; ucon_out[1] = u1; ucon_out[2] = u2; ucon_out[3] = u3; }
   if (bcon_out) { bcon_out[0] = b0; bcon_out[1] = b1; bcon_out[2] = b2; bcon_out[3] = b3; }
   P.bsq = b0 * bc0 + b1 * bc1 + b2 * bc2 + b3 * bc3;
-  P.ne = (rho > (T)0) ? rho * mv<T>(m.Ne_unit, m.fNe_unit) : (T)0;
+  // sign tests of the FP64 instantiation on the bit patterns (x > 0 iff the pattern is positive)
+  auto pos = [](T x) -> bool {
+    if constexpr (kF64) return __double_as_longlong(x) > 0 && __double_as_longlong(x) < 0x7FF0000000000000LL;
+    else return x > (T)0;
+  };
+  const bool rho_pos = pos(rho), bsq_pos = pos(P.bsq);
+  P.ne = rho_pos ? rho * mv<T>(m.Ne_unit, m.fNe_unit) : (T)0;
   P.rb = (T)0;
   P.ith = (T)0;
   if (kF64) {
     // one reciprocal square root gives |b| (for B), 1/b^2 (for beta) and the 1/|b| of cos(theta_B)
-    const T rb = (P.bsq > (T)0) ? rsqrt(P.bsq) : (T)0;
+    const T rb = bsq_pos ? rsqrt(P.bsq) : (T)0;
     P.rb = rb;
     P.B = P.bsq * rb * mv<T>(m.B_unit, m.fB_unit);
   } else {
     P.B = sqrt(fmax(P.bsq, (T)0)) * mv<T>(m.B_unit, m.fB_unit);
   }
-  if (rho > (T)0 && uu > (T)0) {
+  if (rho_pos && pos(uu)) {
     // Theta_e = (m_p/m_e)(gam-1)(u/rho)/(1 + T_i/T_e), T_i/T_e = (R_high beta^2 + R_low)/(1 + beta^2)
     T num, den;
-    if (P.bsq > (T)0) {
+    if (bsq_pos) {
       T beta = kF64 ? (T)2 * uu * (mv<T>(m.gam, m.fgam) - (T)1) * P.rb * P.rb : (T)2 * uu * (mv<T>(m.gam, m.fgam) - (T)1) / P.bsq;
       T b2x = beta * beta;
       num = (T)(kMP / kME) * (mv<T>(m.gam, m.fgam) - (T)1) * uu * ((T)1 + b2x);
@@ -767,7 +818,14 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<
     }
     T th, ith = (T)0;
     const T nd = num * den;
-    if (kF64 && nd > (T)(kF64 ? 1e-300 : 1e-30) && nd < (T)(kF64 ? 1e300 : 1e30)) {
+    bool nd_mid;
+    if constexpr (kF64) {   // nd >= 0: 1e-300 < nd < 1e300 on the bit patterns
+      const long long bnd = __double_as_longlong(nd);
+      nd_mid = bnd > __double_as_longlong(1e-300) && bnd < __double_as_longlong(1e300);
+    } else {
+      nd_mid = false;
+    }
+    if (nd_mid) {
       // Theta_e and 1/Theta_e from one reciprocal
       const T inv = (T)1 / nd;
       th = num * (num * inv);
@@ -776,7 +834,10 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<
       th = num / den;
       if (kF64) ith = den / num;
     }
-    if (th > mv<T>(m.thetae_max, m.fthetae_max)) {
+    bool over;
+    if constexpr (kF64) over = __double_as_longlong(th) > __double_as_longlong(m.thetae_max);   // th >= 0
+    else over = th > m.fthetae_max;
+    if (over) {
       th = mv<T>(m.thetae_max, m.fthetae_max);
       ith = mv<T>(m.ithetae_max, m.fithetae_max);
     }
@@ -785,7 +846,7 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<
   } else {
     P.thetae = (T)0;
   }
-  P.on = P.ne > (T)0;
+  P.on = pos(P.ne);
 }
 
 // Invariant absorption nu alpha_nu (j/B_nu, section 2.5) and scattering nu n_e sigma_h (section 2.7).
@@ -803,21 +864,26 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
   c.thetae = P.thetae;
   if (!P.on) return;
   double eps = -(K[0] * P.ucov[0] + K[1] * P.ucov[1] + K[2] * P.ucov[2] + K[3] * P.ucov[3]);
-  if (!(eps > 0.0)) return;
+  {
+    const long long be = __double_as_longlong(eps);
+    if (!(be > 0 && be < 0x7FF0000000000000LL)) return;   // eps > 0 (and finite) on the bit pattern
+  }
   constexpr double kNuEps = kME * kCL * kCL / kHPL;   // nu / eps
   const double ieps = 1.0 / eps;
   double nu = eps * kNuEps;
-  double lt = log(fmax(P.thetae, 1e-300));
-  if (m.kappa > 0.0 && P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
+  double lt = log(dmax_nn(P.thetae, 1e-300));
+  // Theta_e >= Theta_min and a field (B > 0 implies b^2 > 0), as sign / order tests on bit patterns
+  const bool emits = dge_nn(P.thetae, m.thetae_min) && __double_as_longlong(P.B) > 0;
+  if (m.kappa_on && emits) {
     double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
     double cth = fmin(1.0, fmax(-1.0, kb * P.rb * ieps));
     double s2 = 1.0 - cth * cth;
     if (s2 > 0.0) c.ana = kappa_nu_alpha(m, P.ne, P.thetae, P.B, s2 * rsqrt(s2), nu);
-  } else if (P.thetae >= m.thetae_min && P.B > 0.0 && P.bsq > 0.0) {
+  } else if (emits) {
     double kb = K[0] * P.bcov[0] + K[1] * P.bcov[1] + K[2] * P.bcov[2] + K[3] * P.bcov[3];
     double cth = fmin(1.0, fmax(-1.0, kb * P.rb * ieps));
     double s2 = 1.0 - cth * cth;
-    if (s2 > 0.0) {
+    if (__double_as_longlong(s2) > 0) {   // s2 > 0 (s2 <= 1)
       constexpr double kNus = (2.0 / 9.0) * (kEE / (2.0 * kPI * kME * kCL));   // nu_s / (B Theta^2 sin)
       const double rs = rsqrt(s2);
       double nus = kNus * P.B * P.thetae * P.thetae * (s2 * rs);
@@ -826,7 +892,7 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
       // G(X) / K2 with one exponential: G = t^2 exp(-X^1/3), t = X^1/2 + 2^(11/12) X^1/6
       double x6 = pow_sixth(Xs);
       double x3 = x6 * x6;
-      if (x3 < 745.0) {   // beyond, exp(-X^1/3) underflows: no emission or absorption
+      if (!dge_nn(x3, 745.0)) {   // x3 < 745; beyond, exp(-X^1/3) underflows: no emission or absorption
         double t = x6 * x3 + 1.8877486253633870 * x6;
         double GoK = t * t * exp(-x3 - lnK2_of_ln(m, lt));
         // nu alpha_nu = nu j_nu / B_nu with j_nu = sqrt2 pi e^2 n_e nu_s G / (3 c K2) and
@@ -980,8 +1046,9 @@ __device__ __forceinline__ double bias_of(const DevModel &m, double thetae, int 
   if (m.bias_mode == 1) b = m.bias_p0 * (nsc + 1.0) * (nsc + 1.0);
   else if (m.bias_mode == 2) b = m.bias_p0 * thetae * thetae;
   else b = m.bias_p0;
-  const double b0 = fmax(1.0, fmin(b, m.bias_max));
-  return fmax(1.0, fmin(m.bias_scale * b0, m.bias_max));   // = b0 at scale 1
+  // min / max on bit patterns: exact for the non-negative operands, and a negative b gives 1 as before
+  const double b0 = dmax_nn(1.0, dmin_nn(b, m.bias_max));
+  return dmax_nn(1.0, dmin_nn(m.bias_scale * b0, m.bias_max));   // = b0 at scale 1
 }
 
 // ---------------------------------------------------------------- tetrads (sections 2.1, 2.7)

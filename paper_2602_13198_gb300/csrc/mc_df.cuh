@@ -121,7 +121,10 @@ __device__ __forceinline__ float vdiff(df a, df b) {
 }
 __device__ __forceinline__ double vmag(double a) { return fabs(a); }
 __device__ __forceinline__ float vmag(df a) { return fabsf(a.hi); }
-__device__ __forceinline__ bool below_tol(double a, double tol, float, double b) { return a < tol * b; }
+// a, b >= 0 (sums of magnitudes): compared as bit patterns, off the FP64 pipe
+__device__ __forceinline__ bool below_tol(double a, double tol, float, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(tol * b);
+}
 __device__ __forceinline__ bool below_tol(float a, double, float tolf, float b) { return a < tolf * b; }
 
 // Nearest integer of |x| < 2^22 with FP32 additions only: adding 1.5 * 2^23 leaves the integer in the

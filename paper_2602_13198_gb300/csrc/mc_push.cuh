@@ -21,7 +21,7 @@ struct PhT {
   uint32_t nev;
   int nsteps;
   int model;   // index of the superphoton's model in a batched run (0 otherwise)
-  double wthr;   // roulette threshold roulette_w * wb (set at load; read by the double-float kernels)
+  double wthr;   // roulette threshold roulette_w * wb (set at load; read by the transport kernels)
   double *raddr; // spectrum bin of a record made in this loop iteration (NULL: none), flushed per warp
   double rwe;    // its w E
 };
@@ -241,31 +241,31 @@ static __device__ void load_child(const DevModel &m, const ChildBuf &q, int64_t 
 
 template <typename S>
 __device__ __forceinline__ bool in_grid(const DevModel &m, const S X[4]) {
-  if constexpr (std::is_same<S, df>::value) return df_ge(X[1], m.dx1_0) && df_le(X[1], m.dx1_hi);
-  else return X[1] >= m.x1_0 && X[1] <= m.x1_hi;
+  if constexpr (std::is_same<S, df>::value) {
+    return df_ge(X[1], m.dx1_0) && df_le(X[1], m.dx1_hi);
+  } else {   // order keys of the doubles: the same test on the integer pipes
+    const long long k = dkey(X[1]);
+    return k >= dkey(m.x1_0) && k <= dkey(m.x1_hi);
+  }
 }
-// Weight tests of the termination logic.  The double-float transport compares the bit patterns of the
-// (non-negative) doubles as integers, which order them the same way, and so keeps FP64 instructions
-// out of its loop: w > 0 (NaN fails, as in FP64) and w < roulette_w * wb.
+// Weight tests of the termination logic, on the bit patterns of the (non-negative) doubles compared
+// as integers, which order them the same way, so that they take no FP64-pipe slot: w > 0 (NaN
+// fails, as in FP64) and w < roulette_w * wb (the threshold is formed once, at load).
 template <typename S>
 __device__ __forceinline__ bool w_positive(const PhT<S> &p) {
-  if constexpr (std::is_same<S, df>::value) {
-    const long long b = __double_as_longlong(p.w);
-    return b > 0 && b <= 0x7FF0000000000000LL;
-  } else {
-    return p.w > 0.0;
-  }
+  const long long b = __double_as_longlong(p.w);
+  return b > 0 && b <= 0x7FF0000000000000LL;
 }
 template <typename S>
 __device__ __forceinline__ bool w_roulette(const DevModel &m, const PhT<S> &p) {
-  if constexpr (std::is_same<S, df>::value) return __double_as_longlong(p.w) < __double_as_longlong(p.wthr);
-  else return p.w < m.roulette_w * p.wb;
+  return __double_as_longlong(p.w) < __double_as_longlong(p.wthr);
 }
 
-// termination radii (recording sphere, capture near the horizon) in the geodesic's scalar
-__device__ __forceinline__ bool at_record(const DevModel &m, double r) { return r >= m.r_record; }
+// termination radii (recording sphere, capture near the horizon) in the geodesic's scalar; r > 0,
+// so the FP64 tests compare bit patterns (a negative r_capture, the flat metric's, never captures)
+__device__ __forceinline__ bool at_record(const DevModel &m, double r) { return dge_nn(r, m.r_record); }
 __device__ __forceinline__ bool at_record(const DevModel &m, df r) { return df_ge(r, m.dr_record); }
-__device__ __forceinline__ bool at_capture(const DevModel &m, double r) { return r <= m.r_capture; }
+__device__ __forceinline__ bool at_capture(const DevModel &m, double r) { return dle_nn(r, m.r_capture); }
 __device__ __forceinline__ bool at_capture(const DevModel &m, df r) { return df_le(r, m.dr_capture); }
 
 // Binning of a superphoton at the recording sphere (section 3): E_inf = -k_t, log-frequency bin x
@@ -391,10 +391,10 @@ static __device__ bool step(const DevModel &m, const PushIO &io, PhT<S> &p, Loca
   double wn = w0 * (MIXED ? (double)expf((float)-tau_a) : exp(-tau_a));
   if (scat) {
     double tau_s = 0.5 * (p.ans + c.ans) * C * dld;
-    if (tau_s > 0.0) {
+    if (__double_as_longlong(tau_s) > 0) {   // tau_s > 0 (tau_s >= 0)
       double b = bias_of(m, c.thetae, p.nsc);
       double d = b * tau_s;
-      if (p.acc + d > p.x1t) {
+      if (__double_as_longlong(p.acc + d) > __double_as_longlong(p.x1t)) {   // both >= 0
         double f = (p.x1t - p.acc) / d;
         double Xe[4], Ke[4];
 #pragma unroll
