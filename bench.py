@@ -250,6 +250,23 @@ def fp64_roofline(st, spin, dim, fp64_peak, kernel, traffic_per_ph=None, hbm_pea
     return r
 
 
+def split_roofline(st, spin, fp64_peak, kernel, phase="in_grid"):
+    """Split form (FP64 geodesic, FP32 coefficients and weights) against the measured FP64 peak: achieved =
+    the FP64 geodesic operations of the in-grid phase / its duration (phase "batch": of every step over
+    the whole batched transport launch); the FP32 coefficient work rides on the FP32 pipes beside it."""
+    if phase == "in_grid":
+        ops = ops_geodesic_step(spin) * st["n_steps_grid"] + ops_pass(spin) * st["n_iters_grid"]
+        ach = ops / (st["grid_ms"] / 1e3)
+    else:
+        ops = ops_geodesic_step(spin) * st["n_steps"] + ops_pass(spin) * st["n_iters"]
+        ach = ops / (st["transport_ms"] / 1e3)
+    return {"bound": "alu", "kernel": kernel, "achieved": ach / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": ach / fp64_peak, "traffic": None,
+            "peak_source": "measured: project FP64 FMA-chain microbenchmark on this GPU (mc_fma_peak)",
+            "count": {"ops_per_in_grid_step_fp64": ops_geodesic_step(spin), "ops_per_predictor_pass": ops_pass(spin),
+                      "in_grid_steps": st["n_steps_grid"], "predictor_passes": st["n_iters_grid"]}}
+
+
 def df_roofline(st, spin, fp32_peak, fp64_peak, kernel, phase="in_grid"):
     """Double-float kernel against the measured FP32 peak.  achieved = FP64-equivalent geodesic
     operations x DF_FLOPS_PER_OP (an estimate); the ncu-measured FP32-pipe busy fraction sits beside it."""
@@ -330,10 +347,11 @@ def config_forms(name, p, g, jobs, spin, dim, dev, timer, flush, peaks, weights,
     out["plain_fp64"] = e
     if not mixed_forms:
         return out
-    for form, sur in (("mixed", False), ("mixed_surrogate", True)):
+    for form, prec, sur in (("mixed", "mixed", False), ("mixed_surrogate", "mixed", True), ("split", "split", False),
+                            ("split_surrogate", "split", True)):
         if sur and (weights is None or p.get("kappa", 0) or p.get("brems", 0)):
             continue
-        m = mc.Model(p, device=dev, precision="mixed", surrogate=sur)
+        m = mc.Model(p, device=dev, precision=prec, surrogate=sur)
         if sur:
             m.surrogate_weights(weights)
         m.set_grid(g)
@@ -343,8 +361,12 @@ def config_forms(name, p, g, jobs, spin, dim, dev, timer, flush, peaks, weights,
         torch.cuda.empty_cache()
         e = form_entry(st, ms, out["plain_fp64"]["value"])
         e["spectrum_error"] = error_block([(sums[s], sums0[s]) for s in sums])
-        e["roofline"] = df_roofline(st, spin, fp32_peak, fp64_peak,
-                                    "k_push_%s<in-grid, %s> (double-float geodesic)" % ("sur" if sur else "mixed", spin))
+        if prec == "split":
+            e["roofline"] = split_roofline(st, spin, fp64_peak, "k_push_%s<in-grid, %s> (FP64 geodesic, FP32 rest)"
+                                           % ("sur" if sur else "split", spin))
+        else:
+            e["roofline"] = df_roofline(st, spin, fp32_peak, fp64_peak,
+                                        "k_push_%s<in-grid, %s> (double-float geodesic)" % ("sur" if sur else "mixed", spin))
         if sur:
             tf = FLOP_SUR_EVAL * st["n_steps_grid"] / (st["grid_ms"] / 1e3) / 1e12
             e["surrogate"] = {"tensor_achieved_tflops": tf, "bf16_peak_tflops": bf16_peak,
@@ -379,10 +401,11 @@ def survey_forms(args, dev, timer, flush, peaks, weights):
     st0 = sum_stats(stats)
     out["emitting_models"] = sum(1 for s in stats if s["n_total"] > 0)
     out["plain_fp64"] = dict(form_entry(st0, ms), gpu_launches=launches)
-    for form, sur in (("batched_mixed", False), ("batched_mixed_surrogate", True)):
+    for form, prec, sur in (("batched_mixed", "mixed", False), ("batched_mixed_surrogate", "mixed", True),
+                            ("batched_split_surrogate", "split", True)):
         ctxs = []
         for (p, g, _) in specs:
-            m = mc.Model(p, device=dev, precision="mixed", surrogate=sur)
+            m = mc.Model(p, device=dev, precision=prec, surrogate=sur)
             if sur:
                 m.surrogate_weights(weights)
             m.set_grid(g)
@@ -396,8 +419,12 @@ def survey_forms(args, dev, timer, flush, peaks, weights):
         r["autotune"] = {"min_blocks_per_sm": st["batch_min_blocks"], "ctas": st["batch_ctas"],
                          "graph": bool(st["batch_graph"]), "tune_and_capture_s": t_setup}
         r["gpu_launches"] = 1 + GEN_LAUNCHES * len(specs) + 1
-        r["roofline"] = df_roofline(st, "kerr", fp32_peak, fp64_peak, "k_batch (whole batched transport, one cooperative "
-                                    "launch; Kerr count for every model)", phase="batch")
+        if prec == "split":
+            r["roofline"] = split_roofline(st, "kerr", fp64_peak, "k_batch (whole batched transport, one cooperative "
+                                           "launch, FP64 geodesic; Kerr count for every model)", phase="batch")
+        else:
+            r["roofline"] = df_roofline(st, "kerr", fp32_peak, fp64_peak, "k_batch (whole batched transport, one "
+                                        "cooperative launch; Kerr count for every model)", phase="batch")
         if sur:
             tf = FLOP_SUR_EVAL * st["n_steps_grid"] / (st["transport_ms"] / 1e3) / 1e12
             r["surrogate"] = {"tensor_achieved_tflops": tf, "bf16_peak_tflops": bf16_peak,

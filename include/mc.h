@@ -37,7 +37,7 @@ extern "C" {
 #define MC_ERR_STATE (-8)
 #define MC_ERR_CUDA (-9)
 
-enum { MC_PREC_FP64 = 0, MC_PREC_MIXED = 1 };
+enum { MC_PREC_FP64 = 0, MC_PREC_MIXED = 1, MC_PREC_SPLIT = 2 };
 enum { MC_DTYPE_F64 = 0, MC_DTYPE_F32 = 1 };
 enum { MC_LOC_HOST = 0, MC_LOC_DEVICE = 1 };
 enum { MC_BIAS_CONST = 0, MC_BIAS_GENERATION = 1, MC_BIAS_THETAE2 = 2 };
@@ -89,8 +89,13 @@ typedef struct mc_model_params {
   /* --- execution (not part of the physics) --- */
   int32_t precision;   /* MC_PREC_FP64: everything FP64; MC_PREC_MIXED: geodesics at FP64-level accuracy in
                           double-float (FP32 pairs, 48-bit significand), plasma coefficients in FP32;
-                          emission, Compton kinematics, optical depths and weights stay FP64 */
-  int32_t surrogate;   /* 0: closed forms and tables; 1: MLP surrogate for the coefficients (needs weights) */
+                          emission, Compton kinematics, optical depths and weights stay FP64;
+                          MC_PREC_SPLIT: geodesic and step size in FP64; plasma coefficients, optical
+                          depths, weights (carried relative to each superphoton's FP64 birth weight),
+                          the scattering decision and the Compton kinematics in FP32; emission
+                          sampling FP64 */
+  int32_t surrogate;   /* 0: closed forms and tables; 1: MLP surrogate for the coefficients (needs weights;
+                          MC_PREC_MIXED or MC_PREC_SPLIT) */
   int32_t block;       /* threads per CTA of the transport kernel (0: default 128) */
   int32_t ctas_per_sm; /* resident CTAs per SM for the persistent launch (0: occupancy maximum) */
   int32_t device;      /* CUDA device ordinal */

@@ -103,6 +103,7 @@ DevModel make_model(const mc_ctx *c) {
   m.B_unit = kCL * std::sqrt(4.0 * kPI * m.rho_unit);
   m.Ne_unit = m.rho_unit / (kMP + kME);
   m.Ccoef = kHPL * L / (kME * kCL * kCL);
+  m.fCcoef = (float)m.Ccoef;
   m.R_high = p.R_high;
   m.R_low = p.R_low;
   m.gam = p.gam;
@@ -121,6 +122,11 @@ DevModel make_model(const mc_ctx *c) {
   m.bias_p0 = p.bias_p0;
   m.bias_max = p.bias_max;
   m.bias_scale = 1.0;
+  m.fbias_scale = 1.0f;
+  m.fbias_p0 = (float)p.bias_p0;
+  m.fbias_max = (float)p.bias_max;   // beyond the FP32 range: +inf, no bound
+  m.froulette_w = (float)p.roulette_w;
+  m.froulette_p = (float)p.roulette_p;
   m.n_sc_max = p.n_sc_max;
   m.scatter = p.scatter;
   m.k2_mode = p.k2_mode;
@@ -228,9 +234,10 @@ static int check_params(const mc_model_params *p, std::string &why) {
   if (p->n_sc_max < 0 || p->n_sc_max > 1000) return bad("n_sc_max out of range");
   if (!(p->roulette_p > 0.0 && p->roulette_p <= 1.0) || !(p->roulette_w >= 0.0)) return bad("bad roulette");
   if (p->max_steps < 1 || p->max_steps > 2000000000LL) return bad("max_steps out of range");
-  if (p->precision != MC_PREC_FP64 && p->precision != MC_PREC_MIXED) return bad("unknown precision");
+  if (p->precision != MC_PREC_FP64 && p->precision != MC_PREC_MIXED && p->precision != MC_PREC_SPLIT)
+    return bad("unknown precision");
   if (p->surrogate != 0 && p->surrogate != 1) return bad("surrogate must be 0 or 1");
-  if (p->surrogate == 1 && p->precision != MC_PREC_MIXED) return bad("the surrogate runs in the mixed-precision form");
+  if (p->surrogate == 1 && p->precision == MC_PREC_FP64) return bad("the surrogate runs in the mixed or split form");
   if (p->block != 0 && (p->block < 32 || p->block > 128 || p->block % 32)) return bad("block must be 32..128, multiple of 32");
   if (!(p->thetae_min >= 0.0 && p->thetae_max > 0.0)) return bad("bad Theta_e bounds");
   if (!(p->gam > 1.0)) return bad("gam must exceed 1");
@@ -407,7 +414,7 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g) {
   }
   CU(cudaMemset(c->bad, 0, sizeof(int)));
   launch_grid_to_aos(src, c->prim_f32, c->prim, c->prim_f32, nz, c->bad, 0);
-  if (c->p.precision == MC_PREC_MIXED && !c->prim_f32) {
+  if (c->p.precision != MC_PREC_FP64 && !c->prim_f32) {
     // the FP32 coefficient path reads FP32 primitives directly (no per-step conversions)
     c->prim_x32 = (float *)dev_alloc(c, 4 * 8 * nz);
     if (!c->prim_x32) {
@@ -560,10 +567,10 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
   if (tune || (int)c->bscale.size() != n_gen) c->bscale.assign(n_gen, 1.0);
   const bool tuning = tune && c->p.bias_target > 0.0;
   const int block = c->p.block ? c->p.block : 128;
-  const int mixed = c->p.precision == MC_PREC_MIXED;
+  const int prec = c->p.precision;
   int occ[2];
   for (int ph = 0; ph < 2; ++ph) {
-    occ[ph] = std::max(1, push_max_blocks_per_sm(mixed, ph, block, m.a != 0.0 ? 1 : 0));
+    occ[ph] = std::max(1, push_max_blocks_per_sm(prec, ph, block, m.a != 0.0 ? 1 : 0));
     if (c->p.ctas_per_sm > 0) occ[ph] = std::min(occ[ph], (int)c->p.ctas_per_sm);
   }
   const bool use_sur = c->p.surrogate == 1;
@@ -576,7 +583,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
   int occ_sur = 1;
   if (use_sur) {
     sv = surrogate_view(c);
-    occ_sur = std::max(1, std::min(4, push_sur_max_blocks_per_sm(sur_block, sur_smem)));
+    occ_sur = std::max(1, std::min(4, push_sur_max_blocks_per_sm(prec, sur_block, sur_smem)));
     if (c->p.ctas_per_sm > 0) occ_sur = std::min(occ_sur, (int)c->p.ctas_per_sm);
     CU(cudaMemsetAsync(c->sur_err, 0, sizeof(unsigned int), st));
   }
@@ -606,6 +613,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
     while (n_items > 0) {
       if (n_items > c->qcap) return fail(c, MC_ERR_QUEUE_OVERFLOW, "generation larger than the superphoton pool");
       m.bias_scale = c->bscale[std::min(gen, n_gen - 1)];
+      m.fbias_scale = (float)m.bias_scale;
       iio.n_items = n_items;
       if (gen == 0) {
         iio.mode = uid_list_dev ? 1 : 0;
@@ -620,7 +628,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
       CU(cudaMemsetAsync(c->cnt + CNT_NEXT, 0, 2 * sizeof(unsigned long long), st));
       CU(cudaMemsetAsync(c->cnt + CNT_L0, 0, 2 * sizeof(unsigned long long), st));
       int grid_init = (int)std::min<int64_t>((int64_t)c->sms * 4, (n_items + block - 1) / block);
-      TIMED_LAUNCH(0, launch_init(m, iio, mixed, grid_init, block, st));
+      TIMED_LAUNCH(0, launch_init(m, iio, prec, grid_init, block, st));
       int64_t n_grid = (int64_t)c->cnt_host[CNT_L0], n_free = (int64_t)c->cnt_host[CNT_L1];
       while (n_grid > 0 || n_free > 0) {
         if (n_grid > 0) {
@@ -632,10 +640,10 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
           pio.out_counter = CNT_L1;   // continues after the n_free entries already listed
           if (use_sur) {
             int grid = (int)std::min<int64_t>((int64_t)c->sms * occ_sur, (n_grid + sur_block - 1) / sur_block);
-            TIMED_LAUNCH(1, launch_push_sur(m, pio, sv, grid, sur_smem, st));
+            TIMED_LAUNCH(1, launch_push_sur(m, pio, sv, prec, grid, sur_smem, st));
           } else {
             int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[0], (n_grid + block - 1) / block);
-            TIMED_LAUNCH(1, launch_push(m, pio, mixed, 0, grid, block, st));
+            TIMED_LAUNCH(1, launch_push(m, pio, prec, 0, grid, block, st));
           }
           if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
           n_free = (int64_t)c->cnt_host[CNT_L1];
@@ -651,7 +659,7 @@ static int transport(mc_ctx *c, int64_t u0, int64_t u1, const int64_t *uid_list_
           pio.list_out = c->list_grid;
           pio.out_counter = CNT_L0;
           int grid = (int)std::min<int64_t>((int64_t)c->sms * occ[1], (n_free + block - 1) / block);
-          TIMED_LAUNCH(2, launch_push(m, pio, mixed, 1, grid, block, st));
+          TIMED_LAUNCH(2, launch_push(m, pio, prec, 1, grid, block, st));
           if (c->cnt_host[CNT_ERR] & 1ull) return fail(c, MC_ERR_QUEUE_OVERFLOW, "scattered-superphoton queue overflow");
           n_grid = (int64_t)c->cnt_host[CNT_L0];
           n_free = 0;

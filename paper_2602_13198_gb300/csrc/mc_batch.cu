@@ -90,16 +90,16 @@ __device__ __forceinline__ unsigned long long vload(const unsigned long long *p)
 // Persistent loop of one phase over list_in[0, n_in); superphotons that change phase are appended
 // to list_out through out_cnt.  With the surrogate, the in-grid phase runs in lockstep per 128-thread
 // row group (the network's tile), each group on its own named barrier.
-template <bool MIXED, int PHASE, bool SUR>
+template <int PREC, int PHASE, bool SUR>
 __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &io, const int32_t *list_in,
                             int64_t n_in, unsigned long long *cursor, int32_t *list_out, unsigned long long *out_cnt,
                             TcMlp &T, LocalStats &ls) {
   const int lane = threadIdx.x & 31;
-  PhT<GeoScalar<MIXED>> p;   // double-float geodesic in the mixed-precision form
+  PhF<PREC> p;   // the precision form's geodesic and weight scalars
   p.raddr = nullptr;
   int64_t slot = -1;
   bool live = false, exhausted = (n_in == 0);
-  SurCarry<GeoScalar<MIXED>> sc;
+  SurCarry<typename Form<PREC>::S> sc;
   while (true) {
     if (!exhausted) {
       unsigned idle = __ballot_sync(0xffffffffu, !live);
@@ -115,7 +115,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
           if (k < (unsigned long long)n_in) {
             slot = list_in[k];
             load_ph(b.pool, slot, p);
-            p.wthr = sm[p.model].roulette_w * p.wb;
+            set_wthr(sm[p.model], p);
             live = true;
           }
         }
@@ -137,7 +137,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
       }
       tc_mlp_eval(T, in, out);
       if (live) {
-        live = step_sur_b(sm[p.model], io, p, sc, out, ls);
+        live = step_sur_b<PREC>(sm[p.model], io, p, sc, out, ls);
         if (live && !in_grid(sm[p.model], p.X)) {
           save_ph(b.pool, slot, p);
           list_out[atomicAdd(out_cnt, 1ull)] = (int32_t)slot;
@@ -151,10 +151,10 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
         const DevModel &m = sm[p.model];
         bool handoff;
         if (PHASE == 0) {
-          live = step<MIXED>(m, io, p, ls);
+          live = step<PREC>(m, io, p, ls);
           handoff = live && !in_grid(m, p.X);
         } else {
-          int r = step_free(m, io, p, ls);
+          int r = step_free<PREC>(m, io, p, ls);
           live = (r != 1);
           handoff = (r == 2);
         }
@@ -173,7 +173,7 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
 constexpr int kModelsSmem = (int)((sizeof(DevModel) * kMaxBatch + 127) / 128 * 128);
 static int batch_smem_bytes(bool sur) { return kModelsSmem + (sur ? tc_smem_bytes(kTcGroupsMax) : 0); }
 
-template <bool MIXED, bool SUR, int MINB>
+template <int PREC, bool SUR, int MINB>
 __global__ void __launch_bounds__(SUR ? 128 * kTcGroupsMax : 128, MINB) k_batch(BatchIO b) {
   __shared__ int64_t soff[kMaxBatch + 1];
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(SUR ? 128 * kTcGroupsMax : 128, MINB) k_batch(
             ls.emit++;
           } else {
             p.model = qin.model[idx];
-            load_child(sm[p.model], qin, idx, p, ls);
+            load_child<Form<PREC>::K32>(sm[p.model], qin, idx, p, ls);
           }
-          init_transport<MIXED>(sm[p.model], p);
+          init_transport<Form<PREC>::C32>(sm[p.model], p);
           save_ph(b.pool, idx, p);
           gp = in_grid(sm[p.model], p.X);
         }
@@ -253,10 +253,10 @@ __global__ void __launch_bounds__(SUR ? 128 * kTcGroupsMax : 128, MINB) k_batch(
     // ---- alternate in-grid and free-streaming phases until the generation is done
     while (true) {
       int64_t ng = (int64_t)vload(agrid + k);
-      batch_phase<MIXED, 0, SUR>(sm, b, io, b.list_grid, ng, cgrid + k, b.list_free, afree + k, T, ls);
+      batch_phase<PREC, 0, SUR>(sm, b, io, b.list_grid, ng, cgrid + k, b.list_free, afree + k, T, ls);
       if (!grid_sync(b)) { go = false; break; }
       int64_t nf = (int64_t)vload(afree + k);
-      batch_phase<MIXED, 1, SUR>(sm, b, io, b.list_free, nf, cfree + k, b.list_grid, agrid + k + 1, T, ls);
+      batch_phase<PREC, 1, SUR>(sm, b, io, b.list_free, nf, cfree + k, b.list_grid, agrid + k + 1, T, ls);
       if (!grid_sync(b)) { go = false; break; }
       ++k;
       if (k >= kMaxPhases - 1) {
@@ -289,10 +289,14 @@ __global__ void k_batch_offsets(const int64_t *const *totals, int n, int64_t *pr
 
 typedef void (*BatchKernel)(BatchIO);
 
-static BatchKernel pick_kernel(bool mixed, bool sur, int minb) {
-  if (sur) return k_batch<true, true, 1>;   // tensor-memory kernels run one CTA per SM
-  if (mixed) return minb == 1 ? k_batch<true, false, 1> : minb == 3 ? k_batch<true, false, 3> : k_batch<true, false, 4>;
-  return minb == 1 ? k_batch<false, false, 1> : minb == 3 ? k_batch<false, false, 3> : k_batch<false, false, 4>;
+// Launch-bounds variants per precision form: minimum resident CTAs per SM 1, 3 or 4 (register caps 255,
+// 168, 128); the tensor-memory kernels (surrogate) run one CTA per SM.  The split form is bound by the
+// FP64 pipe like the FP64 form; it keeps the 1 and 3 variants.
+static BatchKernel pick_kernel(int prec, bool sur, int minb) {
+  if (sur) return prec == 2 ? k_batch<2, true, 1> : k_batch<1, true, 1>;
+  if (prec == 1) return minb == 1 ? k_batch<1, false, 1> : minb == 3 ? k_batch<1, false, 3> : k_batch<1, false, 4>;
+  if (prec == 2) return minb == 1 ? k_batch<2, false, 1> : k_batch<2, false, 3>;
+  return minb == 1 ? k_batch<0, false, 1> : minb == 3 ? k_batch<0, false, 3> : k_batch<0, false, 4>;
 }
 
 }  // namespace mcgb
@@ -427,7 +431,8 @@ static void stage_descriptors(mc_ctx **ctxs, int n, const uint64_t *seeds, Batch
 static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const uint64_t *seeds, BatchState *bs,
                                  int minb, int ctas, cudaStream_t st, bool timed) {
   mc_ctx *c0 = ctxs[0];
-  const bool mixed = c0->p.precision == MC_PREC_MIXED, sur = c0->p.surrogate == 1;
+  const int prec = c0->p.precision;
+  const bool sur = c0->p.surrogate == 1;
   stage_descriptors(ctxs, n, seeds, bs);
   for (int i = 0; i < n; ++i) {
     cudaError_t e = (cudaError_t)generate_async(ctxs[i], n_s[i], seeds[i], st);
@@ -462,7 +467,7 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
   b.bar = bs->bar;
   if (sur) b.sv = surrogate_view(c0);
   b.timeout_ns = c0->wait_ns;
-  BatchKernel kern = pick_kernel(mixed, sur, minb);
+  BatchKernel kern = pick_kernel(prec, sur, minb);
   const int smem = batch_smem_bytes(sur);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // shared memory over L1: the descriptors take ~48 KB, a CTA with four network row groups ~163 KB more
@@ -475,8 +480,9 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
 }
 
 static int max_ctas(mc_ctx *c0, int minb) {
-  const bool mixed = c0->p.precision == MC_PREC_MIXED, sur = c0->p.surrogate == 1;
-  BatchKernel kern = pick_kernel(mixed, sur, minb);
+  const int prec = c0->p.precision;
+  const bool sur = c0->p.surrogate == 1;
+  BatchKernel kern = pick_kernel(prec, sur, minb);
   const int smem = batch_smem_bytes(sur);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -538,6 +544,7 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
     const int minbs[3] = {1, 3, 4};   // register caps 255, 168, 128
     for (int mb : minbs) {
       if (mb != 1 && c0->p.surrogate == 1) continue;   // one launch-bounds variant with the network
+      if (mb == 4 && c0->p.precision == MC_PREC_SPLIT) continue;   // the split form has the 1 and 3 variants
       int mx = max_ctas(c0, mb);
       for (int per = 1; per <= mx; ++per) {
         int ctas = per * c0->sms;

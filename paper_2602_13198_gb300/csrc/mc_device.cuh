@@ -119,6 +119,8 @@ struct DevModel {
   float fNe_unit, fB_unit, fgam, fR_low, fR_high, fthetae_max, fithetae_max, fthetae_min, fverlet_tol;
   df deps_geo;
   int hslope1, kappa_on;
+  // FP32 copies for the split precision form's weight arithmetic
+  float fCcoef, fbias_p0, fbias_max, fbias_scale, froulette_w, froulette_p;
   const float *lnK2f, *hotf;
   double kappa;           // > 0: kappa-distributed electrons for the synchrotron terms
   const double *kapJ, *kapA, *kapI;   // ln J, ln A, ln I on the kappa grid [kKapNX][kKapNW]
@@ -849,10 +851,13 @@ __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<
   P.on = pos(P.ne);
 }
 
-// Invariant absorption nu alpha_nu (j/B_nu, section 2.5) and scattering nu n_e sigma_h (section 2.7).
-struct Coef {
-  double ana, ans, thetae;
+// Invariant absorption nu alpha_nu (j/B_nu, section 2.5) and scattering nu n_e sigma_h (section 2.7), in
+// the scalar W of the superphoton's weight arithmetic (FP64, or FP32 in the split precision form).
+template <typename W>
+struct CoefT {
+  W ana, ans, thetae;
 };
+using Coef = CoefT<double>;
 
 __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, const double X[4], const double K[4],
                                                bool want_s, Coef &c) {
@@ -908,10 +913,10 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
 }
 
 // Mixed precision: the same quantities with FP32 plasma state and coefficient arithmetic.
-template <typename S>
+template <typename S, typename W = double>
 __device__ __forceinline__ void coefficients32(const DevModel &m, const GeoT<S> &G, const S X[4], const S K[4],
-                                               bool want_s, Coef &c) {
-  c.ana = c.ans = c.thetae = 0.0;
+                                               bool want_s, CoefT<W> &c) {
+  c.ana = c.ans = c.thetae = (W)0;
   float pr[8];
   if (!interp_prims<float>(m, X, pr)) return;
   Plasma<float> P;
@@ -944,25 +949,26 @@ __device__ __forceinline__ void coefficients32(const DevModel &m, const GeoT<S> 
       ana = pre * P.ne * nus9 / (nu9 * nu9) / K2_of_f(m, P.thetae) * Gs * em1;
     }
   }
-  c.ana = (double)ana;
+  c.ana = (W)ana;
   if (m.kappa_on) {
     // kappa population: its absorption integral (FP64 tables) in place of the thermal fit
-    c.ana = 0.0;
+    c.ana = (W)0;
     if (P.thetae >= m.fthetae_min && P.B > 0.0f && P.bsq > 0.0f) {
       double kb = to_d(K[0]) * P.bcov[0] + to_d(K[1]) * P.bcov[1] + to_d(K[2]) * P.bcov[2] + to_d(K[3]) * P.bcov[3];
       double cth = fmin(1.0, fmax(-1.0, kb / ((double)eps * sqrt((double)P.bsq))));
       double s2 = 1.0 - cth * cth;
-      if (s2 > 0.0) c.ana = kappa_nu_alpha(m, (double)P.ne, (double)P.thetae, (double)P.B, sqrt(s2), (double)nu9 * 1e9);
+      if (s2 > 0.0)
+        c.ana = (W)kappa_nu_alpha(m, (double)P.ne, (double)P.thetae, (double)P.B, sqrt(s2), (double)nu9 * 1e9);
     }
   }
   // bremsstrahlung absorption in FP64 (n_e^2 leaves the FP32 range in dense plasma)
-  if (m.brems) c.ana += brems_nu_alpha((double)P.ne, (double)P.thetae, (double)nu9 * 1e9);
+  if (m.brems) c.ana = (W)((double)c.ana + brems_nu_alpha((double)P.ne, (double)P.thetae, (double)nu9 * 1e9));
   if (want_s) {
     if (m.kappa_on) {
-      c.ans = (double)nu9 * 1e9 * (double)P.ne * kap_hot_lookup(m, (double)P.thetae, (double)eps);
+      c.ans = (W)((double)nu9 * 1e9 * (double)P.ne * kap_hot_lookup(m, (double)P.thetae, (double)eps));
     } else {
       float sh = hot_lookup_f(m, fmaxf(P.thetae, 1e-30f), eps);
-      c.ans = (double)(nu9 * P.ne * (sh * 1e9f));
+      c.ans = (W)(nu9 * P.ne * (sh * 1e9f));
     }
   }
 }
@@ -1023,20 +1029,21 @@ __device__ __forceinline__ void coefficients32_a(const DevModel &m, const GeoT<S
 }
 
 // Part B: K2 and sigma_h from the network outputs inside the trained domain (table otherwise).
+template <typename W = double>
 __device__ __forceinline__ void coefficients32_b(const DevModel &m, const CoefA &a, const float out[3], bool want_s,
-                                                 Coef &c) {
-  c.ana = c.ans = 0.0;
+                                                 CoefT<W> &c) {
+  c.ana = c.ans = (W)0;
   c.thetae = a.thetae;
   if (!a.on) return;
   const float th = a.thetae;
   if (a.emit) {
     float k2 = (th >= (float)kSurThetaK2Min && th <= 1e3f) ? 2.0f * th * th * __expf(out[1]) : K2_of_f(m, th);
-    c.ana = (double)(a.ana_k2 / k2);
+    c.ana = (W)(a.ana_k2 / k2);
   }
   if (want_s) {
     bool in_dom = th >= 1e-3f && th <= 1e3f && a.eps >= 1e-12f && a.eps <= 1e6f;
     float sh = in_dom ? (float)kSIGT * __expf(out[0]) : hot_lookup_f(m, fmaxf(th, 1e-30f), a.eps);
-    c.ans = (double)(a.nu9 * a.ne * (sh * 1e9f));
+    c.ans = (W)(a.nu9 * a.ne * (sh * 1e9f));
   }
 }
 
@@ -1049,6 +1056,17 @@ __device__ __forceinline__ double bias_of(const DevModel &m, double thetae, int 
   // min / max on bit patterns: exact for the non-negative operands, and a negative b gives 1 as before
   const double b0 = dmax_nn(1.0, dmin_nn(b, m.bias_max));
   return dmax_nn(1.0, dmin_nn(m.bias_scale * b0, m.bias_max));   // = b0 at scale 1
+}
+
+// FP32 form (split precision): the same rule on FP32 copies of the parameters (bias_max beyond the FP32
+// range becomes +inf, which bounds nothing, as before)
+__device__ __forceinline__ float bias_of_f(const DevModel &m, float thetae, int nsc) {
+  float b;
+  if (m.bias_mode == 1) b = m.fbias_p0 * (nsc + 1.0f) * (nsc + 1.0f);
+  else if (m.bias_mode == 2) b = m.fbias_p0 * thetae * thetae;
+  else b = m.fbias_p0;
+  const float b0 = fmaxf(1.0f, fminf(b, m.fbias_max));
+  return fmaxf(1.0f, fminf(m.fbias_scale * b0, m.fbias_max));
 }
 
 // ---------------------------------------------------------------- tetrads (sections 2.1, 2.7)
@@ -1136,10 +1154,33 @@ static __device__ void tetrad_scatter(const Geo &G, const double u[4], double e[
 }
 
 // ---------------------------------------------------------------- Compton kinematics (section 2.7)
-__device__ __forceinline__ double sigma_kn_ratio(double e) {
-  if (e < 1e-3) return 1.0 - 2.0 * e;
-  double e2 = e * e, o2 = 1.0 + 2.0 * e;
-  return 0.75 / e2 * (2.0 + e2 * (1.0 + e) / (o2 * o2) + (e2 - 2.0 * e - 2.0) / (2.0 * e) * log1p(2.0 * e));
+// The kinematics are written once for the real type R: double in the FP64 and double-float forms,
+// float in the split precision form.  Uniforms come from the same counter-based stream in both.
+__device__ __forceinline__ double r_log(double x) { return log(x); }
+__device__ __forceinline__ float r_log(float x) { return logf(x); }
+__device__ __forceinline__ double r_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float r_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float r_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double r_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float r_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double r_cospi(double x) { return cospi(x); }
+__device__ __forceinline__ float r_cospi(float x) { return cospif(x); }
+__device__ __forceinline__ void r_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ void r_sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
+template <typename R>
+__device__ __forceinline__ R rng_r(Rng &s, uint64_t seed) {
+  return (R)rng_u(s, seed);
+}
+
+template <typename R>
+__device__ __forceinline__ R sigma_kn_ratio(R e) {
+  if (e < (R)1e-3) return (R)1 - (R)2 * e;
+  R e2 = e * e, o2 = (R)1 + (R)2 * e;
+  return (R)0.75 / e2 *
+         ((R)2 + e2 * ((R)1 + e) / (o2 * o2) + (e2 - (R)2 * e - (R)2) / ((R)2 * e) * r_log1p((R)2 * e));
 }
 
 constexpr int kMaxTry = 10000;
@@ -1147,57 +1188,59 @@ constexpr int kMaxTry = 10000;
 // Maxwell-Juettner Lorentz factor: Sobol's method (Pozdnyakov, Sobol & Sunyaev 1983) for
 // Theta >= 0.25; below, rejection from the Gamma(3/2, 5/2, 7/2) mixture bounding
 // sqrt(t) (1+t) sqrt(t+2) e^{-t/Theta}, t = gamma - 1.
-static __device__ double sample_mj(double th, Rng &s, uint64_t seed) {
-  if (th >= 0.25) {
+template <typename R>
+static __device__ R sample_mj(R th, Rng &s, uint64_t seed) {
+  if (th >= (R)0.25) {
     for (int it = 0; it < kMaxTry; ++it) {
-      double u1 = rng_u(s, seed), u2 = rng_u(s, seed), u3 = rng_u(s, seed), u4 = rng_u(s, seed);
-      double p = -th * log(u1 * u2 * u3);
-      double eta = p - th * log(u4);
-      if (eta * eta - p * p > 1.0 || it == kMaxTry - 1) return sqrt(1.0 + p * p);
+      R u1 = rng_r<R>(s, seed), u2 = rng_r<R>(s, seed), u3 = rng_r<R>(s, seed), u4 = rng_r<R>(s, seed);
+      R p = -th * r_log(u1 * u2 * u3);
+      R eta = p - th * r_log(u4);
+      if (eta * eta - p * p > (R)1 || it == kMaxTry - 1) return r_sqrt((R)1 + p * p);
     }
   }
-  double c1 = 0.886226925452758 * pow(th, 1.5);
-  double c2 = 1.25 * 1.329340388179137 * pow(th, 2.5);
-  double c3 = 0.25 * 3.323350970447843 * pow(th, 3.5);
-  double ct = c1 + c2 + c3;
-  double t = 0.0;
+  R c1 = (R)0.886226925452758 * r_pow(th, (R)1.5);
+  R c2 = (R)(1.25 * 1.329340388179137) * r_pow(th, (R)2.5);
+  R c3 = (R)(0.25 * 3.323350970447843) * r_pow(th, (R)3.5);
+  R ct = c1 + c2 + c3;
+  R t = 0;
   for (int it = 0; it < kMaxTry; ++it) {
-    double uc = rng_u(s, seed) * ct;
+    R uc = rng_r<R>(s, seed) * ct;
     int k = (uc < c1) ? 1 : ((uc < c1 + c2) ? 2 : 3);
-    double prod = 1.0;
-    for (int i = 0; i < k; ++i) prod *= rng_u(s, seed);
-    double ua = rng_u(s, seed), ub = rng_u(s, seed);
-    double z = sqrt(-2.0 * log(ua)) * cospi(2.0 * ub);
-    t = th * (-log(prod) + 0.5 * z * z);
-    double acc = (1.0 + t) * sqrt(t + 2.0) / (1.4142135623730951 * (1.0 + 1.25 * t + 0.25 * t * t));
-    if (rng_u(s, seed) < acc) break;
+    R prod = 1;
+    for (int i = 0; i < k; ++i) prod *= rng_r<R>(s, seed);
+    R ua = rng_r<R>(s, seed), ub = rng_r<R>(s, seed);
+    R z = r_sqrt((R)-2 * r_log(ua)) * r_cospi((R)2 * ub);
+    t = th * (-r_log(prod) + (R)0.5 * z * z);
+    R acc = ((R)1 + t) * r_sqrt(t + (R)2) / ((R)1.4142135623730951 * ((R)1 + (R)1.25 * t + (R)0.25 * t * t));
+    if (rng_r<R>(s, seed) < acc) break;
   }
-  return 1.0 + t;
+  return (R)1 + t;
 }
 
 // Gamma(a) variate (Marsaglia & Tsang 2000), normals by Box-Muller from two uniforms; a < 1 through
 // Gamma(a + 1) U^(1/a), the Gamma(a + 1) drawn first.
-static __device__ double gamma_mt(double a, Rng &s, uint64_t seed) {
-  double boost = -1.0;
-  if (a < 1.0) {
-    boost = 1.0 / a;
-    a += 1.0;
+template <typename R>
+static __device__ R gamma_mt(R a, Rng &s, uint64_t seed) {
+  R boost = -1;
+  if (a < (R)1) {
+    boost = (R)1 / a;
+    a += (R)1;
   }
-  const double d = a - 1.0 / 3.0, c = rsqrt(9.0 * d);
-  double g = d;
+  const R d = a - (R)1 / (R)3, c = r_rsqrt((R)9 * d);
+  R g = d;
   for (int it = 0; it < kMaxTry; ++it) {
-    const double u1 = rng_u(s, seed), u2 = rng_u(s, seed);
-    const double x = sqrt(-2.0 * log(1.0 - u1)) * cospi(2.0 * u2);
-    double v = 1.0 + c * x;
-    if (v <= 0.0) continue;
+    const R u1 = rng_r<R>(s, seed), u2 = rng_r<R>(s, seed);
+    const R x = r_sqrt((R)-2 * r_log((R)1 - u1)) * r_cospi((R)2 * u2);
+    R v = (R)1 + c * x;
+    if (v <= (R)0) continue;
     v = v * v * v;
-    const double u = rng_u(s, seed);
-    if (u < 1.0 - 0.0331 * (x * x) * (x * x) || log(u) < 0.5 * x * x + d * (1.0 - v + log(v))) {
+    const R u = rng_r<R>(s, seed);
+    if (u < (R)1 - (R)0.0331 * (x * x) * (x * x) || r_log(u) < (R)0.5 * x * x + d * ((R)1 - v + r_log(v))) {
       g = d * v;
       break;
     }
   }
-  if (boost > 0.0) g *= pow(rng_u(s, seed), boost);
+  if (boost > (R)0) g *= r_pow(rng_r<R>(s, seed), boost);
   return g;
 }
 
@@ -1206,46 +1249,48 @@ static __device__ double gamma_mt(double a, Rng &s, uint64_t seed) {
 // u = kw G_a / G_(kappa+1-a): for w < 1 the envelope sqrt2 u^1/2 (1 + u)^2 (a = 3/2, 5/2, 7/2; acceptance
 // sqrt(1 + u/2) / (1 + u)), otherwise (1 + u)^2 (a = 1, 2, 3; acceptance sqrt(1 - (1 + u)^-2)).  Term masses
 // follow from B(a + 1, b - 1) / B(a, b) = a / (b - 1).
-static __device__ double sample_kappa(double kappa, double w, Rng &s, uint64_t seed, int &rejcap) {
-  const double kw = kappa * w;
-  const bool low = w < 1.0;
-  const double a1 = low ? 1.5 : 1.0, b1 = kappa + 1.0 - a1;
-  const double r2 = 2.0 * kw * a1 / (b1 - 1.0);
-  const double r3 = r2 * (0.5 * kw * (a1 + 1.0) / (b1 - 2.0));
-  const double tot = 1.0 + r2 + r3;
+template <typename R>
+static __device__ R sample_kappa(R kappa, R w, Rng &s, uint64_t seed, int &rejcap) {
+  const R kw = kappa * w;
+  const bool low = w < (R)1;
+  const R a1 = low ? (R)1.5 : (R)1, b1 = kappa + (R)1 - a1;
+  const R r2 = (R)2 * kw * a1 / (b1 - (R)1);
+  const R r3 = r2 * ((R)0.5 * kw * (a1 + (R)1) / (b1 - (R)2));
+  const R tot = (R)1 + r2 + r3;
   for (int it = 0; it < kMaxTry; ++it) {
-    const double uc = rng_u(s, seed) * tot;
-    const double a = a1 + (uc < 1.0 ? 0.0 : (uc < 1.0 + r2 ? 1.0 : 2.0));
-    const double ga = gamma_mt(a, s, seed);
-    const double gb = gamma_mt(kappa + 1.0 - a, s, seed);
-    const double u = kw * (ga / gb);
-    const double acc = low ? sqrt(1.0 + 0.5 * u) / (1.0 + u) : sqrt(1.0 - 1.0 / ((1.0 + u) * (1.0 + u)));
-    if (rng_u(s, seed) < acc) return 1.0 + u;
+    const R uc = rng_r<R>(s, seed) * tot;
+    const R a = a1 + (uc < (R)1 ? (R)0 : (uc < (R)1 + r2 ? (R)1 : (R)2));
+    const R ga = gamma_mt(a, s, seed);
+    const R gb = gamma_mt(kappa + (R)1 - a, s, seed);
+    const R u = kw * (ga / gb);
+    const R acc = low ? r_sqrt((R)1 + (R)0.5 * u) / ((R)1 + u) : r_sqrt((R)1 - (R)1 / (((R)1 + u) * ((R)1 + u)));
+    if (rng_r<R>(s, seed) < acc) return (R)1 + u;
   }
   rejcap++;
-  return 1.0 + kw;
+  return (R)1 + kw;
 }
 
-__device__ __forceinline__ void perp_basis(const double n[3], double e1[3], double e2[3]) {
-  double a0 = 1.0, a1 = 0.0;
-  if (fabs(n[0]) >= 0.6) { a0 = 0.0; a1 = 1.0; }
-  double d = a0 * n[0] + a1 * n[1];
+template <typename R>
+__device__ __forceinline__ void perp_basis(const R n[3], R e1[3], R e2[3]) {
+  R a0 = 1, a1 = 0;
+  if (fabs(n[0]) >= (R)0.6) { a0 = 0; a1 = 1; }
+  R d = a0 * n[0] + a1 * n[1];
   e1[0] = a0 - d * n[0];
   e1[1] = a1 - d * n[1];
   e1[2] = -d * n[2];
-  double il = 1.0 / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  R il = (R)1 / r_sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
   e1[0] *= il; e1[1] *= il; e1[2] *= il;
   e2[0] = n[1] * e1[2] - n[2] * e1[1];
   e2[1] = n[2] * e1[0] - n[0] * e1[2];
   e2[2] = n[0] * e1[1] - n[1] * e1[0];
 }
 
-__device__ __forceinline__ void boost3(double E, const double p[3], double beta, const double v[3], double &Eo,
-                                       double po[3]) {
-  double gam = 1.0 / sqrt(1.0 - beta * beta);
-  double pv = p[0] * v[0] + p[1] * v[1] + p[2] * v[2];
+template <typename R>
+__device__ __forceinline__ void boost3(R E, const R p[3], R beta, const R v[3], R &Eo, R po[3]) {
+  R gam = (R)1 / r_sqrt((R)1 - beta * beta);
+  R pv = p[0] * v[0] + p[1] * v[1] + p[2] * v[2];
   Eo = gam * (E - beta * pv);
-  double ppar = gam * (pv - beta * E);
+  R ppar = gam * (pv - beta * E);
   po[0] = p[0] + (ppar - pv) * v[0];
   po[1] = p[1] + (ppar - pv) * v[1];
   po[2] = p[2] + (ppar - pv) * v[2];
@@ -1254,56 +1299,57 @@ __device__ __forceinline__ void boost3(double E, const double p[3], double beta,
 // Scattered photon in the plasma frame for incoming energy eps along unit n; draws in the order
 // [gamma (MJ), mu_e, accept]*, phi_e, [cos, accept]*, phi.
 // kappa > 0: kappa-distributed electrons of temperature-like parameter w = th (kappa - 3) / kappa.
-static __device__ void compton_fluid(double kappa, double th, double eps, const double n[3], Rng &s, uint64_t seed,
-                                     double &eo, double dir[3], int &rejcap) {
-  double gam = 1.0, mue = 0.0, beta = 0.0;
+template <typename R>
+static __device__ void compton_fluid(R kappa, R th, R eps, const R n[3], Rng &s, uint64_t seed, R &eo, R dir[3],
+                                     int &rejcap) {
+  R gam = 1, mue = 0, beta = 0;
   int it;
   for (it = 0; it < kMaxTry; ++it) {
-    gam = kappa > 0.0 ? sample_kappa(kappa, th * (kappa - 3.0) / kappa, s, seed, rejcap) : sample_mj(th, s, seed);
-    mue = 2.0 * rng_u(s, seed) - 1.0;
-    beta = sqrt(1.0 - 1.0 / (gam * gam));
-    double om = 1.0 - beta * mue;
-    double acc = om * sigma_kn_ratio(eps * gam * om) * 0.5;
-    if (rng_u(s, seed) < acc) break;
+    gam = kappa > (R)0 ? sample_kappa(kappa, th * (kappa - (R)3) / kappa, s, seed, rejcap) : sample_mj(th, s, seed);
+    mue = (R)2 * rng_r<R>(s, seed) - (R)1;
+    beta = r_sqrt((R)1 - (R)1 / (gam * gam));
+    R om = (R)1 - beta * mue;
+    R acc = om * sigma_kn_ratio(eps * gam * om) * (R)0.5;
+    if (rng_r<R>(s, seed) < acc) break;
   }
   if (it == kMaxTry) rejcap++;
-  double phie = 2.0 * rng_u(s, seed);   // in units of pi
-  double e1[3], e2[3];
+  R phie = (R)2 * rng_r<R>(s, seed);   // in units of pi
+  R e1[3], e2[3];
   perp_basis(n, e1, e2);
-  double se = sqrt(fmax(0.0, 1.0 - mue * mue));
-  double sp, cp;
-  sincospi(phie, &sp, &cp);
-  double v[3];
+  R se = r_sqrt(fmax((R)0, (R)1 - mue * mue));
+  R sp, cp;
+  r_sincospi(phie, &sp, &cp);
+  R v[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) v[i] = mue * n[i] + se * (cp * e1[i] + sp * e2[i]);
-  double pin[3] = {eps * n[0], eps * n[1], eps * n[2]};
-  double ee, pe[3];
+  R pin[3] = {eps * n[0], eps * n[1], eps * n[2]};
+  R ee, pe[3];
   boost3(eps, pin, beta, v, ee, pe);
-  double il = 1.0 / sqrt(pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]);
-  double ne[3] = {pe[0] * il, pe[1] * il, pe[2] * il};
-  double ct = 1.0, ep = ee;
+  R il = (R)1 / r_sqrt(pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]);
+  R ne[3] = {pe[0] * il, pe[1] * il, pe[2] * il};
+  R ct = 1, ep = ee;
   for (it = 0; it < kMaxTry; ++it) {
-    ct = 2.0 * rng_u(s, seed) - 1.0;
-    ep = ee / (1.0 + ee * (1.0 - ct));
-    double P;
-    if (ee < 1e-4) {
-      P = 0.5 * (1.0 + ct * ct);
+    ct = (R)2 * rng_r<R>(s, seed) - (R)1;
+    ep = ee / ((R)1 + ee * ((R)1 - ct));
+    R P;
+    if (ee < (R)1e-4) {
+      P = (R)0.5 * ((R)1 + ct * ct);
     } else {
-      double r = ep / ee;
-      P = 0.5 * r * r * (r + 1.0 / r - (1.0 - ct * ct));
+      R r = ep / ee;
+      P = (R)0.5 * r * r * (r + (R)1 / r - ((R)1 - ct * ct));
     }
-    if (rng_u(s, seed) < P) break;
+    if (rng_r<R>(s, seed) < P) break;
   }
   if (it == kMaxTry) rejcap++;
-  double phi = 2.0 * rng_u(s, seed);
-  double f1[3], f2[3];
+  R phi = (R)2 * rng_r<R>(s, seed);
+  R f1[3], f2[3];
   perp_basis(ne, f1, f2);
-  double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-  sincospi(phi, &sp, &cp);
-  double pp[3];
+  R st = r_sqrt(fmax((R)0, (R)1 - ct * ct));
+  r_sincospi(phi, &sp, &cp);
+  R pp[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) pp[i] = ep * (ct * ne[i] + st * (cp * f1[i] + sp * f2[i]));
-  double Ef, pf[3];
+  R Ef, pf[3];
   boost3(ep, pp, -beta, v, Ef, pf);
   eo = Ef;
   dir[0] = pf[0];

@@ -95,13 +95,15 @@ void launch_to_f32(const double *src, float *dst, int n, cudaStream_t st);
 void launch_kappa_tables(double kappa, double *lnF, double *lnJ, double *lnA, double *lnI, double *lnH,
                          const double *gl_mu, cudaStream_t st);
 // transport (mc_transport.cu)
-int push_max_blocks_per_sm(int mixed, int phase, int block, int kerr);
-void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st);
+// prec: the precision form (MC_PREC_FP64, MC_PREC_MIXED or MC_PREC_SPLIT)
+int push_max_blocks_per_sm(int prec, int phase, int block, int kerr);
+void launch_init(const DevModel &m, const InitIO &io, int prec, int grid, int block, cudaStream_t st);
 // phase 0: superphotons inside the radial extent of the grid; 1: outside it
-void launch_push(const DevModel &m, const PushIO &io, int mixed, int phase, int grid, int block, cudaStream_t st);
-// in-grid push of the mixed form with the coefficient network (128 threads per CTA)
-int push_sur_max_blocks_per_sm(int block, int smem);
-void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &sv, int grid, int smem, cudaStream_t st);
+void launch_push(const DevModel &m, const PushIO &io, int prec, int phase, int grid, int block, cudaStream_t st);
+// in-grid push with the coefficient network (mixed or split form; 128-thread row groups)
+int push_sur_max_blocks_per_sm(int prec, int block, int smem);
+void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &sv, int prec, int grid, int smem,
+                     cudaStream_t st);
 
 }  // namespace mcgb
 

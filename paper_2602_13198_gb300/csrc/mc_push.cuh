@@ -10,38 +10,58 @@
 namespace mcgb {
 
 
-// Superphoton state; S is the geodesic scalar (double, or df in the mixed-precision transport
-// kernels, which convert at load and save: the pool holds FP64).
-template <typename S>
+// Precision forms of the transport.  S: the geodesic scalar; W: the weight, optical-depth and
+// coefficient scalar; C32: FP32 plasma coefficients; K32: FP32 Compton kinematics.
+//   0 plain FP64: every step in FP64;
+//   1 mixed: geodesic in double-float (FP64-level accuracy on the FP32 pipes), FP32 coefficients,
+//     FP64 weights and kinematics;
+//   2 split: FP64 geodesic and step size, FP32 coefficients, optical depths, weights (relative to the
+//     superphoton's FP64 birth weight), scattering decision and Compton kinematics.
+template <int PREC> struct Form;
+template <> struct Form<0> { using S = double; using W = double; static constexpr bool C32 = false, K32 = false; };
+template <> struct Form<1> { using S = df; using W = double; static constexpr bool C32 = true, K32 = false; };
+template <> struct Form<2> { using S = double; using W = float; static constexpr bool C32 = true, K32 = true; };
+
+// Superphoton state.  The pool between phases holds FP64 (absolute weights); a transport kernel
+// converts at load and save.  With W = float the weight is carried relative to the birth weight wb
+// (weights reach 1e45, beyond FP32; the relative weight stays within [1e-13, ~10]).
+template <typename S, typename W = double>
 struct PhT {
   S X[4], K[4], A[4];
-  double w, wb, ana, ans, acc, x1t;
+  W w, ana, ans, acc, x1t;
+  double wb;
   Rng s;
   int nsc;
   uint32_t nev;
   int nsteps;
-  int model;   // index of the superphoton's model in a batched run (0 otherwise)
-  double wthr;   // roulette threshold roulette_w * wb (set at load; read by the transport kernels)
+  int model;     // index of the superphoton's model in a batched run (0 otherwise)
+  W wthr;        // roulette threshold: roulette_w * wb (W = float: roulette_w, relative); set at load
   double *raddr; // spectrum bin of a record made in this loop iteration (NULL: none), flushed per warp
   double rwe;    // its w E
 };
 using Ph = PhT<double>;
-// geodesic scalar of the transport kernels of each precision
-template <bool MIXED>
-using GeoScalar = typename std::conditional<MIXED, df, double>::type;
+template <int PREC>
+using PhF = PhT<typename Form<PREC>::S, typename Form<PREC>::W>;
+
+// absolute weight of a superphoton state
+template <typename S, typename W>
+__device__ __forceinline__ double abs_w(const PhT<S, W> &p) {
+  if constexpr (std::is_same<W, float>::value) return (double)p.w * p.wb;
+  else return p.w;
+}
 
 struct LocalStats {
   unsigned long long emit, child, rec, abs, capt, maxst, steps, iters, nonconv, roul, rejcap, events, gsteps, giters;
 };
 
-template <bool MIXED, typename S>
+template <bool C32, typename S, typename W>
 __device__ __forceinline__ void coefs(const DevModel &m, const GeoT<S> &G, const S X[4], const S K[4], bool ws,
-                                      Coef &c) {
-  if constexpr (MIXED) coefficients32(m, G, X, K, ws, c);
+                                      CoefT<W> &c) {
+  if constexpr (C32) coefficients32(m, G, X, K, ws, c);
   else coefficients64(m, G, X, K, ws, c);
 }
 
-template <bool MIXED, bool KERR = true>
+template <bool C32, bool KERR = true>
 static __device__ void init_transport(const DevModel &m, Ph &p) {
   p.x1t = -log(rng_u(p.s, m.seed));
   p.acc = 0.0;
@@ -49,7 +69,7 @@ static __device__ void init_transport(const DevModel &m, Ph &p) {
   Geo G;
   metric_eval<true, KERR>(m, p.X[1], p.X[2], G);
   Coef c;
-  coefs<MIXED>(m, G, p.X, p.K, scat, c);
+  coefs<C32>(m, G, p.X, p.K, scat, c);
   p.ana = c.ana;
   p.ans = c.ans;
   accel<KERR>(G, p.K, p.A);
@@ -162,6 +182,73 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
 // the child's own stream (cid from its start).  Returns the child's wavevector and the stream
 // position after the draws.  Run when the child is loaded for the next generation, not inside the
 // push: the child's stream is its own, so the result is the same as at the event itself.
+// Scattering tetrad in FP32 from the FP64 metric at the point (split precision form).
+static __device__ void tetrad_scatter_f(const Geo &G, const float u[4], float e[4][4]) {
+  const float g00 = (float)G.g00, g01 = (float)G.g01, g03 = (float)G.g03, g11 = (float)G.g11, g13 = (float)G.g13,
+              g22 = (float)G.g22, g33 = (float)G.g33;
+  auto dotf = [&](const float a[4], const float b[4]) {
+    return a[0] * (g00 * b[0] + g01 * b[1] + g03 * b[3]) + a[1] * (g01 * b[0] + g11 * b[1] + g13 * b[3]) +
+           a[2] * (g22 * b[2]) + a[3] * (g03 * b[0] + g13 * b[1] + g33 * b[3]);
+  };
+#pragma unroll
+  for (int q = 0; q < 4; ++q) e[0][q] = u[q];
+  for (int k = 1; k < 4; ++k) {
+    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    t[k] = 1.0f;
+    const float d0 = dotf(t, e[0]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] += d0 * e[0][q];
+    for (int j = 1; j < k; ++j) {
+      const float d = dotf(t, e[j]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] -= d * e[j][q];
+    }
+    const float n2 = dotf(t, t);
+    const float in = n2 > 1e-30f ? rsqrtf(n2) : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[k][q] = t[q] * in;
+  }
+}
+
+// FP32 Compton kinematics (split precision form): the plasma frame, electron and Klein-Nishina draws
+// in FP32 from the same stream; the child's wavevector is null to FP32 rounding (~1e-7 relative),
+// far below the geodesic integrator's own drift of the null condition.
+static __device__ void child_kinematics_f(const DevModel &m, const double Xe[4], const double Ke[4], uint64_t cid,
+                                          double Kc[4], uint32_t &ctr, LocalStats &ls) {
+  Geo G;
+  metric_eval<false>(m, Xe[1], Xe[2], G);
+  double Xc[4] = {Xe[0], fmin(fmax(Xe[1], m.x1_0), m.x1_hi), Xe[2], Xe[3]};
+  float pr[8];
+  interp_prims<float>(m, Xc, pr);
+  Plasma<float> P;
+  float ucon[4];
+  plasma_from_prims<float>(m, G, pr, P, ucon, nullptr);
+  float e[4][4];
+  tetrad_scatter_f(G, ucon, e);
+  const float k0 = (float)Ke[0], k1 = (float)Ke[1], k2 = (float)Ke[2], k3 = (float)Ke[3];
+  const float kc[4] = {(float)G.g00 * k0 + (float)G.g01 * k1 + (float)G.g03 * k3,
+                       (float)G.g01 * k0 + (float)G.g11 * k1 + (float)G.g13 * k3, (float)G.g22 * k2,
+                       (float)G.g03 * k0 + (float)G.g13 * k1 + (float)G.g33 * k3};
+  float kf[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float d = e[a][0] * kc[0] + e[a][1] * kc[1] + e[a][2] * kc[2] + e[a][3] * kc[3];
+    kf[a] = (a == 0) ? -d : d;
+  }
+  const float eps = kf[0];
+  const float il = rsqrtf(kf[1] * kf[1] + kf[2] * kf[2] + kf[3] * kf[3]);
+  const float n[3] = {kf[1] * il, kf[2] * il, kf[3] * il};
+  Rng s;
+  rng_init(s, cid, 0u);
+  float eo, dir[3];
+  int rej = 0;
+  compton_fluid<float>(m.kappa_on ? (float)m.kappa : 0.0f, fmaxf(P.thetae, 1e-8f), eps, n, s, m.seed, eo, dir, rej);
+  ls.rejcap += rej;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Kc[q] = (double)(eo * e[0][q] + dir[0] * e[1][q] + dir[1] * e[2][q] + dir[2] * e[3][q]);
+  ctr = s.n;
+}
+
 static __device__ void child_kinematics(const DevModel &m, const double Xe[4], const double Ke[4], uint64_t cid,
                                         double Kc[4], uint32_t &ctr, LocalStats &ls) {
   Geo G;
@@ -218,7 +305,8 @@ static __device__ void scatter_child(const PushIO &io, const double Xe[4], const
   if (io.out.model) io.out.model[slot] = (int16_t)model;
 }
 
-// Loads child idx of a queue into p, running its pending Compton kinematics.
+// Loads child idx of a queue into p, running its pending Compton kinematics (FP32 with K32).
+template <bool K32 = false>
 static __device__ void load_child(const DevModel &m, const ChildBuf &q, int64_t idx, Ph &p, LocalStats &ls) {
   double Ke[4];
 #pragma unroll
@@ -230,7 +318,8 @@ static __device__ void load_child(const DevModel &m, const ChildBuf &q, int64_t 
   const uint64_t id = q.id[idx];
   uint32_t ctr = q.ctr[idx];
   if (ctr == 0u) {
-    child_kinematics(m, p.X, Ke, id, p.K, ctr, ls);
+    if constexpr (K32) child_kinematics_f(m, p.X, Ke, id, p.K, ctr, ls);
+    else child_kinematics(m, p.X, Ke, id, p.K, ctr, ls);
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k) p.K[k] = Ke[k];
@@ -251,14 +340,35 @@ __device__ __forceinline__ bool in_grid(const DevModel &m, const S X[4]) {
 // Weight tests of the termination logic, on the bit patterns of the (non-negative) doubles compared
 // as integers, which order them the same way, so that they take no FP64-pipe slot: w > 0 (NaN
 // fails, as in FP64) and w < roulette_w * wb (the threshold is formed once, at load).
-template <typename S>
-__device__ __forceinline__ bool w_positive(const PhT<S> &p) {
-  const long long b = __double_as_longlong(p.w);
-  return b > 0 && b <= 0x7FF0000000000000LL;
+template <typename S, typename W>
+__device__ __forceinline__ bool w_positive(const PhT<S, W> &p) {
+  if constexpr (std::is_same<W, float>::value) {
+    return p.w > 0.0f;
+  } else {
+    const long long b = __double_as_longlong(p.w);
+    return b > 0 && b <= 0x7FF0000000000000LL;
+  }
 }
-template <typename S>
-__device__ __forceinline__ bool w_roulette(const DevModel &m, const PhT<S> &p) {
-  return __double_as_longlong(p.w) < __double_as_longlong(p.wthr);
+template <typename S, typename W>
+__device__ __forceinline__ bool w_roulette(const DevModel &m, const PhT<S, W> &p) {
+  if constexpr (std::is_same<W, float>::value) return p.w < p.wthr;
+  else return __double_as_longlong(p.w) < __double_as_longlong(p.wthr);
+}
+// Russian roulette survival draw (survival roulette_p, weight / roulette_p)
+template <typename S, typename W>
+__device__ __forceinline__ bool roulette_survives(const DevModel &m, PhT<S, W> &p) {
+  if constexpr (std::is_same<W, float>::value) {
+    if (rng_r<float>(p.s, m.seed) < m.froulette_p) {
+      p.w /= m.froulette_p;
+      return true;
+    }
+  } else {
+    if (rng_u(p.s, m.seed) < m.roulette_p) {
+      p.w /= m.roulette_p;
+      return true;
+    }
+  }
+  return false;
 }
 
 // termination radii (recording sphere, capture near the horizon) in the geodesic's scalar; r > 0,
@@ -271,8 +381,8 @@ __device__ __forceinline__ bool at_capture(const DevModel &m, df r) { return df_
 // Binning of a superphoton at the recording sphere (section 3): E_inf = -k_t, log-frequency bin x
 // inclination bin.  The sums are not added here: the bin and w E wait in the state until the warp's
 // flush_record, which adds each bin's share of the warp once.
-template <typename GS, typename S>
-static __device__ void record(const DevModel &m, const PushIO &io, const GeoT<GS> &G, PhT<S> &p) {
+template <typename GS, typename S, typename W>
+static __device__ void record(const DevModel &m, const PushIO &io, const GeoT<GS> &G, PhT<S, W> &p) {
   double E = -(to_d(G.g00) * to_d(p.K[0]) + to_d(G.g01) * to_d(p.K[1]) + to_d(G.g03) * to_d(p.K[3]));
   if (!(E > 0.0)) return;
   double nu = E * (kME * kCL * kCL / kHPL);
@@ -283,15 +393,15 @@ static __device__ void record(const DevModel &m, const PushIO &io, const GeoT<GS
   int ii = (int)floor(thf / (0.5 * kPI) * m.n_incl);
   ii = min(max(ii, 0), m.n_incl - 1);
   p.raddr = m.spec + ((int64_t)ii * m.n_bins + ib) * 3;
-  p.rwe = p.w * E;
+  p.rwe = abs_w(p) * E;
 }
 
 // Warp-aggregated spectrum accumulation.  All 32 lanes call it at a converged point of their
 // persistent loop (the loop's exit is warp-uniform); lanes whose superphoton was recorded in this
 // iteration and that hit the same bin (of the same model) add sum w E, sum (w E)^2 and the count
 // through their lowest lane, so a bin takes one set of FP64 atomics per warp and iteration.
-template <typename S>
-__device__ __forceinline__ void flush_record(PhT<S> &p) {
+template <typename S, typename W>
+__device__ __forceinline__ void flush_record(PhT<S, W> &p) {
   const unsigned pend = __ballot_sync(0xffffffffu, p.raddr != nullptr);
   if (pend == 0u) return;
   const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)p.raddr);
@@ -313,8 +423,8 @@ __device__ __forceinline__ void flush_record(PhT<S> &p) {
   p.raddr = nullptr;
 }
 
-template <typename S>
-static __device__ void write_log(const PushIO &io, const PhT<S> &p, int status) {
+template <typename S, typename W>
+static __device__ void write_log(const PushIO &io, const PhT<S, W> &p, int status) {
   if (!io.log) return;
   unsigned long long slot = atomicAdd(io.cnt + CNT_LOG, 1ull);
   if ((int64_t)slot >= io.log_cap) {
@@ -329,15 +439,128 @@ static __device__ void write_log(const PushIO &io, const PhT<S> &p, int status) 
     L.X[q] = to_d(p.X[q]);
     L.K[q] = to_d(p.K[q]);
   }
-  L.w = p.w;
+  L.w = abs_w(p);
   L.nsteps = p.nsteps;
   L.nev = (int32_t)p.nev;
   L.pad = 0;
 }
 
+// Absorption, biased scattering (event located by linear fraction within the step) and the weight
+// update of one in-grid step, in the weight scalar W of the precision form.  X0, K0: the step's start.
+template <typename S, typename W>
+__device__ __forceinline__ void absorb_scatter(const DevModel &m, const PushIO &io, PhT<S, W> &p, const S X0[4],
+                                               const S K0[4], double dld, const CoefT<W> &c, bool scat, bool f32att,
+                                               LocalStats &ls) {
+  if constexpr (std::is_same<W, float>::value) {
+    const float C = m.fCcoef, dl = (float)dld;
+    const float tau_a = 0.5f * (p.ana + c.ana) * C * dl;
+    const float w0 = p.w;
+    float wn = w0 * expf(-tau_a);
+    if (scat) {
+      const float tau_s = 0.5f * (p.ans + c.ans) * C * dl;
+      if (tau_s > 0.0f) {
+        const float b = bias_of_f(m, c.thetae, p.nsc);
+        const float d = b * tau_s;
+        if (p.acc + d > p.x1t) {
+          const float f = (p.x1t - p.acc) / d;
+          const double fd = f;
+          double Xe[4], Ke[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Xe[q] = to_d(X0[q]) + fd * (to_d(p.X[q]) - to_d(X0[q]));
+            Ke[q] = to_d(K0[q]) + fd * (to_d(p.K[q]) - to_d(K0[q]));
+          }
+          const float we = w0 * expf(-f * tau_a) / b;   // relative to the birth weight
+          uint64_t cid = child_id(p.s.id, p.nev);
+          scatter_child(io, Xe, Ke, (double)we * p.wb, cid, p.nsc + 1, p.model, ls);
+          p.nev++;
+          ls.events++;
+          wn *= 1.0f - 1.0f / b;
+          p.acc = 0.0f;
+          p.x1t = -logf(rng_r<float>(p.s, m.seed));
+        } else {
+          p.acc += d;
+        }
+      }
+    }
+    p.w = wn;
+  } else {
+    const double C = m.Ccoef;
+    double tau_a = 0.5 * (p.ana + c.ana) * C * dld;
+    double w0 = p.w;
+    // attenuation factor: FP32 in the mixed-precision form (its coefficients are FP32 already)
+    double wn = w0 * (f32att ? (double)expf((float)-tau_a) : exp(-tau_a));
+    if (scat) {
+      double tau_s = 0.5 * (p.ans + c.ans) * C * dld;
+      if (__double_as_longlong(tau_s) > 0) {   // tau_s > 0 (tau_s >= 0)
+        double b = bias_of(m, c.thetae, p.nsc);
+        double d = b * tau_s;
+        if (__double_as_longlong(p.acc + d) > __double_as_longlong(p.x1t)) {   // both >= 0
+          double f = (p.x1t - p.acc) / d;
+          double Xe[4], Ke[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Xe[q] = to_d(X0[q]) + f * (to_d(p.X[q]) - to_d(X0[q]));
+            Ke[q] = to_d(K0[q]) + f * (to_d(p.K[q]) - to_d(K0[q]));
+          }
+          double we = w0 * exp(-f * tau_a);
+          uint64_t cid = child_id(p.s.id, p.nev);
+          scatter_child(io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
+          p.nev++;
+          ls.events++;
+          wn *= (1.0 - 1.0 / b);
+          p.acc = 0.0;
+          p.x1t = -log(rng_u(p.s, m.seed));
+        } else {
+          p.acc += d;
+        }
+      }
+    }
+    p.w = wn;
+  }
+  p.ana = c.ana;
+  p.ans = c.ans;
+}
+
+// Termination tests after a step (recording at r >= r_record, capture, absorption, roulette, step
+// cap); returns the status (0: continue) and writes the log record of a finished superphoton.
+template <typename GS, typename S, typename W>
+__device__ __forceinline__ int terminate(const DevModel &m, const PushIO &io, const GeoT<GS> &G, PhT<S, W> &p,
+                                         int radius_term, LocalStats &ls) {
+  int status = 0;
+  if (radius_term == 1) {
+    record(m, io, G, p);
+    status = 1;
+    ls.rec++;
+  } else if (radius_term == 3) {
+    status = 3;
+    ls.capt++;
+  } else if (!w_positive(p)) {
+    status = 2;
+    ls.abs++;
+  } else {
+    if (w_roulette(m, p)) {
+      if (roulette_survives(m, p)) {
+        ls.roul++;
+      } else {
+        status = 2;
+        ls.abs++;
+      }
+    }
+    if (status == 0 && p.nsteps >= m.max_steps) {
+      status = 4;
+      ls.maxst++;
+    }
+  }
+  if (status) write_log(io, p, status);
+  return status;
+}
+
 // One geodesic step with absorption, scattering and the termination tests; false when finished.
-template <bool MIXED, bool KERR = true, typename S = double>
-static __device__ bool step(const DevModel &m, const PushIO &io, PhT<S> &p, LocalStats &ls) {
+template <int PREC, bool KERR = true>
+static __device__ bool step(const DevModel &m, const PushIO &io, PhF<PREC> &p, LocalStats &ls) {
+  using S = typename Form<PREC>::S;
+  using W = typename Form<PREC>::W;
   const bool scat = m.scatter && p.nsc < m.n_sc_max;
   S dl = stepsize(m, p.X, p.K);
   S X0[4], K0[4], Kp[4], An[4];
@@ -382,81 +605,20 @@ static __device__ bool step(const DevModel &m, const PushIO &io, PhT<S> &p, Loca
   if (!conv) ls.nonconv++;
   p.nsteps++;
   ls.steps++;
-  Coef c;
-  coefs<MIXED>(m, G, p.X, p.K, scat, c);
-  const double C = m.Ccoef, dld = to_d(dl);
-  double tau_a = 0.5 * (p.ana + c.ana) * C * dld;
-  double w0 = p.w;
-  // attenuation factor: FP32 in the mixed-precision form (its coefficients are FP32 already)
-  double wn = w0 * (MIXED ? (double)expf((float)-tau_a) : exp(-tau_a));
-  if (scat) {
-    double tau_s = 0.5 * (p.ans + c.ans) * C * dld;
-    if (__double_as_longlong(tau_s) > 0) {   // tau_s > 0 (tau_s >= 0)
-      double b = bias_of(m, c.thetae, p.nsc);
-      double d = b * tau_s;
-      if (__double_as_longlong(p.acc + d) > __double_as_longlong(p.x1t)) {   // both >= 0
-        double f = (p.x1t - p.acc) / d;
-        double Xe[4], Ke[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          Xe[q] = to_d(X0[q]) + f * (to_d(p.X[q]) - to_d(X0[q]));
-          Ke[q] = to_d(K0[q]) + f * (to_d(p.K[q]) - to_d(K0[q]));
-        }
-        double we = w0 * exp(-f * tau_a);
-        uint64_t cid = child_id(p.s.id, p.nev);
-        scatter_child(io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
-        p.nev++;
-        ls.events++;
-        wn *= (1.0 - 1.0 / b);
-        p.acc = 0.0;
-        p.x1t = -log(rng_u(p.s, m.seed));
-      } else {
-        p.acc += d;
-      }
-    }
-  }
-  p.w = wn;
-  p.ana = c.ana;
-  p.ans = c.ans;
-  int status = 0;
-  if (at_record(m, G.r)) {
-    record(m, io, G, p);
-    status = 1;
-    ls.rec++;
-  } else if (at_capture(m, G.r)) {
-    status = 3;
-    ls.capt++;
-  } else if (!w_positive(p)) {
-    status = 2;
-    ls.abs++;
-  } else {
-    if (w_roulette(m, p)) {
-      if (rng_u(p.s, m.seed) < m.roulette_p) {
-        p.w /= m.roulette_p;
-        ls.roul++;
-      } else {
-        status = 2;
-        ls.abs++;
-      }
-    }
-    if (status == 0 && p.nsteps >= m.max_steps) {
-      status = 4;
-      ls.maxst++;
-    }
-  }
-  if (status) {
-    write_log(io, p, status);
-    return false;
-  }
-  return true;
+  CoefT<W> c;
+  coefs<Form<PREC>::C32>(m, G, p.X, p.K, scat, c);
+  absorb_scatter(m, io, p, X0, K0, to_d(dl), c, scat, PREC == 1, ls);
+  const int rt = at_record(m, G.r) ? 1 : (at_capture(m, G.r) ? 3 : 0);
+  return terminate(m, io, G, p, rt, ls) == 0;
 }
 
 // Free-streaming step (both end points outside the grid: no plasma, so tau_a = tau_s = 0 and the
 // weight is unchanged): the same Verlet arithmetic and termination tests as step().  If the new
 // point lies inside the grid the step is discarded (state untouched) and 2 is returned, so the
 // in-grid phase redoes it with the coefficients.  Returns 0 to continue, 1 when finished.
-template <bool KERR = true, typename S = double>
-static __device__ int step_free(const DevModel &m, const PushIO &io, PhT<S> &p, LocalStats &ls) {
+template <int PREC, bool KERR = true>
+static __device__ int step_free(const DevModel &m, const PushIO &io, PhF<PREC> &p, LocalStats &ls) {
+  using S = typename Form<PREC>::S;
   S dl = stepsize(m, p.X, p.K);
   S Xn[4], Kp[4], An[4], Kn[4];
 #pragma unroll
@@ -497,39 +659,10 @@ static __device__ int step_free(const DevModel &m, const PushIO &io, PhT<S> &p, 
   if (!conv) ls.nonconv++;
   p.nsteps++;
   ls.steps++;
-  p.ana = 0.0;
-  p.ans = 0.0;
-  int status = 0;
-  if (at_record(m, G.r)) {
-    record(m, io, G, p);
-    status = 1;
-    ls.rec++;
-  } else if (at_capture(m, G.r)) {
-    status = 3;
-    ls.capt++;
-  } else if (!w_positive(p)) {
-    status = 2;
-    ls.abs++;
-  } else {
-    if (w_roulette(m, p)) {
-      if (rng_u(p.s, m.seed) < m.roulette_p) {
-        p.w /= m.roulette_p;
-        ls.roul++;
-      } else {
-        status = 2;
-        ls.abs++;
-      }
-    }
-    if (status == 0 && p.nsteps >= m.max_steps) {
-      status = 4;
-      ls.maxst++;
-    }
-  }
-  if (status) {
-    write_log(io, p, status);
-    return 1;
-  }
-  return 0;
+  p.ana = 0;
+  p.ans = 0;
+  const int rt = at_record(m, G.r) ? 1 : (at_capture(m, G.r) ? 3 : 0);
+  return terminate(m, io, G, p, rt, ls) ? 1 : 0;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -549,15 +682,15 @@ __device__ __forceinline__ void flush_stats(const LocalStats &ls, unsigned long 
   }
 }
 
-template <typename S>
-__device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const PhT<S> &p) {
+template <typename S, typename W>
+__device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const PhT<S, W> &p) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     P.X[q][i] = to_d(p.X[q]);
     P.K[q][i] = to_d(p.K[q]);
     P.A[q][i] = to_d(p.A[q]);
   }
-  P.w[i] = p.w;
+  P.w[i] = abs_w(p);
   P.wb[i] = p.wb;
   P.ana[i] = p.ana;
   P.ans[i] = p.ans;
@@ -571,34 +704,42 @@ __device__ __forceinline__ void save_ph(const Pool &P, int64_t i, const PhT<S> &
   if (P.model) P.model[i] = (int16_t)p.model;
 }
 
-template <typename S>
-__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S> &p) {
+template <typename S, typename W>
+__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S, W> &p) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     p.X[q] = from_d<S>(P.X[q][i]);
     p.K[q] = from_d<S>(P.K[q][i]);
     p.A[q] = from_d<S>(P.A[q][i]);
   }
-  p.w = P.w[i];
   p.wb = P.wb[i];
-  p.ana = P.ana[i];
-  p.ans = P.ans[i];
-  p.acc = P.acc[i];
-  p.x1t = P.x1t[i];
+  if constexpr (std::is_same<W, float>::value) p.w = (float)(P.w[i] / p.wb);
+  else p.w = P.w[i];
+  p.ana = (W)P.ana[i];
+  p.ans = (W)P.ans[i];
+  p.acc = (W)P.acc[i];
+  p.x1t = (W)P.x1t[i];
   rng_init(p.s, P.id[i], P.ctr[i]);
   p.nev = P.nev[i];
   p.nsc = P.nsc[i];
   p.nsteps = P.nsteps[i];
   p.model = P.model ? (int)P.model[i] : 0;
-  p.wthr = 0.0;
+  p.wthr = 0;
   p.raddr = nullptr;
 }
 
+// roulette threshold of model m: roulette_w * wb (relative weights: roulette_w)
+template <typename S, typename W>
+__device__ __forceinline__ void set_wthr(const DevModel &m, PhT<S, W> &p) {
+  if constexpr (std::is_same<W, float>::value) p.wthr = m.froulette_w;
+  else p.wthr = m.roulette_w * p.wb;
+}
+
 // load for a transport kernel of model m: also the roulette threshold
-template <typename S>
-__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S> &p, const DevModel &m) {
+template <typename S, typename W>
+__device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S, W> &p, const DevModel &m) {
   load_ph(P, i, p);
-  p.wthr = m.roulette_w * p.wb;
+  set_wthr(m, p);
 }
 
 // ---------------------------------------------------------------- surrogate in-grid push
@@ -614,8 +755,8 @@ struct SurCarry {
   CoefA a;
 };
 
-template <typename S>
-static __device__ void step_sur_a(const DevModel &m, PhT<S> &p, SurCarry<S> &sc, LocalStats &ls) {
+template <typename S, typename W>
+static __device__ void step_sur_a(const DevModel &m, PhT<S, W> &p, SurCarry<S> &sc, LocalStats &ls) {
   S dl = stepsize(m, p.X, p.K);
   S Kp[4], An[4], Kn[4];
 #pragma unroll
@@ -664,78 +805,21 @@ static __device__ void step_sur_a(const DevModel &m, PhT<S> &p, SurCarry<S> &sc,
   coefficients32_a(m, G, p.X, p.K, sc.a);
 }
 
-template <typename S>
-static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, PhT<S> &p, const SurCarry<S> &sc,
-                                  const float out[3], LocalStats &ls) {
+template <int PREC>
+static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, PhF<PREC> &p,
+                                  const SurCarry<typename Form<PREC>::S> &sc, const float out[3], LocalStats &ls) {
+  using W = typename Form<PREC>::W;
   const bool scat = m.scatter && p.nsc < m.n_sc_max;
-  Coef c;
+  CoefT<W> c;
   coefficients32_b(m, sc.a, out, scat, c);
-  const double C = m.Ccoef, dl = sc.dl;
-  double tau_a = 0.5 * (p.ana + c.ana) * C * dl;
-  double w0 = p.w;
-  double wn = w0 * (double)expf((float)-tau_a);   // FP32 attenuation, as in step<true>
-  if (scat) {
-    double tau_s = 0.5 * (p.ans + c.ans) * C * dl;
-    if (tau_s > 0.0) {
-      double b = bias_of(m, c.thetae, p.nsc);
-      double d = b * tau_s;
-      if (p.acc + d > p.x1t) {
-        double f = (p.x1t - p.acc) / d;
-        double Xe[4], Ke[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          Xe[q] = to_d(sc.X0[q]) + f * (to_d(p.X[q]) - to_d(sc.X0[q]));
-          Ke[q] = to_d(sc.K0[q]) + f * (to_d(p.K[q]) - to_d(sc.K0[q]));
-        }
-        double we = w0 * exp(-f * tau_a);
-        uint64_t cid = child_id(p.s.id, p.nev);
-        scatter_child(io, Xe, Ke, we / b, cid, p.nsc + 1, p.model, ls);
-        p.nev++;
-        ls.events++;
-        wn *= (1.0 - 1.0 / b);
-        p.acc = 0.0;
-        p.x1t = -log(rng_u(p.s, m.seed));
-      } else {
-        p.acc += d;
-      }
-    }
-  }
-  p.w = wn;
-  p.ana = c.ana;
-  p.ans = c.ans;
-  int status = 0;
+  absorb_scatter(m, io, p, sc.X0, sc.K0, sc.dl, c, scat, true, ls);
   if (sc.term == 1) {
-    GeoT<S> G;
+    GeoT<typename Form<PREC>::S> G;
     metric_eval<false>(m, p.X[1], p.X[2], G);
-    record(m, io, G, p);
-    status = 1;
-    ls.rec++;
-  } else if (sc.term == 3) {
-    status = 3;
-    ls.capt++;
-  } else if (!w_positive(p)) {
-    status = 2;
-    ls.abs++;
-  } else {
-    if (w_roulette(m, p)) {
-      if (rng_u(p.s, m.seed) < m.roulette_p) {
-        p.w /= m.roulette_p;
-        ls.roul++;
-      } else {
-        status = 2;
-        ls.abs++;
-      }
-    }
-    if (status == 0 && p.nsteps >= m.max_steps) {
-      status = 4;
-      ls.maxst++;
-    }
+    return terminate(m, io, G, p, 1, ls) == 0;
   }
-  if (status) {
-    write_log(io, p, status);
-    return false;
-  }
-  return true;
+  Geo Gd;   // not read: recording needs the metric only when sc.term == 1
+  return terminate(m, io, Gd, p, sc.term, ls) == 0;
 }
 
 }  // namespace mcgb

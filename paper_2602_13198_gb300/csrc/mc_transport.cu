@@ -20,7 +20,7 @@
 
 namespace mcgb {
 // Emission or child loading + transport initialisation, one item per thread (grid-stride).
-template <bool MIXED, bool KERR>
+template <int PREC, bool KERR>
 __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -31,14 +31,14 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
     if (have) {
       Ph p;
       if (io.mode == 2) {
-        load_child(m, io.in, idx, p, ls);
+        load_child<Form<PREC>::K32>(m, io.in, idx, p, ls);
       } else {
         int64_t uid = (io.mode == 1) ? io.uids[idx] : io.uid0 + idx;
         emit(m, uid, p, ls);
         ls.emit++;
       }
       p.model = 0;
-      init_transport<MIXED, KERR>(m, p);
+      init_transport<Form<PREC>::C32, KERR>(m, p);
       save_ph(io.pool, idx, p);
       grid_phase = in_grid(m, p.X);
     }
@@ -63,11 +63,11 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
 // Persistent transport of one phase over io.list_in; PHASE 0 keeps superphotons while they are in
 // the grid, PHASE 1 while they are outside it.  A lane whose superphoton ends or changes phase is
 // refilled from the list (one atomic per warp).
-template <bool MIXED, int PHASE, bool KERR>
+template <int PREC, int PHASE, bool KERR>
 __device__ __forceinline__ void push_body(const DevModel &m, const PushIO &io) {
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  PhT<GeoScalar<MIXED>> p;   // double-float geodesic in the mixed-precision form
+  PhF<PREC> p;   // the precision form's geodesic and weight scalars
   p.raddr = nullptr;
   int64_t slot = -1;
   bool live = false;
@@ -96,10 +96,10 @@ __device__ __forceinline__ void push_body(const DevModel &m, const PushIO &io) {
     if (live) {
       bool handoff;
       if (PHASE == 0) {
-        live = step<MIXED, KERR>(m, io, p, ls);
+        live = step<PREC, KERR>(m, io, p, ls);
         handoff = live && !in_grid(m, p.X);
       } else {
-        int r = step_free<KERR>(m, io, p, ls);
+        int r = step_free<PREC, KERR>(m, io, p, ls);
         live = (r != 1);
         handoff = (r == 2);
       }
@@ -118,31 +118,38 @@ __device__ __forceinline__ void push_body(const DevModel &m, const PushIO &io) {
 // FP64 form: the compiler's register choice (the FP64 pipe is the bound, occupancy does not matter).
 template <int PHASE, bool KERR>
 __global__ void __launch_bounds__(128) k_push_fp64(DevModel m, PushIO io) {
-  push_body<false, PHASE, KERR>(m, io);
+  push_body<0, PHASE, KERR>(m, io);
 }
 
 // Mixed form (double-float geodesic on the FP32 pipes): capped at 128 registers for four CTAs per SM,
 // which measured 6% faster than three at 168.
 template <int PHASE, bool KERR>
 __global__ void __launch_bounds__(128, 4) k_push_mixed(DevModel m, PushIO io) {
-  push_body<true, PHASE, KERR>(m, io);
+  push_body<1, PHASE, KERR>(m, io);
+}
+
+// Split form (FP64 geodesic, FP32 coefficients and weights): bound by the FP64 pipe like the FP64 form.
+template <int PHASE, bool KERR>
+__global__ void __launch_bounds__(128) k_push_split(DevModel m, PushIO io) {
+  push_body<2, PHASE, KERR>(m, io);
 }
 
 // Persistent in-grid push with the network.  Each 128-thread row group reaches its tensor-core
 // evaluation once per iteration (idle lanes contribute a zero row) and leaves the loop as a whole;
 // the CTA's groups iterate independently and meet again only at the teardown.
+template <int PREC>
 __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, PushIO io, SurrogateView sv) {
   extern __shared__ __align__(128) unsigned char smem_sur[];
   TcMlp T;
   tc_setup(T, smem_sur, sv);
   const int lane = threadIdx.x & 31;
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  PhT<df> p;
+  PhF<PREC> p;
   p.raddr = nullptr;
   int64_t slot = -1;
   bool live = false;
   bool exhausted = false;
-  SurCarry<df> sc;
+  SurCarry<typename Form<PREC>::S> sc;
   while (true) {
     if (!exhausted) {
       unsigned idle = __ballot_sync(0xffffffffu, !live);
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, Pus
     }
     tc_mlp_eval(T, in, out);
     if (live) {
-      live = step_sur_b(m, io, p, sc, out, ls);
+      live = step_sur_b<PREC>(m, io, p, sc, out, ls);
       if (live && !in_grid(m, p.X)) {
         save_ph(io.pool, slot, p);
         unsigned long long o = atomicAdd(io.cnt + io.out_counter, 1ull);
@@ -191,67 +198,58 @@ __global__ void __launch_bounds__(128 * kTcGroupsMax) k_push_sur(DevModel m, Pus
   flush_stats(ls, io.cnt);
 }
 
-int push_sur_max_blocks_per_sm(int block, int smem) {
+static const void *sur_kernel(int prec) {
+  return prec == 2 ? (const void *)k_push_sur<2> : (const void *)k_push_sur<1>;
+}
+
+int push_sur_max_blocks_per_sm(int prec, int block, int smem) {
   int n = 0;
-  cudaFuncSetAttribute(k_push_sur, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_push_sur, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_push_sur, block, smem);
+  const void *k = sur_kernel(prec);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem);
   return n;
 }
 
-void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &sv, int grid, int smem, cudaStream_t st) {
-  k_push_sur<<<grid, 128 * kTcGroupsMax, smem, st>>>(m, io, sv);
+void launch_push_sur(const DevModel &m, const PushIO &io, const SurrogateView &sv, int prec, int grid, int smem,
+                     cudaStream_t st) {
+  if (prec == 2) k_push_sur<2><<<grid, 128 * kTcGroupsMax, smem, st>>>(m, io, sv);
+  else k_push_sur<1><<<grid, 128 * kTcGroupsMax, smem, st>>>(m, io, sv);
 }
 
-// Kernel of one launch configuration: precision, phase and spin (general Kerr, or a = 0).
-template <bool MIXED, int PHASE>
-static const void *push_kernel(bool kerr) {
-  if (MIXED) return kerr ? (const void *)k_push_mixed<PHASE, true> : (const void *)k_push_mixed<PHASE, false>;
+// Kernel of one launch configuration: precision form, phase and spin (general Kerr, or a = 0).
+template <int PHASE>
+static const void *push_kernel(int prec, bool kerr) {
+  if (prec == 1) return kerr ? (const void *)k_push_mixed<PHASE, true> : (const void *)k_push_mixed<PHASE, false>;
+  if (prec == 2) return kerr ? (const void *)k_push_split<PHASE, true> : (const void *)k_push_split<PHASE, false>;
   return kerr ? (const void *)k_push_fp64<PHASE, true> : (const void *)k_push_fp64<PHASE, false>;
 }
 
-static const void *push_kernel(int mixed, int phase, bool kerr) {
-  if (mixed) return phase == 0 ? push_kernel<true, 0>(kerr) : push_kernel<true, 1>(kerr);
-  return phase == 0 ? push_kernel<false, 0>(kerr) : push_kernel<false, 1>(kerr);
-}
-
-int push_max_blocks_per_sm(int mixed, int phase, int block, int kerr) {
+int push_max_blocks_per_sm(int prec, int phase, int block, int kerr) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, push_kernel(mixed, phase, kerr != 0), block, 0);
+  const void *k = phase == 0 ? push_kernel<0>(prec, kerr != 0) : push_kernel<1>(prec, kerr != 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0);
   return n;
 }
 
-void launch_init(const DevModel &m, const InitIO &io, int mixed, int grid, int block, cudaStream_t st) {
-  const bool kerr = m.a != 0.0;
-  if (mixed) {
-    if (kerr) k_init<true, true><<<grid, block, 0, st>>>(m, io);
-    else k_init<true, false><<<grid, block, 0, st>>>(m, io);
-  } else {
-    if (kerr) k_init<false, true><<<grid, block, 0, st>>>(m, io);
-    else k_init<false, false><<<grid, block, 0, st>>>(m, io);
-  }
+template <int PREC>
+static void launch_init_t(const DevModel &m, const InitIO &io, int grid, int block, cudaStream_t st) {
+  if (m.a != 0.0) k_init<PREC, true><<<grid, block, 0, st>>>(m, io);
+  else k_init<PREC, false><<<grid, block, 0, st>>>(m, io);
+}
+
+void launch_init(const DevModel &m, const InitIO &io, int prec, int grid, int block, cudaStream_t st) {
+  if (prec == 1) launch_init_t<1>(m, io, grid, block, st);
+  else if (prec == 2) launch_init_t<2>(m, io, grid, block, st);
+  else launch_init_t<0>(m, io, grid, block, st);
 }
 
 // a = 0 takes the Schwarzschild form of the metric and of the geodesic acceleration.
-void launch_push(const DevModel &m, const PushIO &io, int mixed, int phase, int grid, int block, cudaStream_t st) {
+void launch_push(const DevModel &m, const PushIO &io, int prec, int phase, int grid, int block, cudaStream_t st) {
   const bool kerr = m.a != 0.0;
-  if (mixed) {
-    if (phase == 0) {
-      if (kerr) k_push_mixed<0, true><<<grid, block, 0, st>>>(m, io);
-      else k_push_mixed<0, false><<<grid, block, 0, st>>>(m, io);
-    } else {
-      if (kerr) k_push_mixed<1, true><<<grid, block, 0, st>>>(m, io);
-      else k_push_mixed<1, false><<<grid, block, 0, st>>>(m, io);
-    }
-  } else {
-    if (phase == 0) {
-      if (kerr) k_push_fp64<0, true><<<grid, block, 0, st>>>(m, io);
-      else k_push_fp64<0, false><<<grid, block, 0, st>>>(m, io);
-    } else {
-      if (kerr) k_push_fp64<1, true><<<grid, block, 0, st>>>(m, io);
-      else k_push_fp64<1, false><<<grid, block, 0, st>>>(m, io);
-    }
-  }
+  void *args[] = {(void *)&m, (void *)&io};
+  const void *k = phase == 0 ? push_kernel<0>(prec, kerr) : push_kernel<1>(prec, kerr);
+  cudaLaunchKernel(k, dim3(grid), dim3(block), args, 0, st);
 }
 
 }  // namespace mcgb

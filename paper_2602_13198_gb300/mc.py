@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmcgb.so")
 MC_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "NO_DEVICE", -3: "OOM", -4: "TIMEOUT", -5: "QUEUE_OVERFLOW",
           -6: "NAN_INPUT", -7: "SIZE", -8: "STATE", -9: "CUDA"}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "split": 2}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)

@@ -110,11 +110,11 @@ def test_trained_network_against_quadrature(model):
     err_tab = np.abs(sig_tab / sig_q - 1)
     # photon energies up to 100 m_e c^2: the network reproduces the quadrature to ~1%
     assert np.median(err_nn) < 5e-3 and err_nn.max() < 3e-2
-    # What the network gains, measured: one evaluation gives all three coefficients from 4611 FP32
-    # weights (18 KB, shared by every model of a batch) where the method without it reads three
-    # tables (ln sigma_h alone is 121 x 181 doubles, 175 KB).  What it does not gain: a bilinear
-    # sigma_h table with the network's footprint (24 x 96 doubles) is more accurate at these points.
-    assert model.N_WEIGHTS * 4 * 9 < 121 * 181 * 8
+    # What the network gains and does not gain, measured at these points against the quadrature.
+    # Gains: one evaluation gives all three coefficients from 4611 FP32 weights (18 KB, shared by every
+    # model of a batch), where the method without it reads three tables (ln sigma_h alone is 121 x 181
+    # doubles, 175 KB).  Does not gain accuracy: the full table, and even a bilinear table of the
+    # network's footprint (24 x 96 doubles = 18 KB), are more accurate than the network.
     gt = np.linspace(np.log(1e-3), np.log(1e3), 24)
     ge = np.linspace(np.log(1e-12), np.log(1e6), 96)
     tab = np.array([[np.log(oracle.sigma_hot_quad(np.exp(a), np.exp(b))) for b in ge] for a in gt])
@@ -125,6 +125,8 @@ def test_trained_network_against_quadrature(model):
           "equal-footprint table median %.2e max %.2e"
           % (np.median(err_nn), err_nn.max(), np.median(err_tab), err_tab.max(), np.median(err_small),
              err_small.max()))
+    assert np.median(err_tab) < 1e-5 and np.median(err_tab) < 0.1 * np.median(err_nn)
+    assert np.median(err_small) < np.median(err_nn)
 
 
 @pytest.fixture(scope="module")
@@ -151,3 +153,48 @@ def test_surrogate_spectrum_within_tolerance(trained_weights, case, n_s, seed):
     ok, bad = spectra_agree(m.spectrum_sums(), ro["spec"])
     assert ok, bad
     assert st["n_emit"] == ro["stats"]["n_emit"]
+
+
+def test_batched_surrogate_speed_against_batched_mixed(trained_weights):
+    """Timed on the GPU: a 12-model survey slice batched in mixed precision with and without the
+    network in the in-grid phase (autotuned, graph replay, CUDA events).  The network form is recorded
+    by assertion as no faster than the table form and at most 30% slower (measured: ~9% slower on the
+    full survey, because every 128-row group waits for the tensor cores in lockstep while the lookups
+    it replaces are already cheap), with the same spectra within max(1%, 3 sigma)."""
+    import torch
+
+    from helpers import spectra_agree
+    from paper_2602_13198_gb300 import mc
+    specs = synth.survey(64, 1)
+    pick = [(p, g, n) for (p, g, n) in specs if p["R_high"] <= 10.0][:12]
+    ns = [min(n, 2e6) for (_, _, n) in pick]
+    seeds = [201 + i for i in range(len(pick))]
+    res = {}
+    for sur in (False, True):
+        ctxs = []
+        for p, g, _ in pick:
+            m = mc.Model(p, precision="mixed", surrogate=sur)
+            if sur:
+                m.surrogate_weights(trained_weights)
+            m.set_grid(g)
+            ctxs.append(m)
+        mc.run_batch(ctxs, ns, seeds, autotune=True, graph=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0.record()
+            st = mc.run_batch(ctxs, ns, seeds, autotune=True, graph=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        rate = (st["n_emit"] + st["n_child"]) / (best / 1e3)
+        res[sur] = (rate, [c.spectrum_sums().copy() for c in ctxs])
+    ratio = res[True][0] / res[False][0]
+    print("batched surrogate / batched mixed throughput: %.3f (%.3e vs %.3e superphotons/s)"
+          % (ratio, res[True][0], res[False][0]))
+    assert 0.70 <= ratio <= 1.0
+    for a, b in zip(res[True][1], res[False][1]):
+        ok, bad = spectra_agree(a, b)
+        assert ok, bad
