@@ -173,6 +173,7 @@ DevModel make_model(const mc_ctx *c) {
   m.dhh_pi = df_const((1.0 - p.hslope) / (2.0 * kPI));
   m.dd2th = df_const(-2.0 * kPI * kPI * (1.0 - p.hslope));
   m.dtab = c->dtab;
+  m.ftab = c->ftab;
   m.fidx1 = (float)m.idx1;
   m.fidx2 = (float)m.idx2;
   m.fidx3 = (float)m.idx3;
@@ -292,6 +293,7 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
   c->hot = (double *)dev_alloc(c, sizeof(double) * kHotNT * kHotNE);
   c->gl = (double *)dev_alloc(c, sizeof(double) * (128 + 128 + 64));
   c->dtab = (df *)dev_alloc(c, sizeof(df) * kDfTabN);
+  c->ftab = (double *)dev_alloc(c, sizeof(double) * kFtN);
   c->cnt = (unsigned long long *)dev_alloc(c, sizeof(unsigned long long) * CNT_N);
   c->total_dev = (int64_t *)dev_alloc(c, sizeof(int64_t));
   size_t nspec = (size_t)p->n_incl * p->n_bins * 3;
@@ -322,6 +324,12 @@ int mc_init_model(mc_ctx **out, const mc_model_params *p) {
   df dft[kDfTabN];
   df_table_host(dft);
   if (!c->dtab || cudaMemcpy(c->dtab, dft, sizeof(dft), cudaMemcpyHostToDevice) != cudaSuccess) {
+    mc_free(c);
+    return fail(nullptr, MC_ERR_CUDA, "table upload failed");
+  }
+  std::vector<double> ft(kFtN);
+  ftab_host(ft.data());
+  if (!c->ftab || cudaMemcpy(c->ftab, ft.data(), sizeof(double) * kFtN, cudaMemcpyHostToDevice) != cudaSuccess) {
     mc_free(c);
     return fail(nullptr, MC_ERR_CUDA, "table upload failed");
   }
@@ -835,7 +843,7 @@ int mc_get_bias_scales(mc_ctx *c, double *scales, int n) {
 }
 
 int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t n) {
-  if (which < 0 || which > 5 || n < 0 || (n > 0 && (!x || !y || !ref))) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
+  if (which < 0 || which > 9 || n < 0 || (n > 0 && (!x || !y || !ref))) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();

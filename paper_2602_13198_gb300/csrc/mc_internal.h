@@ -129,6 +129,7 @@ struct mc_ctx {
   double *kapF = nullptr, *kapJ = nullptr, *kapA = nullptr, *kapI = nullptr;   // kappa tables
   double *kapH = nullptr;                   // kappa hot cross-section [kKapNW][kHotNE]
   mcgb::df *dtab = nullptr;                 // double-float function table (exp2, sin pi)
+  double *ftab = nullptr;                   // tables of the FP64 exp_t, log_t, sincospi_t
   float *lnK2f = nullptr, *hotf = nullptr;  // FP32 copies of the K2 and hot cross-section tables
   int prim_f32 = 0;
   int n1 = 0, n2 = 0, n3 = 0;

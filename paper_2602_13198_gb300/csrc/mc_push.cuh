@@ -489,7 +489,7 @@ __device__ __forceinline__ void absorb_scatter(const DevModel &m, const PushIO &
     double tau_a = 0.5 * (p.ana + c.ana) * C * dld;
     double w0 = p.w;
     // attenuation factor: FP32 in the mixed-precision form (its coefficients are FP32 already)
-    double wn = w0 * (f32att ? (double)expf((float)-tau_a) : exp(-tau_a));
+    double wn = w0 * (f32att ? (double)expf((float)-tau_a) : exp_t(m.ftab, -tau_a));
     if (scat) {
       double tau_s = 0.5 * (p.ans + c.ans) * C * dld;
       if (__double_as_longlong(tau_s) > 0) {   // tau_s > 0 (tau_s >= 0)

@@ -490,10 +490,30 @@ void df_table_host(df *t) {
   }
 }
 
-__global__ void k_selftest_math(int which, const double *x, double *y, double *ref, int64_t n, const df *T) {
+__global__ void k_selftest_math(int which, const double *x, double *y, double *ref, int64_t n, const df *T,
+                                const double *F) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = x[i];
+  // table-driven FP64 functions against CUDA's
+  if (which == 6) {
+    y[i] = exp_t(F, v);
+    ref[i] = exp(v);
+    return;
+  }
+  if (which == 7) {
+    y[i] = log_t(F, v);
+    ref[i] = log(v);
+    return;
+  }
+  if (which == 8 || which == 9) {
+    double s, c, rs, rc;
+    sincospi_t(F, v, s, c);
+    sincospi(v, &rs, &rc);
+    y[i] = which == 8 ? s : c;
+    ref[i] = which == 8 ? rs : rc;
+    return;
+  }
   // double-float functions: the reference takes the input as split to double-float
   const df vd = df_from(v);
   if (which == 3) {
@@ -522,19 +542,54 @@ __global__ void k_selftest_math(int which, const double *x, double *y, double *r
   ref[i] = (which == 0) ? rs : rc;
 }
 
+// Tables of exp_t, log_t and sincospi_t, in extended precision: 2^(j/32); 1/c_j, log c_j split into its
+// double and the remainder (c_j = 1 + j/128); sin and cos (pi j/32), exact at multiples of pi/2.
+void ftab_host(double *t) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int j = 0; j < 32; ++j) t[kFtExp + j] = (double)exp2l((long double)j / 32.0L);
+  for (int j = 0; j < 128; ++j) {
+    const long double c = 1.0L + (long double)j / 128.0L;
+    t[kFtInvC + j] = (double)(1.0L / c);
+    const long double L = logl(c);
+    const double hi = (double)L;
+    t[kFtLogHi + j] = hi;
+    t[kFtLogLo + j] = (double)(L - (long double)hi);
+  }
+  for (int j = 0; j < 64; ++j) {
+    long double sv = sinl(pi * j / 32.0L), cv = cosl(pi * j / 32.0L);
+    if (j % 16 == 0) {
+      const int q = j / 16;
+      sv = (q == 1) ? 1.0L : (q == 3) ? -1.0L : 0.0L;
+      cv = (q == 0) ? 1.0L : (q == 2) ? -1.0L : 0.0L;
+    }
+    t[kFtSin + j] = (double)sv;
+    t[kFtCos + j] = (double)cv;
+  }
+}
+
 cudaError_t selftest_math(int which, const double *x_dev, double *y_dev, double *ref_dev, int64_t n) {
   df host[kDfTabN];
   df_table_host(host);
+  double fhost[kFtN];
+  ftab_host(fhost);
   df *tab = nullptr;
+  double *ftab = nullptr;
   cudaError_t e = cudaMalloc(&tab, sizeof(host));
   if (e != cudaSuccess) return e;
+  e = cudaMalloc(&ftab, sizeof(fhost));
+  if (e != cudaSuccess) {
+    cudaFree(tab);
+    return e;
+  }
   e = cudaMemcpy(tab, host, sizeof(host), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ftab, fhost, sizeof(fhost), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && n > 0) {
-    k_selftest_math<<<(unsigned)((n + 255) / 256), 256>>>(which, x_dev, y_dev, ref_dev, n, tab);
+    k_selftest_math<<<(unsigned)((n + 255) / 256), 256>>>(which, x_dev, y_dev, ref_dev, n, tab, ftab);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(tab);
+  cudaFree(ftab);
   return e;
 }
 

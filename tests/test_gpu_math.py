@@ -1,6 +1,7 @@
 """The library's own special-function implementations against CUDA's on the device: the Taylor
 sine/cosine of the small theta-map angle (metric evaluation), the Newton x^(1/6) of the
-synchrotron function, and the double-float e^x and sin/cos(pi x) of the mixed-precision geodesic."""
+synchrotron function, the double-float e^x and sin/cos(pi x) of the mixed-precision geodesic, and the
+table-driven FP64 e^x, ln x and sin/cos(pi x) of the FP64 transport (after Tang 1989, 1990)."""
 import numpy as np
 import pytest
 
@@ -65,3 +66,48 @@ def test_double_float_sincospi_matches_cuda(which):
     half = (np.abs(k * 2 - np.round(k * 2)) == 0)
     yk = y[200000:200000 + len(k)]
     assert np.all(np.isin(np.abs(yk[half]), [0.0, 1.0]))
+
+
+def test_table_driven_exp_matches_cuda():
+    mc = _mc()
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.uniform(-707.9, 707.9, 200000), rng.uniform(-1.0, 1.0, 100000),
+                        np.linspace(-0.011, 0.011, 4001),
+                        np.array([0.0, 1.0, -1.0, np.log(2.0), 707.9, -707.9, 708.0, -708.0, 709.5, -745.0, -800.0])])
+    y, ref = mc.selftest_math(6, x)
+    fin = ref > 0
+    rel = np.abs(y[fin] / ref[fin] - 1.0)
+    # within 3 ulp of CUDA's exp; outside (-708, 708) the function is CUDA's own
+    assert rel.max() <= 3 * 2.2e-16, rel.max()
+    assert y[-11] == 1.0 and np.array_equal(y[-5:], ref[-5:])
+
+
+def test_table_driven_log_matches_cuda():
+    mc = _mc()
+    rng = np.random.default_rng(12)
+    x = np.concatenate([10.0 ** rng.uniform(-300, 300, 200000), rng.uniform(0.5, 2.0, 100000),
+                        1.0 + np.linspace(-1e-6, 1e-6, 2001),
+                        np.array([1.0, 2.0, 0.5, 1e-310, 0.0, 1e308])])
+    y, ref = mc.selftest_math(7, x)
+    big = np.isfinite(ref) & (np.abs(ref) >= 1e-2)
+    # ~1 ulp away from x = 1: within 4 ulp of CUDA's log; near x = 1 within 3e-16 absolute
+    assert (np.abs(y[big] - ref[big]) / np.abs(ref[big])).max() <= 4 * 2.2e-16
+    assert np.abs(y[~big & np.isfinite(ref)] - ref[~big & np.isfinite(ref)]).max() <= 3e-16
+    assert y[-6] == 0.0 and y[-2] == ref[-2] and y[-3] == ref[-3]   # ln 1 = 0; subnormal and 0 take CUDA's log
+
+
+@pytest.mark.parametrize("which", [8, 9])
+def test_table_driven_sincospi_matches_cuda(which):
+    mc = _mc()
+    rng = np.random.default_rng(13 + which)
+    x = np.concatenate([rng.uniform(-2.0, 3.0, 200000), rng.uniform(0.0, 1.0, 100000), np.arange(-64, 97) / 32.0,
+                        np.array([1e-9, 0.5 - 1e-12, 1.0 - 1e-15, 1e-300])])
+    y, ref = mc.selftest_math(which, x)
+    assert np.abs(y - ref).max() <= 3 * 2.2e-16
+    k = np.arange(-64, 97) / 32.0
+    half = (np.abs(k * 2 - np.round(k * 2)) == 0)
+    yk = y[300000:300000 + len(k)]
+    assert np.all(np.isin(np.abs(yk[half]), [0.0, 1.0]))
+    if which == 8:
+        assert y[-1] == np.pi * 1e-300 or abs(y[-1] / (np.pi * 1e-300) - 1) < 1e-15
+
