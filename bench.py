@@ -101,7 +101,7 @@ DF_FLOPS_PER_OP = 15.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch / superphotons it carried); traffic grows
 # in proportion to the superphotons a launch carries.  Keyed by (workload, form); re-taken whenever
 # the kernel changes (profiles/ holds the summaries).
-TRAFFIC_B_PER_PH = {("c2", "fp64"): 285.9, ("c4", "fp64"): 6634.2}
+TRAFFIC_B_PER_PH = {("c4", "fp64"): 6647.6}
 # ncu-measured pipe utilisation of the double-float transport kernels (profiles/
 # k_push_mixed_double_float_scattering_sphere.md): FP32 pipe busy, in-grid / free-streaming.
 NCU_MIXED_FP32_PIPE = {"in_grid": 0.225, "free": 0.509, "source": "ncu, scattering sphere N_s=1e6"}
