@@ -170,24 +170,34 @@ __device__ void batch_phase(const DevModel *sm, const BatchIO &b, const PushIO &
 }
 
 // Dynamic shared memory of a batch CTA: the model descriptors, then (surrogate) the network's tiles.
+// Variants of 6 or more resident CTAs per SM (the double-float form, latency-bound, gains from resident
+// warps) read the descriptors from global memory through L1 instead: ~48 KB per CTA of shared memory
+// would cap residency at 4.
 constexpr int kModelsSmem = (int)((sizeof(DevModel) * kMaxBatch + 127) / 128 * 128);
-static int batch_smem_bytes(bool sur) { return kModelsSmem + (sur ? tc_smem_bytes(kTcGroupsMax) : 0); }
+__host__ __device__ constexpr bool global_desc(bool sur, int minb) { return !sur && minb >= 6; }
+static int batch_smem_bytes(bool sur, int minb) {
+  return (global_desc(sur, minb) ? 0 : kModelsSmem) + (sur ? tc_smem_bytes(kTcGroupsMax) : 0);
+}
 
 template <int PREC, bool SUR, int MINB>
 __global__ void __launch_bounds__(SUR ? 128 * kTcGroupsMax : 128, MINB) k_batch(BatchIO b) {
   __shared__ int64_t soff[kMaxBatch + 1];
   extern __shared__ __align__(128) unsigned char dyn[];
-  DevModel *sm = reinterpret_cast<DevModel *>(dyn);
-  {
+  const DevModel *sm;
+  if constexpr (global_desc(SUR, MINB)) {
+    sm = b.models;
+  } else {
+    DevModel *ds = reinterpret_cast<DevModel *>(dyn);
     const unsigned long long *src = (const unsigned long long *)b.models;
-    unsigned long long *dst = (unsigned long long *)sm;
+    unsigned long long *dst = (unsigned long long *)ds;
     const int words = (int)(b.n_models * sizeof(DevModel) / 8);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-    for (int i = threadIdx.x; i <= b.n_models; i += blockDim.x) soff[i] = b.prim_off[i];
+    sm = ds;
   }
+  for (int i = threadIdx.x; i <= b.n_models; i += blockDim.x) soff[i] = b.prim_off[i];
   __syncthreads();
   TcMlp T;
-  if (SUR) tc_setup(T, dyn + kModelsSmem, b.sv);
+  if (SUR) tc_setup(T, dyn + (global_desc(SUR, MINB) ? 0 : kModelsSmem), b.sv);
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long *agrid = b.ph + kPhBase, *afree = agrid + kMaxPhases, *cgrid = afree + kMaxPhases,
                      *cfree = cgrid + kMaxPhases;
@@ -294,7 +304,12 @@ typedef void (*BatchKernel)(BatchIO);
 // FP64 pipe like the FP64 form; it keeps the 1 and 3 variants.
 static BatchKernel pick_kernel(int prec, bool sur, int minb) {
   if (sur) return prec == 2 ? k_batch<2, true, 1> : k_batch<1, true, 1>;
-  if (prec == 1) return minb == 1 ? k_batch<1, false, 1> : minb == 3 ? k_batch<1, false, 3> : k_batch<1, false, 4>;
+  if (prec == 1)
+    return minb == 1   ? k_batch<1, false, 1>
+           : minb == 3 ? k_batch<1, false, 3>
+           : minb == 4 ? k_batch<1, false, 4>
+           : minb == 6 ? k_batch<1, false, 6>
+                       : k_batch<1, false, 8>;
   if (prec == 2) return minb == 1 ? k_batch<2, false, 1> : k_batch<2, false, 3>;
   return minb == 1 ? k_batch<0, false, 1> : minb == 3 ? k_batch<0, false, 3> : k_batch<0, false, 4>;
 }
@@ -468,7 +483,7 @@ static cudaError_t batch_enqueue(mc_ctx **ctxs, int n, const double *n_s, const 
   if (sur) b.sv = surrogate_view(c0);
   b.timeout_ns = c0->wait_ns;
   BatchKernel kern = pick_kernel(prec, sur, minb);
-  const int smem = batch_smem_bytes(sur);
+  const int smem = batch_smem_bytes(sur, minb);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // shared memory over L1: the descriptors take ~48 KB, a CTA with four network row groups ~163 KB more
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -483,7 +498,7 @@ static int max_ctas(mc_ctx *c0, int minb) {
   const int prec = c0->p.precision;
   const bool sur = c0->p.surrogate == 1;
   BatchKernel kern = pick_kernel(prec, sur, minb);
-  const int smem = batch_smem_bytes(sur);
+  const int smem = batch_smem_bytes(sur, minb);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute((const void *)kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int n = 0;
@@ -541,12 +556,13 @@ extern "C" int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint6
     const double frac = std::min(1.0, std::max(0.05, 5e6 / ns_tot));
     for (int i = 0; i < n; ++i) ns_small[i] = std::max(1.0, frac * n_s[i]);
     double best = 1e300;
-    const int minbs[3] = {1, 3, 4};   // register caps 255, 168, 128
+    const int minbs[5] = {1, 3, 4, 6, 8};   // register caps 255, 168, 128, 80, 64
     for (int mb : minbs) {
       if (mb != 1 && c0->p.surrogate == 1) continue;   // one launch-bounds variant with the network
       if (mb == 4 && c0->p.precision == MC_PREC_SPLIT) continue;   // the split form has the 1 and 3 variants
+      if (mb >= 6 && c0->p.precision != MC_PREC_MIXED) continue;   // the double-float form only
       int mx = max_ctas(c0, mb);
-      for (int per = 1; per <= mx; ++per) {
+      for (int per = (mb >= 6 ? 5 : 1); per <= mx; ++per) {
         int ctas = per * c0->sms;
         cudaError_t e = batch_enqueue(ctxs, n, ns_small.data(), seeds, bs, mb, ctas, st, true);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);

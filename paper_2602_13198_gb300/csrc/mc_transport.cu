@@ -115,22 +115,33 @@ __device__ __forceinline__ void push_body(const DevModel &m, const PushIO &io) {
   flush_stats(ls, io.cnt);
 }
 
-// FP64 form: the compiler's register choice (the FP64 pipe is the bound, occupancy does not matter).
+// Minimum resident CTAs of 128 threads per SM that each form's register cap allows (65536 / (128 x
+// CTAs) registers per thread).  FP64 form: the FP64 pipe is the bound.  Mixed form (double-float
+// geodesic on the FP32 pipes): latency-bound, it gains from resident warps even with spills at the
+// cap; measured on the 3-D snapshot, the 2-D torus and the sphere, 8 CTAs (64 registers) beat 2 to 6
+// and 10 to 16.
+#ifndef MC_FP64_MINB
+#define MC_FP64_MINB 1
+#endif
+#ifndef MC_MIXED_MINB
+#define MC_MIXED_MINB 8
+#endif
+#ifndef MC_SPLIT_MINB
+#define MC_SPLIT_MINB 1
+#endif
 template <int PHASE, bool KERR>
-__global__ void __launch_bounds__(128) k_push_fp64(DevModel m, PushIO io) {
+__global__ void __launch_bounds__(128, MC_FP64_MINB) k_push_fp64(DevModel m, PushIO io) {
   push_body<0, PHASE, KERR>(m, io);
 }
 
-// Mixed form (double-float geodesic on the FP32 pipes): capped at 128 registers for four CTAs per SM,
-// which measured 6% faster than three at 168.
 template <int PHASE, bool KERR>
-__global__ void __launch_bounds__(128, 4) k_push_mixed(DevModel m, PushIO io) {
+__global__ void __launch_bounds__(128, MC_MIXED_MINB) k_push_mixed(DevModel m, PushIO io) {
   push_body<1, PHASE, KERR>(m, io);
 }
 
-// Split form (FP64 geodesic, FP32 coefficients and weights): bound by the FP64 pipe like the FP64 form.
+// Split form (FP64 geodesic, FP32 coefficients and weights).
 template <int PHASE, bool KERR>
-__global__ void __launch_bounds__(128) k_push_split(DevModel m, PushIO io) {
+__global__ void __launch_bounds__(128, MC_SPLIT_MINB) k_push_split(DevModel m, PushIO io) {
   push_body<2, PHASE, KERR>(m, io);
 }
 
