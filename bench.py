@@ -489,6 +489,8 @@ def main():
     ap.add_argument("--n-s", type=float, default=N_S_C4, help="N_s of the main job (smaller for profiling)")
     ap.add_argument("--shards", type=int, default=SHARDS, help="shards per job (one per step)")
     ap.add_argument("--grid", default="288x128x128", help="3-D grid of the main workload (smaller for tests)")
+    ap.add_argument("--main-precision", default="fp64", choices=["fp64", "mixed", "split"],
+                    help="precision form of the main line (profiling; the headline is plain FP64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass (profiling runs)")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-configuration forms")
@@ -526,7 +528,7 @@ def main():
 
     # ---- main workload: the 3-D snapshot, plain FP64, one shard of the job per step
     p4, g4 = synth.torus3d(**grid_dims(args))
-    m4 = mc.Model(p4, device=dev, precision="fp64")
+    m4 = mc.Model(p4, device=dev, precision=args.main_precision)
     m4.set_grid(g4)
     S = args.shards
 
@@ -597,10 +599,17 @@ def main():
     else:
         e2e_value = e2e_units / t_e2e
 
-    roofline = fp64_roofline(st_main, "kerr", 3, fp64_peak, "k_push_fp64<in-grid, kerr> (FP64, trilinear FP32 fields): "
-                             "dominant kernel, %.0f%% of transport time"
-                             % (100 * st_main["grid_ms"] / max(st_main["transport_ms"], 1e-30)),
-                             TRAFFIC_B_PER_PH.get(("c4", "fp64")), hbm_peak, fp32_peak)
+    share = 100 * st_main["grid_ms"] / max(st_main["transport_ms"], 1e-30)
+    if args.main_precision == "mixed":
+        roofline = df_roofline(st_main, "kerr", fp32_peak, fp64_peak, "k_push_mixed<in-grid, kerr>: %.0f%% of transport "
+                               "time" % share)
+    elif args.main_precision == "split":
+        roofline = split_roofline(st_main, "kerr", fp64_peak, "k_push_split<in-grid, kerr>: %.0f%% of transport time"
+                                  % share)
+    else:
+        roofline = fp64_roofline(st_main, "kerr", 3, fp64_peak, "k_push_fp64<in-grid, kerr> (FP64, trilinear FP32 "
+                                 "fields): dominant kernel, %.0f%% of transport time" % share,
+                                 TRAFFIC_B_PER_PH.get(("c4", "fp64")), hbm_peak, fp32_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -623,7 +632,7 @@ def main():
                                            % (n1, u_1, dt1)}}
 
     forms = None
-    if world == 1 and not args.no_forms:
+    if world == 1 and not args.no_forms and args.main_precision == "fp64":
         forms = {"peaks": {"fp64_tflops": fp64_peak / 1e12, "fp32_tflops": fp32_peak / 1e12,
                            "hbm_gbs": hbm_peak, "bf16_tflops": bf16_peak, "hbm_bf16_source": peak_src}}
         # the coefficient network, trained on the GPU by the library's own kernels (untimed set-up)
@@ -681,9 +690,13 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "mixed": "f32 pairs (double-float) + f32", "split": "f64 + f32"}[args.main_precision],
+                "data": "synthetic",
                 "config": {"workload": WORKLOAD_C4 if not grid_dims(args) else WORKLOAD_C4 + " (grid " + args.grid + ")",
-                           "form": "plain FP64", "n_s_per_job": args.n_s,
+                           "form": {"fp64": "plain FP64", "mixed": "mixed (double-float geodesic)",
+                                    "split": "split (FP64 geodesic, FP32 rest)"}[args.main_precision],
+                           "n_s_per_job": args.n_s,
                            "shards_per_job": S, "step": "one mc_run of one shard (generation over the whole grid + "
                                                         "the shard's transport and binning)",
                            "grid": [int(x) for x in args.grid.split("x")],
