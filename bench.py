@@ -102,9 +102,10 @@ DF_FLOPS_PER_OP = 15.0
 # in proportion to the superphotons a launch carries.  Keyed by (workload, form); re-taken whenever
 # the kernel changes (profiles/ holds the summaries).
 TRAFFIC_B_PER_PH = {("c4", "fp64"): 6647.6}
-# ncu-measured pipe utilisation of the double-float transport kernels (profiles/
-# k_push_mixed_double_float_scattering_sphere.md): FP32 pipe busy, in-grid / free-streaming.
-NCU_MIXED_FP32_PIPE = {"in_grid": 0.225, "free": 0.509, "source": "ncu, scattering sphere N_s=1e6"}
+# ncu-measured pipe utilisation of the double-float in-grid kernel (profiles/
+# k_push_mixed_ingrid_snapshot3d.md): FP32 and FP64 pipes busy, issue active.
+NCU_MIXED_FP32_PIPE = {"in_grid_fp32": 0.261, "in_grid_fp64": 0.227, "issue_active": 0.350,
+                       "source": "ncu, 3-D snapshot N_s=4e6, k_push_mixed<0,1> at 8 CTAs/SM"}
 
 
 def log(*a):
