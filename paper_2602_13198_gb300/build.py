@@ -14,8 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmcgb.so")
-SOURCES = ["mc_api.cu", "mc_tables.cu", "mc_transport.cu", "mc_noalloc.cu", "mc_mlp.cu", "mc_batch.cu"]
-HEADERS = ["mc_device.cuh", "mc_df.cuh", "mc_internal.h", "mc_mlp.cuh", "mc_push.cuh"]
+SOURCES = ["mc_api.cu", "mc_tables.cu", "mc_transport.cu", "mc_noalloc.cu", "mc_mlp.cu", "mc_batch.cu",
+           "mc_batch_fp64.cu", "mc_batch_mixed.cu", "mc_batch_split.cu"]
+HEADERS = ["mc_device.cuh", "mc_df.cuh", "mc_internal.h", "mc_mlp.cuh", "mc_push.cuh", "mc_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -818,7 +818,7 @@ static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, PhF<PREC>
     metric_eval<false>(m, p.X[1], p.X[2], G);
     return terminate(m, io, G, p, 1, ls) == 0;
   }
-  Geo Gd;   // not read: recording needs the metric only when sc.term == 1
+  const Geo Gd{};   // not read: recording needs the metric only when sc.term == 1
   return terminate(m, io, Gd, p, sc.term, ls) == 0;
 }
 
