@@ -707,7 +707,10 @@ template <> __device__ __forceinline__ double mv<double>(double d, float) { retu
 template <> __device__ __forceinline__ float mv<float>(double, float f) { return f; }
 
 // metric component of scalar GS as the plasma arithmetic's type T
-template <typename T> __device__ __forceinline__ T cvt(double x) { return (T)x; }
+template <typename T> __device__ __forceinline__ T cvt(double x) {
+  if constexpr (sizeof(T) == 4) return narrow_f(x);   // FP32 plasma state from the FP64 metric (split form)
+  else return (T)x;
+}
 template <typename T> __device__ __forceinline__ T cvt(df x);
 template <> __device__ __forceinline__ float cvt<float>(df x) { return to_f(x); }
 template <> __device__ __forceinline__ double cvt<double>(df x) { return to_d(x); }
@@ -733,6 +736,17 @@ __device__ __forceinline__ float zone_coord(const DevModel &m, const df X[4], in
   return d == 1 ? to_f(X[1] - m.dx1_0) * m.fidx1 - 0.5f
                 : d == 2 ? (to_f(X[2]) - m.fx2_0) * m.fidx2 - 0.5f : (to_f(X[3]) - m.fx3_0) * m.fidx3 - 0.5f;
 }
+// FP32 zone coordinates of an FP64 position (split form): the radial offset from the grid origin in
+// FP64, then FP32, as the double-float form does.
+__device__ __forceinline__ float zone_coord_f(const DevModel &m, const double X[4], int d) {
+  return d == 1 ? narrow_f(X[1] - m.x1_0) * m.fidx1 - 0.5f
+                : d == 2 ? (narrow_f(X[2]) - m.fx2_0) * m.fidx2 - 0.5f : (narrow_f(X[3]) - m.fx3_0) * m.fidx3 - 0.5f;
+}
+template <typename R, typename S>
+__device__ __forceinline__ R zone_coord_r(const DevModel &m, const S X[4], int d) {
+  if constexpr (std::is_same<R, float>::value && std::is_same<S, double>::value) return zone_coord_f(m, X, d);
+  else return zone_coord(m, X, d);
+}
 __device__ __forceinline__ bool outside_radially(const DevModel &m, const double X[4]) {
   const long long k = dkey(X[1]);
   return k < dkey(m.x1_0) || k > dkey(m.x1_hi);
@@ -744,11 +758,12 @@ __device__ __forceinline__ bool outside_radially(const DevModel &m, const df X[4
 template <typename T, typename S>
 __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T pr[8]) {
   if (outside_radially(m, X)) return false;
-  using R = decltype(vmag(X[0]));   // index arithmetic: double, or float for double-float positions
+  // index arithmetic: double for FP64 output; float for FP32 output (double-float or FP64 positions)
+  using R = typename std::conditional<sizeof(T) == 4, float, decltype(vmag(X[0]))>::type;
   int i, j;
   R di, dj;
   {
-    const R f1 = zone_coord(m, X, 1);
+    const R f1 = zone_coord_r<R>(m, X, 1);
     i = zone_floor(f1);
     di = f1 - i;
     if (m.n1 == 1) { i = 0; di = 0; }
@@ -756,7 +771,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
     else if (i > m.n1 - 2) { i = m.n1 - 2; di = 1; }
   }
   {
-    const R f2 = zone_coord(m, X, 2);
+    const R f2 = zone_coord_r<R>(m, X, 2);
     j = zone_floor(f2);
     dj = f2 - j;
     if (m.n2 == 1) { j = 0; dj = 0; }
@@ -766,7 +781,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   int k0 = 0, k1 = 0;
   R dk = 0;
   if (m.n3 > 1) {
-    const R f3 = zone_coord(m, X, 3);
+    const R f3 = zone_coord_r<R>(m, X, 3);
     const int ki = zone_floor(f3);
     dk = f3 - (R)ki;
     long long kk = ki;

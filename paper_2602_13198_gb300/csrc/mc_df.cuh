@@ -91,7 +91,19 @@ __host__ __device__ constexpr df df_const(double x) {
 // S = df (mixed precision); for double every helper is the identity or the plain operation.
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(df x) { return df_to(x); }
-__device__ __forceinline__ float to_f(double x) { return (float)x; }
+// FP64 -> FP32 on the integer pipes, truncating (within one FP32 ulp): sign, exponent re-biased by
+// 1023 - 127 and the top 23 mantissa bits.  Zeros keep their sign; values beyond the FP32 normal range,
+// infinities and NaN take the conversion instruction.  For the split precision form, whose FP32
+// coefficient arithmetic reads the FP64 geodesic state: conversions take FP64-pipe slots on GB300.
+__device__ __forceinline__ float narrow_f(double d) {
+  const long long b = __double_as_longlong(d);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  if (e > 0 && e < 255) return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29));
+  if ((b & 0x7fffffffffffffffLL) == 0) return __uint_as_float(hi & 0x80000000u);
+  return (float)d;
+}
+__device__ __forceinline__ float to_f(double x) { return narrow_f(x); }
 __device__ __forceinline__ float to_f(df x) { return __fadd_rn(x.hi, x.lo); }
 __device__ __forceinline__ double sabs(double x) { return fabs(x); }
 __device__ __forceinline__ df sabs(df x) { return df_abs(x); }

@@ -452,7 +452,7 @@ __device__ __forceinline__ void absorb_scatter(const DevModel &m, const PushIO &
                                                const S K0[4], double dld, const CoefT<W> &c, bool scat, bool f32att,
                                                LocalStats &ls) {
   if constexpr (std::is_same<W, float>::value) {
-    const float C = m.fCcoef, dl = (float)dld;
+    const float C = m.fCcoef, dl = narrow_f(dld);
     const float tau_a = 0.5f * (p.ana + c.ana) * C * dl;
     const float w0 = p.w;
     float wn = w0 * expf(-tau_a);
