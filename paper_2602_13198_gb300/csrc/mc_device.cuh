@@ -707,9 +707,17 @@ template <> __device__ __forceinline__ double mv<double>(double d, float) { retu
 template <> __device__ __forceinline__ float mv<float>(double, float f) { return f; }
 
 // metric component of scalar GS as the plasma arithmetic's type T
-template <typename T> __device__ __forceinline__ T cvt(double x) {
-  if constexpr (sizeof(T) == 4) return narrow_f(x);   // FP32 plasma state from the FP64 metric (split form)
-  else return (T)x;
+template <typename T> __device__ __forceinline__ T cvt(double x) { return (T)x; }
+// FP32 from an FP64 value: truncated on the integer pipes in the split form's transport (NARROW), else
+// the rounding conversion
+template <bool NARROW> __device__ __forceinline__ float f32_of(double x) {
+  if constexpr (NARROW) return narrow_f(x);
+  else return (float)x;
+}
+template <bool NARROW> __device__ __forceinline__ float f32_of(df x) { return to_f(x); }
+template <typename T, bool NARROW, typename V> __device__ __forceinline__ T cvtn(V x) {
+  if constexpr (NARROW && sizeof(T) == 4) return f32_of<true>(x);
+  else return cvt<T>(x);
 }
 template <typename T> __device__ __forceinline__ T cvt(df x);
 template <> __device__ __forceinline__ float cvt<float>(df x) { return to_f(x); }
@@ -742,9 +750,9 @@ __device__ __forceinline__ float zone_coord_f(const DevModel &m, const double X[
   return d == 1 ? narrow_f(X[1] - m.x1_0) * m.fidx1 - 0.5f
                 : d == 2 ? (narrow_f(X[2]) - m.fx2_0) * m.fidx2 - 0.5f : (narrow_f(X[3]) - m.fx3_0) * m.fidx3 - 0.5f;
 }
-template <typename R, typename S>
-__device__ __forceinline__ R zone_coord_r(const DevModel &m, const S X[4], int d) {
-  if constexpr (std::is_same<R, float>::value && std::is_same<S, double>::value) return zone_coord_f(m, X, d);
+template <bool F32IDX, typename S>
+__device__ __forceinline__ auto zone_coord_r(const DevModel &m, const S X[4], int d) {
+  if constexpr (F32IDX && std::is_same<S, double>::value) return zone_coord_f(m, X, d);
   else return zone_coord(m, X, d);
 }
 __device__ __forceinline__ bool outside_radially(const DevModel &m, const double X[4]) {
@@ -755,15 +763,16 @@ __device__ __forceinline__ bool outside_radially(const DevModel &m, const df X[4
   return !(df_ge(X[1], m.dx1_0) && df_le(X[1], m.dx1_hi));
 }
 
-template <typename T, typename S>
+// F32IDX: FP32 index arithmetic for an FP64 position (the split form's transport); otherwise FP64 for
+// FP64 positions and FP32 for double-float ones.
+template <typename T, typename S, bool F32IDX = false>
 __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T pr[8]) {
   if (outside_radially(m, X)) return false;
-  // index arithmetic: double for FP64 output; float for FP32 output (double-float or FP64 positions)
-  using R = typename std::conditional<sizeof(T) == 4, float, decltype(vmag(X[0]))>::type;
+  using R = typename std::conditional<F32IDX, float, decltype(vmag(X[0]))>::type;
   int i, j;
   R di, dj;
   {
-    const R f1 = zone_coord_r<R>(m, X, 1);
+    const R f1 = zone_coord_r<F32IDX>(m, X, 1);
     i = zone_floor(f1);
     di = f1 - i;
     if (m.n1 == 1) { i = 0; di = 0; }
@@ -771,7 +780,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
     else if (i > m.n1 - 2) { i = m.n1 - 2; di = 1; }
   }
   {
-    const R f2 = zone_coord_r<R>(m, X, 2);
+    const R f2 = zone_coord_r<F32IDX>(m, X, 2);
     j = zone_floor(f2);
     dj = f2 - j;
     if (m.n2 == 1) { j = 0; dj = 0; }
@@ -781,7 +790,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   int k0 = 0, k1 = 0;
   R dk = 0;
   if (m.n3 > 1) {
-    const R f3 = zone_coord_r<R>(m, X, 3);
+    const R f3 = zone_coord_r<F32IDX>(m, X, 3);
     const int ki = zone_floor(f3);
     dk = f3 - (R)ki;
     long long kk = ki;
@@ -855,20 +864,21 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
 
 // Fluid-frame quantities from primitives with metric G: 4-velocity from the normal-observer
 // velocity, magnetic 4-vector b, n_e, |B| [G] and Theta_e from the R_high/R_low model.
-template <typename T, typename GS = double>
+template <typename T, typename GS = double, bool NARROW = false>
 __device__ __forceinline__ void plasma_from_prims(const DevModel &m, const GeoT<GS> &G, const T pr[8], Plasma<T> &P,
                                                   T ucon_out[4], T bcon_out[4]) {
-  T g00 = cvt<T>(G.g00), g01 = cvt<T>(G.g01), g03 = cvt<T>(G.g03), g11 = cvt<T>(G.g11), g13 = cvt<T>(G.g13),
-    g22 = cvt<T>(G.g22), g33 = cvt<T>(G.g33);
+  T g00 = cvtn<T, NARROW>(G.g00), g01 = cvtn<T, NARROW>(G.g01), g03 = cvtn<T, NARROW>(G.g03),
+    g11 = cvtn<T, NARROW>(G.g11), g13 = cvtn<T, NARROW>(G.g13), g22 = cvtn<T, NARROW>(G.g22),
+    g33 = cvtn<T, NARROW>(G.g33);
   T rho = pr[0], uu = pr[1];
   T U1 = pr[5], U2 = pr[6], U3 = pr[7];
   constexpr bool kF64 = sizeof(T) == 8;
-  T alpha = rsqrt(-cvt<T>(G.G00));
+  T alpha = rsqrt(-cvtn<T, NARROW>(G.G00));
   T q = g11 * U1 * U1 + g22 * U2 * U2 + g33 * U3 * U3 + (T)2 * g13 * U1 * U3;
   T rg = rsqrt((T)1 + q);                   // 1 / gamma
   T gamma = kF64 ? ((T)1 + q) * rg : sqrt((T)1 + q);
-  T u0 = gamma * (-cvt<T>(G.G00)) * alpha;   // gamma / alpha, alpha = (-g^tt)^(-1/2)
-  T u1 = U1 - gamma * alpha * cvt<T>(G.G01);
+  T u0 = gamma * (-cvtn<T, NARROW>(G.G00)) * alpha;   // gamma / alpha, alpha = (-g^tt)^(-1/2)
+  T u1 = U1 - gamma * alpha * cvtn<T, NARROW>(G.G01);
   T u2 = U2, u3 = U3;
   T uc0 = g00 * u0 + g01 * u1 + g03 * u3;
   T uc1 = g01 * u0 + g11 * u1 + g13 * u3;
@@ -1013,14 +1023,15 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
 template <typename S, typename W = double>
 __device__ __forceinline__ void coefficients32(const DevModel &m, const GeoT<S> &G, const S X[4], const S K[4],
                                                bool want_s, CoefT<W> &c) {
+  constexpr bool kSplit = std::is_same<W, float>::value;   // the split form's transport: narrow on integer pipes
   c.ana = c.ans = c.thetae = (W)0;
   float pr[8];
-  if (!interp_prims<float>(m, X, pr)) return;
+  if (!interp_prims<float, S, kSplit>(m, X, pr)) return;
   Plasma<float> P;
-  plasma_from_prims<float>(m, G, pr, P, nullptr, nullptr);
+  plasma_from_prims<float, S, kSplit>(m, G, pr, P, nullptr, nullptr);
   c.thetae = P.thetae;
   if (!P.on) return;
-  float kf[4] = {to_f(K[0]), to_f(K[1]), to_f(K[2]), to_f(K[3])};
+  float kf[4] = {f32_of<kSplit>(K[0]), f32_of<kSplit>(K[1]), f32_of<kSplit>(K[2]), f32_of<kSplit>(K[3])};
   float eps = -(kf[0] * P.ucov[0] + kf[1] * P.ucov[1] + kf[2] * P.ucov[2] + kf[3] * P.ucov[3]);
   if (!(eps > 0.0f)) return;
   // frequencies and emissivities span ~1e-40..1e40: keep the products in ranges float holds
@@ -1082,16 +1093,17 @@ struct CoefA {
 template <typename S>
 __device__ __forceinline__ void coefficients32_a(const DevModel &m, const GeoT<S> &G, const S X[4], const S K[4],
                                                  CoefA &a) {
+  constexpr bool kSplit = std::is_same<S, double>::value;   // FP64 geodesic: the split form with the network
   a.on = a.emit = false;
   a.thetae = a.ne = a.eps = a.nu9 = a.ana_k2 = 0.0f;
   a.in[0] = a.in[1] = a.in[2] = 0.0f;
   float pr[8];
-  if (!interp_prims<float>(m, X, pr)) return;
+  if (!interp_prims<float, S, kSplit>(m, X, pr)) return;
   Plasma<float> P;
-  plasma_from_prims<float>(m, G, pr, P, nullptr, nullptr);
+  plasma_from_prims<float, S, kSplit>(m, G, pr, P, nullptr, nullptr);
   a.thetae = P.thetae;
   if (!P.on) return;
-  float kf[4] = {to_f(K[0]), to_f(K[1]), to_f(K[2]), to_f(K[3])};
+  float kf[4] = {f32_of<kSplit>(K[0]), f32_of<kSplit>(K[1]), f32_of<kSplit>(K[2]), f32_of<kSplit>(K[3])};
   float eps = -(kf[0] * P.ucov[0] + kf[1] * P.ucov[1] + kf[2] * P.ucov[2] + kf[3] * P.ucov[3]);
   if (!(eps > 0.0f)) return;
   a.on = true;

@@ -103,7 +103,7 @@ __device__ __forceinline__ float narrow_f(double d) {
   if ((b & 0x7fffffffffffffffLL) == 0) return __uint_as_float(hi & 0x80000000u);
   return (float)d;
 }
-__device__ __forceinline__ float to_f(double x) { return narrow_f(x); }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
 __device__ __forceinline__ float to_f(df x) { return __fadd_rn(x.hi, x.lo); }
 __device__ __forceinline__ double sabs(double x) { return fabs(x); }
 __device__ __forceinline__ df sabs(df x) { return df_abs(x); }

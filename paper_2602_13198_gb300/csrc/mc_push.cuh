@@ -219,10 +219,10 @@ static __device__ void child_kinematics_f(const DevModel &m, const double Xe[4],
   metric_eval<false>(m, Xe[1], Xe[2], G);
   double Xc[4] = {Xe[0], fmin(fmax(Xe[1], m.x1_0), m.x1_hi), Xe[2], Xe[3]};
   float pr[8];
-  interp_prims<float>(m, Xc, pr);
+  interp_prims<float, double, true>(m, Xc, pr);
   Plasma<float> P;
   float ucon[4];
-  plasma_from_prims<float>(m, G, pr, P, ucon, nullptr);
+  plasma_from_prims<float, double, true>(m, G, pr, P, ucon, nullptr);
   float e[4][4];
   tetrad_scatter_f(G, ucon, e);
   const float k0 = (float)Ke[0], k1 = (float)Ke[1], k2 = (float)Ke[2], k3 = (float)Ke[3];
