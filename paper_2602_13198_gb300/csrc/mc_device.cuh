@@ -155,6 +155,29 @@ __device__ __forceinline__ void sincospi_t(const double *T, double x, double &s,
   c = fma(cj, ca, -(sj * sa));
 }
 
+// floor(f) and f - floor(f) of an FP64 index coordinate.  For 0 <= f < 2^30 the integer part is cut from
+// the mantissa bits (exact), leaving one FP64 subtraction for the fraction instead of a floor, two
+// conversions and a subtraction on the FP64 pipe; other arguments take floor().
+__device__ __forceinline__ int floor_frac(double f, double &frac) {
+  const long long b = __double_as_longlong(f);
+  const int e = (int)(b >> 52) - 1023;   // b >= 0 here: the unbiased exponent
+  if (b >= 0 && e < 30) {
+    if (e < 0) {
+      frac = f;
+      return 0;
+    }
+    const long long keep = ~((1LL << (52 - e)) - 1);
+    frac = f - __longlong_as_double(b & keep);
+    return (int)((((b & 0x000fffffffffffffLL) | 0x0010000000000000LL)) >> (52 - e));
+  }
+  const double fl = floor(f);
+  frac = f - fl;
+  return (int)fl;
+}
+
+// cell index and the fraction within it, FP64 coordinates
+__device__ __forceinline__ int zone_split(double f, double &frac) { return floor_frac(f, frac); }
+
 // ---------------------------------------------------------------- model view passed to kernels
 struct DevModel {
   // metric and units
@@ -510,10 +533,10 @@ __device__ __forceinline__ df stepsize<df>(const DevModel &m, const df X[4], con
 
 // ---------------------------------------------------------------- tables
 __device__ __forceinline__ double cubic_table(const double *t, int n, double x0, double inv_step, double x) {
-  double f = (x - x0) * inv_step;
-  int i = (int)floor(f);
-  i = max(1, min(i, n - 3));
-  double u = f - i;
+  double f = (x - x0) * inv_step, fr;
+  const int i0 = floor_frac(f, fr);
+  const int i = max(1, min(i0, n - 3));
+  const double u = (i == i0) ? fr : f - i;
   double y0 = t[i - 1], y1 = t[i], y2 = t[i + 1], y3 = t[i + 2];
   // 4-point Lagrange through nodes i-1 .. i+2 at offset u from node i
   double um1 = u + 1.0, u1 = u - 1.0, u2 = u - 2.0;
@@ -525,9 +548,9 @@ __device__ __forceinline__ double F_of_lnK(const DevModel &m, double lnK) {
   if (lnK >= kFLnK1) return 0.0;
   if (lnK <= kFLnK0) {
     // small-K power law F ~ K^(1/3) continued from the first node
-    return exp(m.lnF[0] + (lnK - kFLnK0) / 3.0);
+    return exp_t(m.ftab, m.lnF[0] + (lnK - kFLnK0) / 3.0);
   }
-  return exp(cubic_table(m.lnF, m.nF, kFLnK0, 1.0 / kFStep, lnK));
+  return exp_t(m.ftab, cubic_table(m.lnF, m.nF, kFLnK0, 1.0 / kFStep, lnK));
 }
 
 __device__ __forceinline__ double K2_of(const DevModel &m, double thetae) {
@@ -560,8 +583,11 @@ __device__ __forceinline__ double hot_lookup_ln(const DevModel &m, double lt, do
   double fe = (le - kHotLE0) * se;
   ft = dmin_nn(dmax0(ft), (double)(kHotNT - 1));
   fe = dmin_nn(dmax0(fe), (double)(kHotNE - 1));
-  int i = min((int)ft, kHotNT - 2), j = min((int)fe, kHotNE - 2);
-  double a = ft - i, b = fe - j;
+  double a, b;
+  const int i0 = floor_frac(ft, a), j0 = floor_frac(fe, b);
+  const int i = min(i0, kHotNT - 2), j = min(j0, kHotNE - 2);
+  if (i != i0) a = 1.0;   // at the last node (ft = kHotNT - 1)
+  if (j != j0) b = 1.0;
   const double *h = m.hot;
   double v00 = h[i * kHotNE + j], v01 = h[i * kHotNE + j + 1];
   double v10 = h[(i + 1) * kHotNE + j], v11 = h[(i + 1) * kHotNE + j + 1];
@@ -687,7 +713,7 @@ __device__ __forceinline__ double zone_E(const DevModel &m, int64_t z, double pr
   double e = (pref == 0.0) ? 0.0
              : (m.kappa > 0.0) ? pref * kap_interp(m.kapI, m.lnu_min + j * m.dlnu - lnuc, m.zlnw[z])
                                : pref * F_of_lnK(m, m.lnu_min + j * m.dlnu - lnuc);
-  if (m.brems && m.zbq[z] > 0.0) e += m.zbq[z] * exp(-exp(m.lnu_min + j * m.dlnu) / m.zbnt[z]);
+  if (m.brems && m.zbq[z] > 0.0) e += m.zbq[z] * exp_t(m.ftab, -exp_t(m.ftab, m.lnu_min + j * m.dlnu) / m.zbnt[z]);
   return e;
 }
 
@@ -698,6 +724,13 @@ __device__ __forceinline__ double Gsyn(double X) {
   double x3 = x6 * x6;
   double t = x6 * x6 * x6 + 1.8877486253633870 * x6;   // 2^(11/12)
   return t * t * exp(-x3);
+}
+// the same in the emission sampler: the Newton sixth root and the table-driven exponential
+__device__ __forceinline__ double Gsyn_t(const double *T, double X) {
+  double x6 = pow_sixth(X);
+  double x3 = x6 * x6;
+  double t = x6 * x3 + 1.8877486253633870 * x6;   // 2^(11/12)
+  return t * t * exp_t(T, -x3);
 }
 
 // ---------------------------------------------------------------- fluid (sections 2.5-2.7)
@@ -773,16 +806,14 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   R di, dj;
   {
     const R f1 = zone_coord_r<F32IDX>(m, X, 1);
-    i = zone_floor(f1);
-    di = f1 - i;
+    i = zone_split(f1, di);
     if (m.n1 == 1) { i = 0; di = 0; }
     else if (i < 0) { i = 0; di = 0; }
     else if (i > m.n1 - 2) { i = m.n1 - 2; di = 1; }
   }
   {
     const R f2 = zone_coord_r<F32IDX>(m, X, 2);
-    j = zone_floor(f2);
-    dj = f2 - j;
+    j = zone_split(f2, dj);
     if (m.n2 == 1) { j = 0; dj = 0; }
     else if (j < 0) { j = 0; dj = 0; }
     else if (j > m.n2 - 2) { j = m.n2 - 2; dj = 1; }
@@ -791,8 +822,7 @@ __device__ __forceinline__ bool interp_prims(const DevModel &m, const S X[4], T 
   R dk = 0;
   if (m.n3 > 1) {
     const R f3 = zone_coord_r<F32IDX>(m, X, 3);
-    const int ki = zone_floor(f3);
-    dk = f3 - (R)ki;
+    const int ki = zone_split(f3, dk);
     long long kk = ki;
     k0 = (int)(((kk % m.n3) + m.n3) % m.n3);
     k1 = (k0 + 1) % m.n3;

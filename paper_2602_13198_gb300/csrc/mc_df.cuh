@@ -156,6 +156,12 @@ __device__ __forceinline__ int zone_floor(float f) {
   rint_shift(__fsub_rn(f, 0.5f), k);
   return k;
 }
+// cell index and the fraction within it, FP32 coordinates
+__device__ __forceinline__ int zone_split(float f, float &frac) {
+  const int k = zone_floor(f);
+  frac = f - k;
+  return k;
+}
 
 // 2^e for -126 <= e <= 127, from its bit pattern
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }

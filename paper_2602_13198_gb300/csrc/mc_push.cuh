@@ -108,7 +108,7 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
   const double jsyn = (pref == 0.0) ? 0.0
                       : (m.kappa > 0.0) ? pref * kap_interp(m.kapI, lnu - lnuc, m.zlnw[z])
                                         : pref * F_of_lnK(m, lnu - lnuc);
-  const double jbr = (m.brems && m.zbq[z] > 0.0) ? m.zbq[z] * exp(-exp(lnu) / m.zbnt[z]) : 0.0;
+  const double jbr = (m.brems && m.zbq[z] > 0.0) ? m.zbq[z] * exp_t(m.ftab, -exp_t(m.ftab, lnu) / m.zbnt[z]) : 0.0;
   // with bremsstrahlung on, the process is drawn in proportion to the two angle-integrated
   // emissivities; bremsstrahlung is isotropic
   bool synchrotron = true;
@@ -129,14 +129,14 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
     if (it == 100000) ls.rejcap++;
   } else if (synchrotron) {
     // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
-    double K0 = exp(lnu - lnuc);
-    double jmax = Gsyn(K0);
+    double K0 = exp_t(m.ftab, lnu - lnuc);
+    double jmax = Gsyn_t(m.ftab, K0);
     for (it = 0; it < 100000; ++it) {
       double r3 = rng_u(p.s, m.seed);
       cth = 2.0 * r3 - 1.0;
       double r4 = rng_u(p.s, m.seed);
       double sth = sqrt(1.0 - cth * cth);
-      if (r4 * jmax < sth * Gsyn(K0 / sth)) break;
+      if (r4 * jmax < sth * Gsyn_t(m.ftab, K0 / sth)) break;
     }
     if (it == 100000) ls.rejcap++;
   } else {
@@ -144,7 +144,7 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
   }
   double phi = 2.0 * rng_u(p.s, m.seed);   // units of pi
   double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
-  double eps = exp(lnu) * (kHPL / (kME * kCL * kCL));
+  double eps = exp_t(m.ftab, lnu) * (kHPL / (kME * kCL * kCL));
   // plasma at the zone centre
   int64_t iz = z / ((int64_t)m.n2 * m.n3), jz = (z / m.n3) % m.n2, kz = z % m.n3;
   double X[4] = {0.0, m.x1_0 + (iz + 0.5) * m.dx1, m.x2_0 + (jz + 0.5) * m.dx2, m.x3_0 + (kz + 0.5) * m.dx3};
