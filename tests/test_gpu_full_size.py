@@ -3,7 +3,8 @@ that hold at any size (the oracle cannot build the weights of a 4.7-million-zone
 in test time; its parity with the device is tested on the same workloads at small sizes):
   - 2-D torus (a = 0.9375, 256 x 128, N_s = 1e7) with the coefficient surrogate;
   - 3-D snapshot (a = 0.5, 288 x 128 x 128 FP32, N_s = 1e8, 6 inclination bins) in mixed precision
-    with the surrogate.
+    with the surrogate, and in the configuration's stated form: the split precision (FP64 geodesic,
+    FP32 rest) with the surrogate.
 Each named form's spectrum agrees with the plain FP64 run of the same job (FP64 itself is parity-
 tested against the oracle) within 1 % in total luminosity and max(1 %, 3 sigma) per bin."""
 import numpy as np
@@ -61,11 +62,13 @@ def test_torus_2d_full_size_with_surrogate(weights):
     print("2-D torus, surrogate vs FP64: total luminosity %.2e, %d superphotons" % (e, st1["n_emit"] + st1["n_child"]))
 
 
-def test_snapshot_3d_full_size_mixed_with_surrogate(weights):
+def test_snapshot_3d_full_size_mixed_and_split_with_surrogate(weights):
     p, g = synth.torus3d()
     assert (g["n1"], g["n2"], g["n3"]) == (288, 128, 128) and g["prim"].dtype == np.float32 and p["n_incl"] == 6
     st0, s0 = run(p, g, 1e8, 1, "fp64")
-    st1, s1 = run(p, g, 1e8, 1, "mixed", weights)
-    assert s1.shape[0] == 6
-    e = compare(st0, s0, st1, s1, 1e8)
-    print("3-D snapshot, mixed + surrogate vs FP64: total luminosity %.2e, %d superphotons" % (e, st1["n_emit"] + st1["n_child"]))
+    for form in ("mixed", "split"):
+        st1, s1 = run(p, g, 1e8, 1, form, weights)
+        assert s1.shape[0] == 6
+        e = compare(st0, s0, st1, s1, 1e8)
+        print("3-D snapshot, %s + surrogate vs FP64: total luminosity %.2e, %d superphotons"
+              % (form, e, st1["n_emit"] + st1["n_child"]))
