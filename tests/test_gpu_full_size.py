@@ -72,3 +72,29 @@ def test_snapshot_3d_full_size_mixed_and_split_with_surrogate(weights):
         e = compare(st0, s0, st1, s1, 1e8)
         print("3-D snapshot, %s + surrogate vs FP64: total luminosity %.2e, %d superphotons"
               % (form, e, st1["n_emit"] + st1["n_child"]))
+
+
+def test_snapshot_3d_full_size_sampled_against_oracle():
+    """The benchmark's main workload in its launch configuration (3-D snapshot, N_s = 1e8, shard 0 of 8,
+    plain FP64) against the oracle: zone counts bit-exact over all 4.7 M zones, the shard's primaries
+    the same, and per-superphoton end states of 400 sampled uids of the shard within 1e-9 (the oracle
+    traces them one by one)."""
+    from helpers import compare_logs, oracle_model
+    from paper_2602_13198_gb300 import mc
+    p, g = synth.torus3d()
+    m = mc.Model(p, precision="fp64")
+    m.set_grid(g)
+    st = m.run(1e8, 1, shard=0, n_shards=8)
+    om = oracle_model(p, dict(g, prim=np.asarray(g["prim"], dtype=np.float64)))
+    tot = om.prepare(1e8, 1)
+    assert st["n_total"] == tot
+    assert np.array_equal(m.zone_counts(), om.zones()["counts"])
+    u0, u1 = mc.shard_bounds(tot, 0, 8)
+    assert st["n_emit"] == u1 - u0
+    rng = np.random.default_rng(11)
+    uids = np.sort(rng.choice(np.arange(u0, u1), size=400, replace=False))
+    r = compare_logs(m.trace(1e8, 1, uids), om.run(uids=uids, log=True)["log"])
+    assert r["n"] >= 0.99 * len(uids)
+    assert len(r["flips"]) <= 2
+    assert r["worst"]["X"] < 1e-9 and r["worst"]["K"] < 1e-9 and r["worst"]["w"] < 1e-7, r["worst"]
+
