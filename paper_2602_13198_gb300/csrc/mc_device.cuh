@@ -469,44 +469,45 @@ __device__ __forceinline__ double dot(const Geo &G, const double a[4], const dou
 // dk^mu/dlambda = -Gamma^mu_ab k^a k^b = -g^{mu nu} (k^1 (d1 g k)_nu + k^2 (d2 g k)_nu - 1/2 d_nu g_ab k^a k^b)
 template <bool KERR = true, typename S = double>
 __device__ __forceinline__ void accel(const GeoT<S> &G, const S k[4], S A[4]) {
+  // sdot: the plain sums of products for double, one-pass accumulations for df
   if constexpr (!KERR) {
     // a = 0: d103 = d113 = d2(0,1,3) = G13 = 0
-    S p0 = G.d100 * k[0] + G.d101 * k[1];
-    S p1 = G.d101 * k[0] + G.d111 * k[1];
+    S p0 = sdot(G.d100, k[0], G.d101, k[1]);
+    S p1 = sdot(G.d101, k[0], G.d111, k[1]);
     S p2 = G.d122 * k[2];
     S p3 = G.d133 * k[3];
     S q2 = G.d222 * k[2];
     S q3 = G.d233 * k[3];
-    S kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
-    S kDk2 = k[2] * q2 + k[3] * q3;
+    S kDk1 = sdot(k[0], p0, k[1], p1, k[2], p2, k[3], p3);
+    S kDk2 = sdot(k[2], q2, k[3], q3);
     S w0 = k[1] * p0;
-    S w1 = k[1] * p1 - 0.5f * kDk1;
-    S w2 = k[1] * p2 + k[2] * q2 - 0.5f * kDk2;
-    S w3 = k[1] * p3 + k[2] * q3;
-    A[0] = -(G.G00 * w0 + G.G01 * w1);
-    A[1] = -(G.G01 * w0 + G.G11 * w1);
+    S w1 = sdot_mh(k[1], p1, kDk1);
+    S w2 = sdot_mh(k[1], p2, k[2], q2, kDk2);
+    S w3 = sdot(k[1], p3, k[2], q3);
+    A[0] = -sdot(G.G00, w0, G.G01, w1);
+    A[1] = -sdot(G.G01, w0, G.G11, w1);
     A[2] = -(G.G22 * w2);
     A[3] = -(G.G33 * w3);
     return;
   }
-  S p0 = G.d100 * k[0] + G.d101 * k[1] + G.d103 * k[3];
-  S p1 = G.d101 * k[0] + G.d111 * k[1] + G.d113 * k[3];
+  S p0 = sdot(G.d100, k[0], G.d101, k[1], G.d103, k[3]);
+  S p1 = sdot(G.d101, k[0], G.d111, k[1], G.d113, k[3]);
   S p2 = G.d122 * k[2];
-  S p3 = G.d103 * k[0] + G.d113 * k[1] + G.d133 * k[3];
-  S q0 = G.d200 * k[0] + G.d201 * k[1] + G.d203 * k[3];
-  S q1 = G.d201 * k[0] + G.d211 * k[1] + G.d213 * k[3];
+  S p3 = sdot(G.d103, k[0], G.d113, k[1], G.d133, k[3]);
+  S q0 = sdot(G.d200, k[0], G.d201, k[1], G.d203, k[3]);
+  S q1 = sdot(G.d201, k[0], G.d211, k[1], G.d213, k[3]);
   S q2 = G.d222 * k[2];
-  S q3 = G.d203 * k[0] + G.d213 * k[1] + G.d233 * k[3];
-  S kDk1 = k[0] * p0 + k[1] * p1 + k[2] * p2 + k[3] * p3;
-  S kDk2 = k[0] * q0 + k[1] * q1 + k[2] * q2 + k[3] * q3;
-  S w0 = k[1] * p0 + k[2] * q0;
-  S w1 = k[1] * p1 + k[2] * q1 - 0.5f * kDk1;
-  S w2 = k[1] * p2 + k[2] * q2 - 0.5f * kDk2;
-  S w3 = k[1] * p3 + k[2] * q3;
-  A[0] = -(G.G00 * w0 + G.G01 * w1);
-  A[1] = -(G.G01 * w0 + G.G11 * w1 + G.G13 * w3);
+  S q3 = sdot(G.d203, k[0], G.d213, k[1], G.d233, k[3]);
+  S kDk1 = sdot(k[0], p0, k[1], p1, k[2], p2, k[3], p3);
+  S kDk2 = sdot(k[0], q0, k[1], q1, k[2], q2, k[3], q3);
+  S w0 = sdot(k[1], p0, k[2], q0);
+  S w1 = sdot_mh(k[1], p1, k[2], q1, kDk1);
+  S w2 = sdot_mh(k[1], p2, k[2], q2, kDk2);
+  S w3 = sdot(k[1], p3, k[2], q3);
+  A[0] = -sdot(G.G00, w0, G.G01, w1);
+  A[1] = -sdot(G.G01, w0, G.G11, w1, G.G13, w3);
   A[2] = -(G.G22 * w2);
-  A[3] = -(G.G13 * w1 + G.G33 * w3);
+  A[3] = -sdot(G.G13, w1, G.G33, w3);
 }
 
 // Step size (reading; the paper gives none): each internal coordinate moves at most eps_geo of

@@ -122,6 +122,110 @@ template <typename S> __host__ __device__ constexpr S cst(double x);
 template <> __host__ __device__ constexpr double cst<double>(double x) { return x; }
 template <> __host__ __device__ constexpr df cst<df>(double x) { return df_const(x); }
 
+// Sums of products a0 b0 + a1 b1 + ... in one pass.  Each high-part product is split exactly (FMA),
+// the high parts are summed with two-sum, and every error term (product errors, cross terms, sum
+// errors) collects in one FP32 accumulator; a single renormalisation closes the sum.  Per term 12
+// FP32 operations, where a product and a Dekker sum take 18; the error is bounded normwise like the
+// sum's, by a few 2^-48 sum |a_i b_i|.
+struct DotAcc {
+  float s, e;
+};
+__device__ __forceinline__ DotAcc dot_first(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return {p, e};
+}
+__device__ __forceinline__ void dot_add(DotAcc &d, df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const df t = df_two_sum(d.s, p);
+  d.s = t.hi;
+  d.e = __fadd_rn(d.e, __fadd_rn(t.lo, e));
+}
+__device__ __forceinline__ void dot_add(DotAcc &d, df x) {   // a term that is already a df value
+  const df t = df_two_sum(d.s, x.hi);
+  d.s = t.hi;
+  d.e = __fadd_rn(d.e, __fadd_rn(t.lo, x.lo));
+}
+__device__ __forceinline__ df dot_end(DotAcc d) { return df_fast_two_sum(d.s, d.e); }
+// x / 2, exact (barring underflow)
+__device__ __forceinline__ df df_half(df x) { return {__fmul_rn(x.hi, 0.5f), __fmul_rn(x.lo, 0.5f)}; }
+
+// The scalar-generic forms: for double the plain expression as written (so the FP64 path keeps its
+// arithmetic), for df the one-pass accumulation.
+__device__ __forceinline__ double sdot(double a0, double b0, double a1, double b1) { return a0 * b0 + a1 * b1; }
+__device__ __forceinline__ double sdot(double a0, double b0, double a1, double b1, double a2, double b2) {
+  return a0 * b0 + a1 * b1 + a2 * b2;
+}
+__device__ __forceinline__ double sdot(double a0, double b0, double a1, double b1, double a2, double b2, double a3,
+                                       double b3) {
+  return a0 * b0 + a1 * b1 + a2 * b2 + a3 * b3;
+}
+// a0 b0 + a1 b1 - c / 2 and a0 b0 - c / 2
+__device__ __forceinline__ double sdot_mh(double a0, double b0, double a1, double b1, double c) {
+  return a0 * b0 + a1 * b1 - 0.5f * c;
+}
+__device__ __forceinline__ double sdot_mh(double a0, double b0, double c) { return a0 * b0 - 0.5f * c; }
+__device__ __forceinline__ df sdot(df a0, df b0, df a1, df b1) {
+  DotAcc d = dot_first(a0, b0);
+  dot_add(d, a1, b1);
+  return dot_end(d);
+}
+__device__ __forceinline__ df sdot(df a0, df b0, df a1, df b1, df a2, df b2) {
+  DotAcc d = dot_first(a0, b0);
+  dot_add(d, a1, b1);
+  dot_add(d, a2, b2);
+  return dot_end(d);
+}
+__device__ __forceinline__ df sdot(df a0, df b0, df a1, df b1, df a2, df b2, df a3, df b3) {
+  DotAcc d = dot_first(a0, b0);
+  dot_add(d, a1, b1);
+  dot_add(d, a2, b2);
+  dot_add(d, a3, b3);
+  return dot_end(d);
+}
+__device__ __forceinline__ df sdot_mh(df a0, df b0, df a1, df b1, df c) {
+  DotAcc d = dot_first(a0, b0);
+  dot_add(d, a1, b1);
+  dot_add(d, -df_half(c));
+  return dot_end(d);
+}
+__device__ __forceinline__ df sdot_mh(df a0, df b0, df c) {
+  DotAcc d = dot_first(a0, b0);
+  dot_add(d, -df_half(c));
+  return dot_end(d);
+}
+
+// Velocity-Verlet updates x + k dl + a dl^2 / 2, k + a dl and k + (a + a') dl / 2, as sums of
+// products for df
+__device__ __forceinline__ double verlet_x(double x, double k, double a, double dl) {
+  return x + k * dl + 0.5f * a * dl * dl;
+}
+__device__ __forceinline__ double verlet_k(double k, double a, double dl) { return k + a * dl; }
+__device__ __forceinline__ double verlet_k2(double k, double a, double a1, double dl) {
+  return k + 0.5f * (a + a1) * dl;
+}
+__device__ __forceinline__ df verlet_x(df x, df k, df a, df dl) {
+  DotAcc d{x.hi, x.lo};
+  dot_add(d, k, dl);
+  dot_add(d, df_half(a) * dl, dl);
+  return dot_end(d);
+}
+__device__ __forceinline__ df verlet_k(df k, df a, df dl) {
+  DotAcc d{k.hi, k.lo};
+  dot_add(d, a, dl);
+  return dot_end(d);
+}
+__device__ __forceinline__ df verlet_k2(df k, df a, df a1, df dl) {
+  DotAcc d{k.hi, k.lo};
+  dot_add(d, df_half(a + a1), dl);
+  return dot_end(d);
+}
+
 template <typename S> __device__ __forceinline__ S from_d(double x);
 template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
 template <> __device__ __forceinline__ df from_d<df>(double x) { return df_from(x); }

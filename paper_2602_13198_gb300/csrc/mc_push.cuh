@@ -568,8 +568,8 @@ static __device__ bool step(const DevModel &m, const PushIO &io, PhF<PREC> &p, L
   for (int q = 0; q < 4; ++q) {
     X0[q] = p.X[q];
     K0[q] = p.K[q];
-    p.X[q] = X0[q] + K0[q] * dl + 0.5f * p.A[q] * dl * dl;
-    Kp[q] = K0[q] + p.A[q] * dl;
+    p.X[q] = verlet_x(X0[q], K0[q], p.A[q], dl);
+    Kp[q] = verlet_k(K0[q], p.A[q], dl);
   }
   GeoT<S> G;
   metric_eval<true, KERR>(m, p.X[1], p.X[2], G);
@@ -581,7 +581,7 @@ static __device__ bool step(const DevModel &m, const PushIO &io, PhF<PREC> &p, L
     decltype(vmag(dl)) num = 0, den = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      Kn[q] = K0[q] + 0.5f * (p.A[q] + An[q]) * dl;
+      Kn[q] = verlet_k2(K0[q], p.A[q], An[q], dl);
       num += vdiff(Kn[q], Kp[q]);
       den += vmag(Kn[q]);
     }
@@ -623,8 +623,8 @@ static __device__ int step_free(const DevModel &m, const PushIO &io, PhF<PREC> &
   S Xn[4], Kp[4], An[4], Kn[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    Xn[q] = p.X[q] + p.K[q] * dl + 0.5f * p.A[q] * dl * dl;
-    Kp[q] = p.K[q] + p.A[q] * dl;
+    Xn[q] = verlet_x(p.X[q], p.K[q], p.A[q], dl);
+    Kp[q] = verlet_k(p.K[q], p.A[q], dl);
   }
   if (in_grid(m, Xn)) return 2;
   GeoT<S> G;
@@ -636,7 +636,7 @@ static __device__ int step_free(const DevModel &m, const PushIO &io, PhF<PREC> &
     decltype(vmag(dl)) num = 0, den = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      Kn[q] = p.K[q] + 0.5f * (p.A[q] + An[q]) * dl;
+      Kn[q] = verlet_k2(p.K[q], p.A[q], An[q], dl);
       num += vdiff(Kn[q], Kp[q]);
       den += vmag(Kn[q]);
     }
@@ -763,8 +763,8 @@ static __device__ void step_sur_a(const DevModel &m, PhT<S, W> &p, SurCarry<S> &
   for (int q = 0; q < 4; ++q) {
     sc.X0[q] = p.X[q];
     sc.K0[q] = p.K[q];
-    p.X[q] = sc.X0[q] + sc.K0[q] * dl + 0.5f * p.A[q] * dl * dl;
-    Kp[q] = sc.K0[q] + p.A[q] * dl;
+    p.X[q] = verlet_x(sc.X0[q], sc.K0[q], p.A[q], dl);
+    Kp[q] = verlet_k(sc.K0[q], p.A[q], dl);
   }
   GeoT<S> G;
   metric_eval<true>(m, p.X[1], p.X[2], G);
@@ -775,7 +775,7 @@ static __device__ void step_sur_a(const DevModel &m, PhT<S, W> &p, SurCarry<S> &
     decltype(vmag(dl)) num = 0, den = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      Kn[q] = sc.K0[q] + 0.5f * (p.A[q] + An[q]) * dl;
+      Kn[q] = verlet_k2(sc.K0[q], p.A[q], An[q], dl);
       num += vdiff(Kn[q], Kp[q]);
       den += vmag(Kn[q]);
     }
