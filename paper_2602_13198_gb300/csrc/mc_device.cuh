@@ -333,6 +333,96 @@ __device__ __forceinline__ void sincos_small(double d, double &s, double &c) {
   c = 1.0 + d2 * (c2 + d2 * (c4 + d2 * (c6 + d2 * (c8 + d2 * (c10 + d2 * (c12 + d2 * (c14 + d2 * c16)))))));
 }
 
+// The double-float form of the metric below (after r, sin, cos of theta and the theta map): the same
+// quantities, with the shared factors formed once, the factors 2 and 4 applied exactly, and the sums of
+// products as one-pass accumulations (sdot).  The grouping differs from the FP64 form's; the values
+// agree to double-float accuracy.
+__device__ __forceinline__ df df_twice(df x) { return {__fmul_rn(x.hi, 2.0f), __fmul_rn(x.lo, 2.0f)}; }
+template <bool DERIV, bool KERR>
+__device__ __forceinline__ void metric_rest_df(df r, df s, df c, df dth, df d2th, df a, df M, df a2, GeoT<df> &G) {
+  const df zero = df_const(0.0);
+  const df s2 = s * s, r2 = r * r;
+  const df sig = KERR ? sdot(r, r, a2, c * c) : r2;   // r^2 + a^2 cos^2
+  const df rs = r * s2;
+  const df Q = df_rcp(sig * rs * dth);   // one division for 1/Sigma, 1/r, 1/sin^2 and 1/(dtheta/dx2)
+  const df Qd = Q * dth, sigs2 = sig * s2;
+  const df isig = Qd * rs, ir = Qd * sigs2, is2 = Qd * sig * r, idth = Q * sig * rs;
+  const df M2 = df_twice(M), M2r = M2 * r;
+  const df f = M2r * isig, opf = f + 1.0f;
+  const df as2 = KERR ? a * s2 : zero, a2s2 = KERR ? a2 * s2 : zero;
+  const df Grp = KERR ? -(as2 * opf) : zero;
+  const df dth2 = dth * dth;
+  G.r = r;
+  G.sth = s;
+  G.cth = c;
+  G.g00 = f - 1.0f;
+  G.g01 = f * r;
+  G.g03 = KERR ? -(as2 * f) : zero;
+  G.g11 = opf * r2;
+  G.g13 = Grp * r;
+  G.g22 = sig * dth2;
+  if constexpr (KERR) {
+    DotAcc d{sig.hi, sig.lo};
+    dot_add(d, a2s2, opf);
+    G.g33 = s2 * dot_end(d);   // sin^2 (Sigma + a^2 sin^2 (1 + f))
+  } else {
+    G.g33 = sigs2;
+  }
+  G.G00 = -opf;
+  G.G01 = f * ir;
+  {
+    DotAcc d = dot_first(r, r - M2);   // Delta = r (r - 2M) + a^2
+    if (KERR) dot_add(d, a2);
+    G.G11 = dot_end(d) * isig * (ir * ir);
+  }
+  G.G13 = KERR ? a * isig * ir : zero;
+  G.G22 = isig * (idth * idth);
+  G.G33 = isig * is2;
+  if (!DERIV) return;
+  const df isig2 = isig * isig;
+  const df dfr = M2 * (sig - df_twice(r2)) * isig2;   // d f / d r
+  const df rdfr = r * dfr;
+  G.d100 = rdfr;
+  G.d101 = r * (rdfr + f);
+  G.d111 = r2 * (rdfr + df_twice(opf));
+  G.d122 = df_twice(r2) * dth2;
+  if constexpr (!KERR) {
+    G.d103 = G.d113 = zero;
+    G.d133 = df_twice(r * rs);
+    G.d200 = G.d201 = G.d203 = G.d211 = G.d213 = zero;
+    G.d222 = df_twice(sig * dth) * d2th;
+    G.d233 = dth * (df_twice(s * c) * sig);
+    return;
+  }
+  const df sc2 = df_twice(s * c);   // 2 sin cos
+  const df dft = df_twice(M2r * isig2 * (a2 * s * c));   // d f / d theta = 4 M r a^2 s c / Sigma^2
+  const df dGp_r = -(as2 * dfr);   // d g_tphi / dr = d g_rphi / dr
+  const df dGtp_t = -(a * sdot(dft, s2, f, sc2));
+  const df dGrp_t = -(a * sdot(sc2, opf, s2, dft));
+  DotAcc dr{df_twice(rs).hi, df_twice(rs).lo};   // d g_phph / dr = 2 r s^2 + a^2 s^4 df/dr
+  dot_add(dr, a2s2 * s2, dfr);
+  const df dGpp_r = dot_end(dr);
+  // d g_phph / dtheta = 2 s c (Sigma - a^2 s^2) + a^2 s^2 (4 s c (1 + f) + s^2 df/dtheta)
+  const df dGpp_t = sdot(sc2, sig - a2s2, a2s2, sdot(df_twice(sc2), opf, s2, dft));
+  // d/dx1 = r d/dr
+  G.d103 = r * dGp_r;
+  {
+    DotAcc d{Grp.hi, Grp.lo};
+    dot_add(d, r, dGp_r);
+    G.d113 = r * dot_end(d);
+  }
+  G.d133 = r * dGpp_r;
+  // d/dx2 = dth d/dtheta
+  const df d200 = dth * dft;
+  G.d200 = d200;
+  G.d201 = d200 * r;
+  G.d203 = dth * dGtp_t;
+  G.d211 = d200 * r2;
+  G.d213 = dth * dGrp_t * r;
+  G.d222 = dth * sdot(-df_twice(a2 * s * c), dth2, df_twice(sig), d2th);
+  G.d233 = dth * dGpp_t;
+}
+
 // Metric, inverse metric and (DERIV) x1/x2 derivatives at (x1, x2).  theta = pi x2 + delta with
 // delta = (1-h)/2 sin(2 pi x2): sin and cos of theta come from sincospi(x2) and the series of the
 // small angle delta (|delta| < 1/2 for h in (0, 1]) by angle addition.
@@ -354,11 +444,13 @@ __device__ __forceinline__ void metric_eval(const DevModel &m, S x1s, S x2s, Geo
       s = sp;
       c = cp;
     } else {
-      const df s2x = (sp * cp) * 2.0f, c2x = (cp - sp) * (cp + sp);   // sin, cos of 2 pi x2
+      const df s2x = df_twice(sp * cp), c2x = (cp - sp) * (cp + sp);   // sin, cos of 2 pi x2
       dth = m.dpi2hh * c2x + kPiS;
       d2th = m.dd2th * s2x;
       df_sincospi(x2s + m.dhh_pi * s2x, m.dtab, s, c);
     }
+    metric_rest_df<DERIV, KERR>(r, s, c, dth, d2th, a, M, a2, G);
+    return;
   } else {
     const double x1 = x1s, x2 = x2s;
     r = exp_t(m.ftab, x1);
