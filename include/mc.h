@@ -171,8 +171,9 @@ int mc_set_grid(mc_ctx *c, const mc_grid_desc *g);
  * work on `stream` is complete (it reads the counters back).  stats may be NULL.
  * A scattered generation that exceeds the queues makes the call grow them and start again
  * (same result: every superphoton has its own counter-based stream), up to three times while
- * device memory allows.  Errors: STATE (no grid), INVALID_ARG, QUEUE_OVERFLOW (the queues could
- * not grow enough; results invalid), OOM, CUDA. */
+ * device memory allows.  Errors: STATE (no grid, or the surrogate on without trained weights),
+ * INVALID_ARG, QUEUE_OVERFLOW (the queues could not grow enough; results invalid), TIMEOUT (a
+ * tensor-core wait of the surrogate ran out, see mc_set_wait_limit), NAN_INPUT, OOM, CUDA. */
 int mc_run(mc_ctx *c, double n_s, uint64_t seed, int64_t shard, int64_t n_shards, void *stream,
            mc_run_stats *stats);
 
@@ -292,7 +293,8 @@ int mc_surrogate_infer(mc_ctx *c, const float *x, float *y, int64_t n, int tenso
  * configuration.  State (queues, graph, tuning) is kept by ctxs[0].  A scattered generation larger
  * than the pool makes the batch run again with a pool twice as large (same result; up to two times).
  * Errors: INVALID_ARG, SIZE (more than 64 models, or more transport phases than one launch holds),
- * STATE, QUEUE_OVERFLOW (the pool cannot grow further), TIMEOUT (grid barrier), OOM, CUDA. */
+ * STATE, QUEUE_OVERFLOW (the pool cannot grow further), TIMEOUT (grid barrier or tensor-core wait), OOM,
+ * CUDA. */
 #define MC_BATCH_AUTOTUNE 1
 #define MC_BATCH_GRAPH 2
 int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint64_t *seeds, int flags, void *stream,
@@ -302,9 +304,12 @@ int mc_run_batch(mc_ctx **ctxs, int n, const double *n_s, const uint64_t *seeds,
  * run led by c (ctxs[0] of mc_run_batch); default 120.  A wait that runs out raises an error bit on
  * the device; every CTA then leaves the kernel at its next barrier, and mc_run_batch returns
  * MC_ERR_TIMEOUT with the context still usable (the next call starts from reset counters).  The
- * limit is part of a captured batch graph's key, so changing it re-captures.  Not in the paper: a
- * guard of this library's persistent launch (section 3 launches one kernel per stage).
- * Errors: INVALID_ARG (c NULL, or seconds outside [1e-9, 3600]). */
+ * limit is part of a captured batch graph's key, so changing it re-captures.  The same limit, capped
+ * at 1 s, bounds each wait of the surrogate network for its tensor-core products (mc_run,
+ * mc_run_batch and mc_surrogate_infer with the surrogate on): a wait that runs out still lets the
+ * products in flight complete before the kernel goes on, and the call returns MC_ERR_TIMEOUT.  Not
+ * in the paper: a guard of this library's persistent and tensor-core launches (section 3 launches
+ * one kernel per stage).  Errors: INVALID_ARG (c NULL, or seconds outside [1e-9, 3600]). */
 int mc_set_wait_limit(mc_ctx *c, double seconds);
 
 /* Releases the context and all its device memory.  NULL is a no-op. */

@@ -32,12 +32,6 @@ struct BatchIO {
   double timeout_ns;
 };
 
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Grid-wide barrier (all CTAs are co-resident under the cooperative launch).  A CTA waits at most
 // timeout_ns; on timeout it raises bit 2 of the error word and every CTA leaves the kernel at its
 // next barrier.  Returns false when the kernel must stop.

@@ -307,6 +307,7 @@ mcgb::SurrogateView surrogate_view(const mc_ctx *c) {
   v.packed = c->sur_packed;
   v.bias = c->sur_bias;
   v.err = c->sur_err;
+  v.wait_ns = std::min(c->wait_ns, 1e9);   // a completion takes microseconds: at most 1 s
   return v;
 }
 

@@ -43,6 +43,7 @@ struct SurrogateView {
   const unsigned char *packed;   // kPackedBytes of BF16 tiles
   const float *bias;             // b1[64] b2[64] b3[3] (FP32)
   unsigned int *err;             // timeout flag
+  double wait_ns;                // limit on each tensor-core completion wait (ns)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,11 +92,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; on timeout the error flag is set and false returned.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, unsigned int *err) {
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase (the completion of MMAs this CTA issued).  A wait that lasts
+// longer than wait_ns (by the global nanosecond timer, read around each poll) sets bit 0 of the error
+// flag and returns false, but only once the MMAs in flight have completed (a second wait of at most
+// 2^22 polls; bit 1 if that one runs out too), so that the caller may reuse their operand tiles and
+// free the tensor memory.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, unsigned int *err, double wait_ns) {
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    const bool done = mbar_try_wait(mbar, parity);
+    if ((double)(globaltimer() - t0) > wait_ns) {
+      if (err) atomicOr(err, 1u);
+      if (done) return false;
+      break;
+    }
+    if (done) return true;
+  }
   for (int i = 0; i < (1 << 22); ++i)
-    if (mbar_try_wait(mbar, parity)) return true;
-  if (err) atomicOr(err, 1u);
+    if (mbar_try_wait(mbar, parity)) return false;
+  if (err) atomicOr(err, 2u);
   return false;
 }
 
@@ -182,6 +203,7 @@ struct TcMlp {
   uint32_t tmem, mbar[kTcGroupsMax], phase[kTcGroupsMax];
   int groups;
   unsigned int *err;
+  double wait_ns;
 };
 
 // Shared memory needed by one CTA of `groups` row groups (tiles + biases + mbarrier + TMEM slot).
@@ -214,6 +236,7 @@ __device__ __forceinline__ void tc_setup(TcMlp &T, unsigned char *smem, const Su
   for (int i = tid; i < 64 + 64 + 16; i += blockDim.x) bias[i] = (i < 128 + 3) ? sv.bias[i] : 0.0f;
   T.bias = bias;
   T.err = sv.err;
+  T.wait_ns = sv.wait_ns;
   for (int g = 0; g < kTcGroupsMax; ++g) {
     T.mbar[g] = smem_addr(mb + g);
     T.phase[g] = 0;
@@ -258,7 +281,7 @@ __device__ __forceinline__ bool tc_layer(TcMlp &T, int g, const unsigned char *c
     }
     tc_commit(T.mbar[g]);
   }
-  bool ok = mbar_wait_bounded(T.mbar[g], T.phase[g], T.err);
+  bool ok = mbar_wait_bounded(T.mbar[g], T.phase[g], T.err, T.wait_ns);
   T.phase[g] ^= 1u;
   tc_fence_after();
   return ok;

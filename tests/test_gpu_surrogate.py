@@ -155,6 +155,29 @@ def test_surrogate_spectrum_within_tolerance(trained_weights, case, n_s, seed):
     assert st["n_emit"] == ro["stats"]["n_emit"]
 
 
+def test_tensor_core_wait_limit_times_out_and_context_recovers(trained_weights):
+    """A 1 ns limit (mc_set_wait_limit) on the network's tensor-core completion waits makes them run
+    out while the products still complete: mc_run must end with MC_ERR_TIMEOUT, and the same context
+    must run to the unlimited result once the default limit is back."""
+    from paper_2602_13198_gb300 import mc
+    p, g = synth.torus(n1=64, n2=32)
+    m = mc.Model(p, precision="mixed", surrogate=True)
+    m.surrogate_weights(trained_weights)
+    m.set_grid(g)
+    ref = m.run(2e4, 3)
+    rspec = m.spectrum_sums().copy()
+    m.set_wait_limit(1e-9)
+    with pytest.raises(mc.MCError) as e:
+        m.run(2e4, 3)
+    assert e.value.code == -4                  # MC_ERR_TIMEOUT
+    m.set_wait_limit(120.0)
+    st = m.run(2e4, 3)
+    assert (st["n_emit"], st["n_child"], st["n_rec"]) == (ref["n_emit"], ref["n_child"], ref["n_rec"])
+    s = m.spectrum_sums()
+    assert np.array_equal(s[..., 2], rspec[..., 2])
+    assert np.allclose(s[..., :2], rspec[..., :2], rtol=1e-11, atol=0)
+
+
 def test_batched_surrogate_speed_against_batched_mixed(trained_weights):
     """Timed on the GPU: a 12-model survey slice batched in mixed precision with and without the
     network in the in-grid phase (autotuned, graph replay, CUDA events).  The network form is recorded
