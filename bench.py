@@ -91,11 +91,13 @@ def ops_pass(spin):
 GEN_LAUNCHES = 7          # zone prep, weight partials, weight final, counts, 3 scan kernels
 FLOP_SUR_EVAL = 2.0 * (3 * 64 + 64 * 64 + 64 * 3)   # one 3-64-64-3 network evaluation (algorithmic)
 # The mixed-precision forms run the geodesic in double-float on the FP32 pipes.  FP32 flops per
-# FP64-equivalent operation of the hand count, from the library's double-float arithmetic: an
-# addition is 20 (two two-sums, two fast two-sums, two additions), a product 10 (a product, three
-# FMAs at 2, a fast two-sum); the geodesic's mix of the two averages about 15 (an estimate: the ncu
-# pipe figures below are the measured counterpart).
-DF_FLOPS_PER_OP = 15.0
+# FP64-equivalent operation of the hand count, from the library's double-float arithmetic (FMA = 2):
+# a term of a one-pass sum of products (a product and an addition, 2 operations) is 15 (a product,
+# three FMAs, a two-sum, two additions), 7.5 per operation; a separate Dekker sum is 11 and a separate
+# product 10.  The geodesic's accelerations, Verlet updates and metric body are sums of products, the
+# rest separate sums and products: about 9 per operation (an estimate; the ncu pipe figures below are
+# the measured counterpart).
+DF_FLOPS_PER_OP = 9.0
 
 # DRAM bytes (read + write) per superphoton handed to the in-grid kernel, from ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch / superphotons it carried); traffic grows
@@ -270,7 +272,8 @@ def split_roofline(st, spin, fp64_peak, kernel, phase="in_grid"):
 
 def df_roofline(st, spin, fp32_peak, fp64_peak, kernel, phase="in_grid"):
     """Double-float kernel against the measured FP32 peak.  achieved = FP64-equivalent geodesic
-    operations x DF_FLOPS_PER_OP (an estimate); the ncu-measured FP32-pipe busy fraction sits beside it."""
+    operations x DF_FLOPS_PER_OP (an estimate from the library's double-float arithmetic); the ncu-measured
+    FP32-pipe busy fraction sits beside it."""
     if phase == "in_grid":
         ops = ops_geodesic_step(spin) * st["n_steps_grid"] + ops_pass(spin) * st["n_iters_grid"]
         sec = st["grid_ms"] / 1e3
