@@ -88,8 +88,9 @@ typedef struct mc_model_params {
   int32_t scatter;     /* 0: Compton scattering off */
   /* --- execution (not part of the physics) --- */
   int32_t precision;   /* MC_PREC_FP64: everything FP64; MC_PREC_MIXED: geodesics at FP64-level accuracy in
-                          double-float (FP32 pairs, 48-bit significand), plasma coefficients in FP32;
-                          emission, Compton kinematics, optical depths and weights stay FP64;
+                          double-float (FP32 pairs, 48-bit significand); plasma coefficients, optical
+                          depths, weights (carried relative to each superphoton's FP64 birth weight)
+                          and the scattering decision in FP32; emission and Compton kinematics FP64;
                           MC_PREC_SPLIT: geodesic and step size in FP64; plasma coefficients, optical
                           depths, weights (carried relative to each superphoton's FP64 birth weight),
                           the scattering decision and the Compton kinematics in FP32; emission

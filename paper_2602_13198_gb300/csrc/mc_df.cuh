@@ -105,6 +105,9 @@ __device__ __forceinline__ float narrow_f(double d) {
 }
 __device__ __forceinline__ float to_f(double x) { return (float)x; }
 __device__ __forceinline__ float to_f(df x) { return __fadd_rn(x.hi, x.lo); }
+// a geodesic scalar in FP32 without an FP64-pipe conversion: narrowed on the integer pipes, or hi + lo
+__device__ __forceinline__ float step_f(double x) { return narrow_f(x); }
+__device__ __forceinline__ float step_f(df x) { return __fadd_rn(x.hi, x.lo); }
 __device__ __forceinline__ double sabs(double x) { return fabs(x); }
 __device__ __forceinline__ df sabs(df x) { return df_abs(x); }
 __device__ __forceinline__ double srcp(double x) { return 1.0 / x; }

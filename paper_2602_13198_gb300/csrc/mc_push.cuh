@@ -13,13 +13,14 @@ namespace mcgb {
 // Precision forms of the transport.  S: the geodesic scalar; W: the weight, optical-depth and
 // coefficient scalar; C32: FP32 plasma coefficients; K32: FP32 Compton kinematics.
 //   0 plain FP64: every step in FP64;
-//   1 mixed: geodesic in double-float (FP64-level accuracy on the FP32 pipes), FP32 coefficients,
-//     FP64 weights and kinematics;
+//   1 mixed: geodesic in double-float (FP64-level accuracy on the FP32 pipes); FP32 coefficients,
+//     optical depths, weights (relative to the FP64 birth weight) and scattering decision; FP64
+//     Compton kinematics;
 //   2 split: FP64 geodesic and step size, FP32 coefficients, optical depths, weights (relative to the
 //     superphoton's FP64 birth weight), scattering decision and Compton kinematics.
 template <int PREC> struct Form;
 template <> struct Form<0> { using S = double; using W = double; static constexpr bool C32 = false, K32 = false; };
-template <> struct Form<1> { using S = df; using W = double; static constexpr bool C32 = true, K32 = false; };
+template <> struct Form<1> { using S = df; using W = float; static constexpr bool C32 = true, K32 = false; };
 template <> struct Form<2> { using S = double; using W = float; static constexpr bool C32 = true, K32 = true; };
 
 // Superphoton state.  The pool between phases holds FP64 (absolute weights); a transport kernel
@@ -449,10 +450,10 @@ static __device__ void write_log(const PushIO &io, const PhT<S, W> &p, int statu
 // update of one in-grid step, in the weight scalar W of the precision form.  X0, K0: the step's start.
 template <typename S, typename W>
 __device__ __forceinline__ void absorb_scatter(const DevModel &m, const PushIO &io, PhT<S, W> &p, const S X0[4],
-                                               const S K0[4], double dld, const CoefT<W> &c, bool scat, bool f32att,
-                                               LocalStats &ls) {
+                                               const S K0[4], S dls, const CoefT<W> &c, bool scat, LocalStats &ls) {
   if constexpr (std::is_same<W, float>::value) {
-    const float C = m.fCcoef, dl = narrow_f(dld);
+    // the step length in FP32: narrowed on the integer pipes (FP64), or hi + lo (double-float)
+    const float C = m.fCcoef, dl = step_f(dls);
     const float tau_a = 0.5f * (p.ana + c.ana) * C * dl;
     const float w0 = p.w;
     float wn = w0 * expf(-tau_a);
@@ -485,11 +486,10 @@ __device__ __forceinline__ void absorb_scatter(const DevModel &m, const PushIO &
     }
     p.w = wn;
   } else {
-    const double C = m.Ccoef;
+    const double C = m.Ccoef, dld = to_d(dls);
     double tau_a = 0.5 * (p.ana + c.ana) * C * dld;
     double w0 = p.w;
-    // attenuation factor: FP32 in the mixed-precision form (its coefficients are FP32 already)
-    double wn = w0 * (f32att ? (double)expf((float)-tau_a) : exp_t(m.ftab, -tau_a));
+    double wn = w0 * exp_t(m.ftab, -tau_a);
     if (scat) {
       double tau_s = 0.5 * (p.ans + c.ans) * C * dld;
       if (__double_as_longlong(tau_s) > 0) {   // tau_s > 0 (tau_s >= 0)
@@ -607,7 +607,7 @@ static __device__ bool step(const DevModel &m, const PushIO &io, PhF<PREC> &p, L
   ls.steps++;
   CoefT<W> c;
   coefs<Form<PREC>::C32>(m, G, p.X, p.K, scat, c);
-  absorb_scatter(m, io, p, X0, K0, to_d(dl), c, scat, PREC == 1, ls);
+  absorb_scatter(m, io, p, X0, K0, dl, c, scat, ls);
   const int rt = at_record(m, G.r) ? 1 : (at_capture(m, G.r) ? 3 : 0);
   return terminate(m, io, G, p, rt, ls) == 0;
 }
@@ -750,7 +750,7 @@ __device__ __forceinline__ void load_ph(const Pool &P, int64_t i, PhT<S, W> &p, 
 template <typename S>
 struct SurCarry {
   S X0[4], K0[4];
-  double dl;
+  S dl;
   int term;   // radius test at the step end: 1 recording sphere reached, 3 captured, 0 neither
   CoefA a;
 };
@@ -799,7 +799,7 @@ static __device__ void step_sur_a(const DevModel &m, PhT<S, W> &p, SurCarry<S> &
   if (!conv) ls.nonconv++;
   p.nsteps++;
   ls.steps++;
-  sc.dl = to_d(dl);
+  sc.dl = dl;
   // only the radius tests cross the network evaluation (the metric is re-evaluated to record)
   sc.term = at_record(m, G.r) ? 1 : (at_capture(m, G.r) ? 3 : 0);
   coefficients32_a(m, G, p.X, p.K, sc.a);
@@ -812,7 +812,7 @@ static __device__ bool step_sur_b(const DevModel &m, const PushIO &io, PhF<PREC>
   const bool scat = m.scatter && p.nsc < m.n_sc_max;
   CoefT<W> c;
   coefficients32_b(m, sc.a, out, scat, c);
-  absorb_scatter(m, io, p, sc.X0, sc.K0, sc.dl, c, scat, true, ls);
+  absorb_scatter(m, io, p, sc.X0, sc.K0, sc.dl, c, scat, ls);
   if (sc.term == 1) {
     GeoT<typename Form<PREC>::S> G;
     metric_eval<false>(m, p.X[1], p.X[2], G);

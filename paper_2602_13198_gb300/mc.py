@@ -153,9 +153,10 @@ class Model:
     """One model context: ``Model(params, device=0)`` then ``set_grid`` and ``run``.
 
     ``precision="fp64"`` runs every step in FP64.  ``precision="mixed"`` runs the geodesic in
-    double-float on the FP32 pipes (FP64-level accuracy) and the plasma coefficients in FP32
-    (see ``precision`` in include/mc.h); ``surrogate=True`` (mixed only) takes K2, sigma_h and
-    the emissivity shape from the tensor-core network."""
+    double-float on the FP32 pipes (FP64-level accuracy) and the plasma coefficients, optical
+    depths and weights in FP32; ``precision="split"`` runs the geodesic in FP64 and the rest in
+    FP32 (see ``precision`` in include/mc.h); ``surrogate=True`` (mixed or split) takes K2,
+    sigma_h and the emissivity shape from the tensor-core network."""
 
     def __init__(self, params: dict, device: int = 0, precision: str = "fp64", use_torch_allocator: bool = True,
                  block: int = 0, ctas_per_sm: int = 0, surrogate: bool = False):
