@@ -103,7 +103,7 @@ DF_FLOPS_PER_OP = 9.0
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch / superphotons it carried); traffic grows
 # in proportion to the superphotons a launch carries.  Keyed by (workload, form); re-taken whenever
 # the kernel changes (profiles/ holds the summaries).
-TRAFFIC_B_PER_PH = {("c4", "fp64"): 6647.6}
+TRAFFIC_B_PER_PH = {("c4", "fp64"): 6641.8}
 # ncu-measured pipe utilisation of the double-float in-grid kernel (profiles/
 # k_push_mixed_ingrid_snapshot3d.md): FP32 and FP64 pipes busy, issue active.
 NCU_MIXED_FP32_PIPE = {"in_grid_fp32": 0.261, "in_grid_fp64": 0.227, "issue_active": 0.350,
