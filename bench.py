@@ -106,8 +106,8 @@ DF_FLOPS_PER_OP = 9.0
 TRAFFIC_B_PER_PH = {("c4", "fp64"): 6641.8}
 # ncu-measured pipe utilisation of the double-float in-grid kernel (profiles/
 # k_push_mixed_ingrid_snapshot3d.md): FP32 and FP64 pipes busy, issue active.
-NCU_MIXED_FP32_PIPE = {"in_grid_fp32": 0.261, "in_grid_fp64": 0.227, "issue_active": 0.350,
-                       "source": "ncu, 3-D snapshot N_s=4e6, k_push_mixed<0,1> at 8 CTAs/SM"}
+NCU_MIXED_FP32_PIPE = {"in_grid_fp32": 0.257, "in_grid_fp64": 0.159, "issue_active": 0.370,
+                       "source": "ncu, 3-D snapshot N_s=4e6, k_push_mixed<0,1> at 8 CTAs/SM, FP32 weights"}
 
 
 def log(*a):
