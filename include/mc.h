@@ -223,7 +223,7 @@ int mc_fma_peak(int device, int dtype, double *flops);
  * |x| < 80); 4, 5: sin(pi x), cos(pi x) in double-float (ref: CUDA sincospi).  Inputs 3-5 are split
  * to double-float first and results joined back to double.  6: e^x and 7: ln x by the table-driven
  * FP64 functions of the FP64 transport (ref: CUDA exp, log); 8, 9: their sin(pi x), cos(pi x) (ref:
- * CUDA sincospi).  x, y, ref are n host doubles (caller-owned).  Errors: INVALID_ARG, NO_DEVICE, CUDA. */
+ * CUDA sincospi); 10: their e^x - 1 (ref: CUDA expm1).  x, y, ref are n host doubles (caller-owned).  Errors: INVALID_ARG, NO_DEVICE, CUDA. */
 int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t n);
 
 /* Zone superphoton counts for (N_s, seed) -- the same numbers mc_run computes and

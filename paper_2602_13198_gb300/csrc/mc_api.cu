@@ -843,7 +843,7 @@ int mc_get_bias_scales(mc_ctx *c, double *scales, int n) {
 }
 
 int mc_selftest_math(int which, const double *x, double *y, double *ref, int64_t n) {
-  if (which < 0 || which > 9 || n < 0 || (n > 0 && (!x || !y || !ref))) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
+  if (which < 0 || which > 10 || n < 0 || (n > 0 && (!x || !y || !ref))) return fail(nullptr, MC_ERR_INVALID_ARG, "bad argument");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();

@@ -107,6 +107,27 @@ __device__ __forceinline__ double exp_t(const double *T, double x) {
   return __hiloint2double(__double2hiint(y) + ((n >> 5) << 20), __double2loint(y));
 }
 
+// e^x - 1: for |x| < 1/4 its Taylor series to x^12 (truncation below 1e-17 relative), by Horner in
+// FP64; otherwise e^x - 1 from exp_t, where the subtraction costs at most ~2.2 bits (e^x / |e^x - 1|
+// < 4.5 for |x| >= 1/4).  Outside (-708, 708) exp_t takes CUDA's exp, which gives -1 and +inf at the
+// ends as expm1 does.
+__device__ __forceinline__ double expm1_t(const double *T, double x) {
+  if ((__double_as_longlong(x) & 0x7fffffffffffffffLL) < 0x3FD0000000000000LL) {   // |x| < 1/4 (NaN fails)
+    double q = fma(x, 1.0 / 479001600.0, 1.0 / 39916800.0);   // 1/12!, 1/11!
+    q = fma(q, x, 1.0 / 3628800.0);
+    q = fma(q, x, 1.0 / 362880.0);
+    q = fma(q, x, 1.0 / 40320.0);
+    q = fma(q, x, 1.0 / 5040.0);
+    q = fma(q, x, 1.0 / 720.0);
+    q = fma(q, x, 1.0 / 120.0);
+    q = fma(q, x, 1.0 / 24.0);
+    q = fma(q, x, 1.0 / 6.0);
+    q = fma(q, x, 0.5);
+    return fma(q, x * x, x);
+  }
+  return exp_t(T, x) - 1.0;
+}
+
 // log x = e ln2 + log c + log(1 + r): x = 2^e m, m in [1, 2), c = 1 + j/128 from the top 7 mantissa bits
 // (so m - c is exact), r = (m - c)/c with 1/c from the table, log(1 + r) by its series to r^9
 // (|r| < 1/128).  Accurate to ~1 ulp away from x = 1 and to ~2e-16 absolute near it.  Non-positive,
@@ -1134,7 +1155,7 @@ __device__ __forceinline__ void coefficients64(const DevModel &m, const Geo &G, 
         // B_nu = 2 h nu^3 / (c^2 expm1(h nu / k T)), h nu / k T = eps / Theta_e:
         // nu alpha_nu = (sqrt2 pi e^2 c / 6h) n_e (G / K2) expm1(eps/Theta) nu_s / nu^2
         const double C1 = 1.4142135623730951 * kPI * kEE * kEE * kCL / (6.0 * kHPL) / (kNuEps * kNuEps);
-        c.ana = C1 * P.ne * GoK * expm1(eps * P.ith) * nus * (ieps * ieps);
+        c.ana = C1 * P.ne * GoK * expm1_t(m.ftab, eps * P.ith) * nus * (ieps * ieps);
       }
     }
   }

@@ -506,6 +506,11 @@ __global__ void k_selftest_math(int which, const double *x, double *y, double *r
     ref[i] = log(v);
     return;
   }
+  if (which == 10) {
+    y[i] = expm1_t(F, v);
+    ref[i] = expm1(v);
+    return;
+  }
   if (which == 8 || which == 9) {
     double s, c, rs, rc;
     sincospi_t(F, v, s, c);

@@ -82,6 +82,25 @@ def test_table_driven_exp_matches_cuda():
     assert y[-11] == 1.0 and np.array_equal(y[-5:], ref[-5:])
 
 
+def test_table_driven_expm1_matches_cuda():
+    mc = _mc()
+    rng = np.random.default_rng(14)
+    x = np.concatenate([rng.uniform(-0.25, 0.25, 200000), rng.uniform(-40.0, 40.0, 200000),
+                        10.0 ** rng.uniform(-300, -1, 50000) * rng.choice([-1.0, 1.0], 50000),
+                        np.linspace(0.2499, 0.2501, 2001), np.linspace(-0.2501, -0.2499, 2001),
+                        np.array([0.0, -0.0, 0.25, -0.25, 1e-300, 700.0, -700.0, -800.0, 800.0])])
+    y, ref = mc.selftest_math(10, x)
+    fin = np.isfinite(ref) & (ref != 0.0)
+    rel = np.abs(y[fin] / ref[fin] - 1.0)
+    # the series below |x| = 1/4 within 3 ulp of CUDA's expm1; above it e^x - 1 from exp_t (within
+    # 3 ulp of CUDA's exp) loses at most ~2.2 bits to the subtraction: 3 ulp x 4.5 < 3e-15
+    small = np.abs(x[fin]) < 0.25
+    assert rel[small].max() <= 3 * 2.2e-16, rel[small].max()
+    assert rel[~small].max() <= 3e-15, rel[~small].max()
+    assert y[-9] == 0.0 and y[-8] == 0.0 and y[-5] == 1e-300
+    assert y[-2] == -1.0 and np.isinf(y[-1]) and y[-1] > 0
+
+
 def test_table_driven_log_matches_cuda():
     mc = _mc()
     rng = np.random.default_rng(12)
