@@ -634,6 +634,21 @@ def main():
                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                                  "sample": "first %d primaries (%d superphotons) of the same shard, %.1f s"
                                            % (n1, u_1, dt1)}}
+        del om
+        # the oracle on the other configurations' workloads (bounded samples, all cores), beside the
+        # device forms of the same jobs
+        per = {}
+        for cname, (pc, gc), n_s in (("c3_torus_2d", synth.torus(), 1e7),
+                                     ("c2_scattering_sphere_tau_0.1", synth.scattering_sphere(1e-1), 1e7),
+                                     ("c1_thin_sphere", synth.sphere("ks"), 1e5)):
+            omc = oracle.Model(pc, gc)
+            totc = omc.prepare(n_s, 1)
+            rc, uc, dtc, nc = oracle_sample(omc, totc, 0, totc, 3.0, cores)
+            per[cname] = {"value": rc, "unit": UNIT, "cores": cores,
+                          "sample": "first %d primaries (%d superphotons) of the seed-1 job at N_s = %.0e, %.1f s"
+                                    % (nc, uc, n_s, dtc)}
+            del omc
+        cpu["per_config"] = per
 
     forms = None
     if world == 1 and not args.no_forms and args.main_precision == "fp64":
