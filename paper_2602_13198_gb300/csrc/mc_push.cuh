@@ -81,31 +81,148 @@ static __device__ void init_transport(const DevModel &m, Ph &p) {
 
 // Emission of primary uid (section 2.3) at the centre of its zone: frequency proposed from the
 // piecewise-linear interpolant of the zone's dN/dln(nu) node values, weighted back to the exact one.
-static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &ls) {
+// In three parts, so that the frequency rejection can also run warp-cooperatively (emit_warp): the
+// zone and its emission data, the frequency draw, and the rest (direction, tetrad, wavevector, weight).
+constexpr int kMaxRej = 100000;   // proposals per rejection loop before the draw is taken as it stands
+
+struct EmitZone {
+  int64_t z;
+  double pref, lnuc, gm;
+};
+
+__device__ __forceinline__ EmitZone emit_zone(const DevModel &m, int64_t uid) {
   int64_t lo = 0, hi = m.nz - 1;
   while (lo < hi) {
     int64_t mid = (lo + hi + 1) >> 1;
     if (__ldg(m.start + mid) <= uid) lo = mid;
     else hi = mid - 1;
   }
-  const int64_t z = lo;
+  return {lo, m.zpref[lo], m.zlnuc[lo], m.zgmax[lo]};
+}
+
+// Proposal k of the frequency rejection from stream positions n and n + 1 (n = n0 + 2k): ln nu uniform
+// over the table, accepted when r2 gm < g_lin(ln nu).
+__device__ __forceinline__ bool nu_proposal(const DevModel &m, const EmitZone &Z, Rng &s, double &lnu, double &glin) {
+  double r1 = rng_u(s, m.seed);
+  lnu = m.lnu_min + r1 * m.dlntot;
+  double fj = (lnu - m.lnu_min) / m.dlnu;
+  int j = min(max((int)floor(fj), 0), m.n_nu - 2);
+  double fr = fj - j;
+  double g0 = zone_E(m, Z.z, Z.pref, Z.lnuc, j) * m.winv[j];
+  double g1 = zone_E(m, Z.z, Z.pref, Z.lnuc, j + 1) * m.winv[j + 1];
+  glin = (1.0 - fr) * g0 + fr * g1;
+  double r2 = rng_u(s, m.seed);
+  return r2 * Z.gm < glin;
+}
+
+static __device__ void emit_finish(const DevModel &m, const EmitZone &Z, double lnu, double glin, Ph &p,
+                                   LocalStats &ls);
+
+static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &ls) {
+  const EmitZone Z = emit_zone(m, uid);
   rng_init(p.s, (uint64_t)uid, 0u);
-  const double pref = m.zpref[z], lnuc = m.zlnuc[z], gm = m.zgmax[z];
   double lnu = m.lnu_min, glin = 0.0;
   int it;
-  for (it = 0; it < 100000; ++it) {
-    double r1 = rng_u(p.s, m.seed);
-    lnu = m.lnu_min + r1 * m.dlntot;
-    double fj = (lnu - m.lnu_min) / m.dlnu;
-    int j = min(max((int)floor(fj), 0), m.n_nu - 2);
-    double fr = fj - j;
-    double g0 = zone_E(m, z, pref, lnuc, j) * m.winv[j];
-    double g1 = zone_E(m, z, pref, lnuc, j + 1) * m.winv[j + 1];
-    glin = (1.0 - fr) * g0 + fr * g1;
-    double r2 = rng_u(p.s, m.seed);
-    if (r2 * gm < glin) break;
+  for (it = 0; it < kMaxRej; ++it)
+    if (nu_proposal(m, Z, p.s, lnu, glin)) break;
+  if (it == kMaxRej) ls.rejcap++;
+  emit_finish(m, Z, lnu, glin, p, ls);
+}
+
+// The frequency rejection of the 32 superphotons of a warp at once; every lane of the warp calls it
+// (have = false: the lane has no superphoton).  Sequentially, superphoton i evaluates its proposals
+// k = 0, 1, ... from its own stream positions and takes the first accepted one.  Here each round hands
+// the next proposals of the p pending superphotons to all 32 lanes (lane L evaluates proposal k0 + L/p
+// of the (L mod p)-th pending superphoton, whose zone data and stream it reads by shuffles), and each
+// superphoton takes its lowest accepted proposal of the round.  Draws, the accepted proposal, ln nu,
+// g_lin and the stream position afterwards are those of the sequential loop (the stream is counter
+// based); the lanes no longer wait for a warp's slowest acceptance.  Proposals past the first accepted
+// one are evaluated and dropped.
+static __device__ void emit_nu_warp(const DevModel &m, bool have, const EmitZone &Z, uint64_t id, uint32_t &n,
+                                    double &lnu_out, double &glin_out, LocalStats &ls) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  bool done = !have;
+  int it = 0;   // proposals of this lane's superphoton evaluated so far
+  lnu_out = m.lnu_min;
+  glin_out = 0.0;
+  while (true) {
+    const unsigned P = __ballot_sync(FULL, !done);
+    if (!P) break;
+    const int np = __popc(P);
+    const int rank = lane % np, k = lane / np;
+    unsigned rest = P;   // the lane of the rank-th pending superphoton: drop the rank lowest set bits
+    for (int i = 0; i < rank; ++i) rest &= rest - 1u;
+    const int owner = __ffs(rest) - 1;
+    EmitZone Zo;
+    Zo.z = __shfl_sync(FULL, Z.z, owner);
+    Zo.pref = __shfl_sync(FULL, Z.pref, owner);
+    Zo.lnuc = __shfl_sync(FULL, Z.lnuc, owner);
+    Zo.gm = __shfl_sync(FULL, Z.gm, owner);
+    const uint64_t ido = __shfl_sync(FULL, id, owner);
+    const uint32_t no = __shfl_sync(FULL, n, owner);
+    const int ito = __shfl_sync(FULL, it, owner);
+    const bool valid = ito + k < kMaxRej;
+    bool acc = false;
+    double lnu = 0.0, glin = 0.0;
+    if (valid) {
+      Rng s;
+      rng_init(s, ido, no + 2u * (uint32_t)k);
+      acc = nu_proposal(m, Zo, s, lnu, glin);
+    }
+    // lanes working for the same superphoton; its proposals rise with the lane index
+    const unsigned grp = __match_any_sync(FULL, owner);
+    const unsigned A = __ballot_sync(FULL, acc) & grp, V = __ballot_sync(FULL, valid) & grp;
+    const int win = A ? __ffs(A) - 1 : -1;
+    const int last = V ? 31 - __clz(V) : -1;
+    const int cnt = __popc(V);
+    // the pending lane of rank r reads the result of its group, whose first lane is lane r
+    const int myrank = __popc(P & ((1u << lane) - 1u));
+    const int src = (!done) ? myrank : lane;
+    const int win_o = __shfl_sync(FULL, win, src);
+    const int last_o = __shfl_sync(FULL, last, src);
+    const int cnt_o = __shfl_sync(FULL, cnt, src);
+    const int pick = win_o >= 0 ? win_o : (last_o >= 0 ? last_o : lane);
+    const double lnu_p = __shfl_sync(FULL, lnu, pick), glin_p = __shfl_sync(FULL, glin, pick);
+    if (!done) {
+      if (win_o >= 0) {
+        const int kw = (win_o - myrank) / np;
+        n += 2u * (uint32_t)(kw + 1);
+        lnu_out = lnu_p;
+        glin_out = glin_p;
+        done = true;
+      } else {
+        n += 2u * (uint32_t)cnt_o;
+        it += cnt_o;
+        if (it >= kMaxRej) {   // the sequential loop's cap: its last proposal stands
+          lnu_out = lnu_p;
+          glin_out = glin_p;
+          ls.rejcap++;
+          done = true;
+        }
+      }
+    }
   }
-  if (it == 100000) ls.rejcap++;
+}
+
+// Emission for the 32 lanes of a warp (every lane calls it; have = false: no superphoton): the same
+// superphoton states as emit(), with the frequency rejection run warp-cooperatively.
+static __device__ void emit_warp(const DevModel &m, bool have, int64_t uid, Ph &p, LocalStats &ls) {
+  EmitZone Z = {0, 0.0, 0.0, 1.0};
+  if (have) Z = emit_zone(m, uid);
+  uint32_t n = 0u;
+  double lnu, glin;
+  emit_nu_warp(m, have, Z, (uint64_t)uid, n, lnu, glin, ls);
+  if (!have) return;
+  rng_init(p.s, (uint64_t)uid, n);
+  emit_finish(m, Z, lnu, glin, p, ls);
+}
+
+static __device__ void emit_finish(const DevModel &m, const EmitZone &Z, double lnu, double glin, Ph &p,
+                                   LocalStats &ls) {
+  const int64_t z = Z.z;
+  const double pref = Z.pref, lnuc = Z.lnuc;
+  int it;
   const double jsyn = (pref == 0.0) ? 0.0
                       : (m.kappa > 0.0) ? pref * kap_interp(m.kapI, lnu - lnuc, m.zlnw[z])
                                         : pref * F_of_lnK(m, lnu - lnuc);
@@ -119,7 +236,7 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
     // kappa: accept with j(theta)/j(pi/2) = sin(th) J(X / sin th, w) / J(X, w), X = nu / nu_B
     const double lX = lnu - lnuc, lw = m.zlnw[z];
     const double jmax = kap_interp(m.kapJ, lX, lw);
-    for (it = 0; it < 100000; ++it) {
+    for (it = 0; it < kMaxRej; ++it) {
       double r3 = rng_u(p.s, m.seed);
       cth = 2.0 * r3 - 1.0;
       double r4 = rng_u(p.s, m.seed);
@@ -127,19 +244,19 @@ static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &l
       double jt = sth > 0.0 ? sth * kap_interp(m.kapJ, lX - log(sth), lw) : 0.0;
       if (r4 * jmax < jt) break;
     }
-    if (it == 100000) ls.rejcap++;
+    if (it == kMaxRej) ls.rejcap++;
   } else if (synchrotron) {
     // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
     double K0 = exp_t(m.ftab, lnu - lnuc);
     double jmax = Gsyn_t(m.ftab, K0);
-    for (it = 0; it < 100000; ++it) {
+    for (it = 0; it < kMaxRej; ++it) {
       double r3 = rng_u(p.s, m.seed);
       cth = 2.0 * r3 - 1.0;
       double r4 = rng_u(p.s, m.seed);
       double sth = sqrt(1.0 - cth * cth);
       if (r4 * jmax < sth * Gsyn_t(m.ftab, K0 / sth)) break;
     }
-    if (it == 100000) ls.rejcap++;
+    if (it == kMaxRej) ls.rejcap++;
   } else {
     cth = 2.0 * rng_u(p.s, m.seed) - 1.0;
   }

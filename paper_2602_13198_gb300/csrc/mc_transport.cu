@@ -19,7 +19,8 @@
 #include "mc_push.cuh"
 
 namespace mcgb {
-// Emission or child loading + transport initialisation, one item per thread (grid-stride).
+// Emission or child loading + transport initialisation, one item per thread (grid-stride; the trip
+// count is warp-uniform, so a warp's lanes reach the cooperative frequency rejection together).
 template <int PREC, bool KERR>
 __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
   LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -28,15 +29,14 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_round; idx += stride) {
     const bool have = idx < io.n_items;
     bool grid_phase = false;
+    Ph p;
+    if (io.mode != 2) {   // emission: every lane of the warp takes part in the frequency rejection
+      const int64_t uid = !have ? 0 : (io.mode == 1) ? io.uids[idx] : io.uid0 + idx;
+      emit_warp(m, have, uid, p, ls);
+      if (have) ls.emit++;
+    }
     if (have) {
-      Ph p;
-      if (io.mode == 2) {
-        load_child<Form<PREC>::K32>(m, io.in, idx, p, ls);
-      } else {
-        int64_t uid = (io.mode == 1) ? io.uids[idx] : io.uid0 + idx;
-        emit(m, uid, p, ls);
-        ls.emit++;
-      }
+      if (io.mode == 2) load_child<Form<PREC>::K32>(m, io.in, idx, p, ls);
       p.model = 0;
       init_transport<Form<PREC>::C32, KERR>(m, p);
       save_ph(io.pool, idx, p);
