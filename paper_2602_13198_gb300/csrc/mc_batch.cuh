@@ -209,19 +209,20 @@ __global__ void __launch_bounds__(SUR ? 128 * kTcGroupsMax : 128, MINB) k_batch(
       for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n_round; idx += stride) {
         const bool have = idx < n_items;
         bool gp = false;
+        Ph p;
+        if (g == 0) {   // emission: every lane of the warp takes part in the frequency rejection
+          int lo = 0, hi = b.n_models - 1;
+          while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (soff[mid] <= idx) lo = mid;
+            else hi = mid - 1;
+          }
+          p.model = lo;
+          emit_warp<true>(sm[0], sm, have, lo, have ? idx - soff[lo] : 0, p, ls);
+          if (have) ls.emit++;
+        }
         if (have) {
-          Ph p;
-          if (g == 0) {
-            int lo = 0, hi = b.n_models - 1;
-            while (lo < hi) {
-              int mid = (lo + hi + 1) >> 1;
-              if (soff[mid] <= idx) lo = mid;
-              else hi = mid - 1;
-            }
-            p.model = lo;
-            emit(sm[lo], idx - soff[lo], p, ls);
-            ls.emit++;
-          } else {
+          if (g != 0) {
             p.model = qin.model[idx];
             load_child<Form<PREC>::K32>(sm[p.model], qin, idx, p, ls);
           }

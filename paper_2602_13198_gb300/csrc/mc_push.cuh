@@ -81,8 +81,8 @@ static __device__ void init_transport(const DevModel &m, Ph &p) {
 
 // Emission of primary uid (section 2.3) at the centre of its zone: frequency proposed from the
 // piecewise-linear interpolant of the zone's dN/dln(nu) node values, weighted back to the exact one.
-// In three parts, so that the frequency rejection can also run warp-cooperatively (emit_warp): the
-// zone and its emission data, the frequency draw, and the rest (direction, tetrad, wavevector, weight).
+// In three parts: the zone and its emission data, the frequency rejection (run warp-cooperatively,
+// emit_nu_warp), and the rest (direction, tetrad, wavevector, weight; emit_finish).
 constexpr int kMaxRej = 100000;   // proposals per rejection loop before the draw is taken as it stands
 
 struct EmitZone {
@@ -118,33 +118,26 @@ __device__ __forceinline__ bool nu_proposal(const DevModel &m, const EmitZone &Z
 static __device__ void emit_finish(const DevModel &m, const EmitZone &Z, double lnu, double glin, Ph &p,
                                    LocalStats &ls);
 
-static __device__ void emit(const DevModel &m, int64_t uid, Ph &p, LocalStats &ls) {
-  const EmitZone Z = emit_zone(m, uid);
-  rng_init(p.s, (uint64_t)uid, 0u);
-  double lnu = m.lnu_min, glin = 0.0;
-  int it;
-  for (it = 0; it < kMaxRej; ++it)
-    if (nu_proposal(m, Z, p.s, lnu, glin)) break;
-  if (it == kMaxRej) ls.rejcap++;
-  emit_finish(m, Z, lnu, glin, p, ls);
-}
-
 // The frequency rejection of the 32 superphotons of a warp at once; every lane of the warp calls it
-// (have = false: the lane has no superphoton).  Sequentially, superphoton i evaluates its proposals
-// k = 0, 1, ... from its own stream positions and takes the first accepted one.  Here each round hands
+// (have = false: the lane has no superphoton).  Sequentially (as the method states it, and as a lane
+// alone would run it), superphoton i evaluates its proposals k = 0, 1, ... from its own stream
+// positions and takes the first accepted one.  Here each round hands
 // the next proposals of the p pending superphotons to all 32 lanes (lane L evaluates proposal k0 + L/p
 // of the (L mod p)-th pending superphoton, whose zone data and stream it reads by shuffles), and each
 // superphoton takes its lowest accepted proposal of the round.  Draws, the accepted proposal, ln nu,
 // g_lin and the stream position afterwards are those of the sequential loop (the stream is counter
 // based); the lanes no longer wait for a warp's slowest acceptance.  Proposals past the first accepted
 // one are evaluated and dropped.
-static __device__ void emit_nu_warp(const DevModel &m, bool have, const EmitZone &Z, uint64_t id, uint32_t &n,
-                                    double &lnu_out, double &glin_out, LocalStats &ls) {
+// BATCH: the superphotons of a warp may belong to different models of a batched run (sm[model]);
+// otherwise every one belongs to m.
+template <bool BATCH>
+static __device__ void emit_nu_warp(const DevModel &m, const DevModel *sm, bool have, int model, const EmitZone &Z,
+                                    uint64_t id, uint32_t &n, double &lnu_out, double &glin_out, LocalStats &ls) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   bool done = !have;
   int it = 0;   // proposals of this lane's superphoton evaluated so far
-  lnu_out = m.lnu_min;
+  lnu_out = 0.0;
   glin_out = 0.0;
   while (true) {
     const unsigned P = __ballot_sync(FULL, !done);
@@ -162,13 +155,15 @@ static __device__ void emit_nu_warp(const DevModel &m, bool have, const EmitZone
     const uint64_t ido = __shfl_sync(FULL, id, owner);
     const uint32_t no = __shfl_sync(FULL, n, owner);
     const int ito = __shfl_sync(FULL, it, owner);
+    const int mo = BATCH ? __shfl_sync(FULL, model, owner) : 0;
     const bool valid = ito + k < kMaxRej;
     bool acc = false;
     double lnu = 0.0, glin = 0.0;
     if (valid) {
       Rng s;
       rng_init(s, ido, no + 2u * (uint32_t)k);
-      acc = nu_proposal(m, Zo, s, lnu, glin);
+      if constexpr (BATCH) acc = nu_proposal(sm[mo], Zo, s, lnu, glin);
+      else acc = nu_proposal(m, Zo, s, lnu, glin);
     }
     // lanes working for the same superphoton; its proposals rise with the lane index
     const unsigned grp = __match_any_sync(FULL, owner);
@@ -205,17 +200,20 @@ static __device__ void emit_nu_warp(const DevModel &m, bool have, const EmitZone
   }
 }
 
-// Emission for the 32 lanes of a warp (every lane calls it; have = false: no superphoton): the same
-// superphoton states as emit(), with the frequency rejection run warp-cooperatively.
-static __device__ void emit_warp(const DevModel &m, bool have, int64_t uid, Ph &p, LocalStats &ls) {
+// Emission for the 32 lanes of a warp (every lane calls it; have = false: no superphoton).
+// BATCH: lane's superphoton belongs to model `model` of the batch descriptors sm (m is not read).
+template <bool BATCH = false>
+static __device__ void emit_warp(const DevModel &m, const DevModel *sm, bool have, int model, int64_t uid, Ph &p,
+                                 LocalStats &ls) {
+  const DevModel &mine = BATCH ? sm[have ? model : 0] : m;
   EmitZone Z = {0, 0.0, 0.0, 1.0};
-  if (have) Z = emit_zone(m, uid);
+  if (have) Z = emit_zone(mine, uid);
   uint32_t n = 0u;
   double lnu, glin;
-  emit_nu_warp(m, have, Z, (uint64_t)uid, n, lnu, glin, ls);
+  emit_nu_warp<BATCH>(m, sm, have, model, Z, (uint64_t)uid, n, lnu, glin, ls);
   if (!have) return;
   rng_init(p.s, (uint64_t)uid, n);
-  emit_finish(m, Z, lnu, glin, p, ls);
+  emit_finish(mine, Z, lnu, glin, p, ls);
 }
 
 static __device__ void emit_finish(const DevModel &m, const EmitZone &Z, double lnu, double glin, Ph &p,

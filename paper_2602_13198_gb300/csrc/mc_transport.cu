@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(128) k_init(DevModel m, InitIO io) {
     Ph p;
     if (io.mode != 2) {   // emission: every lane of the warp takes part in the frequency rejection
       const int64_t uid = !have ? 0 : (io.mode == 1) ? io.uids[idx] : io.uid0 + idx;
-      emit_warp(m, have, uid, p, ls);
+      emit_warp(m, nullptr, have, 0, uid, p, ls);
       if (have) ls.emit++;
     }
     if (have) {
