@@ -100,45 +100,28 @@ __device__ __forceinline__ EmitZone emit_zone(const DevModel &m, int64_t uid) {
   return {lo, m.zpref[lo], m.zlnuc[lo], m.zgmax[lo]};
 }
 
-// Proposal k of the frequency rejection from stream positions n and n + 1 (n = n0 + 2k): ln nu uniform
-// over the table, accepted when r2 gm < g_lin(ln nu).
-__device__ __forceinline__ bool nu_proposal(const DevModel &m, const EmitZone &Z, Rng &s, double &lnu, double &glin) {
-  double r1 = rng_u(s, m.seed);
-  lnu = m.lnu_min + r1 * m.dlntot;
-  double fj = (lnu - m.lnu_min) / m.dlnu;
-  int j = min(max((int)floor(fj), 0), m.n_nu - 2);
-  double fr = fj - j;
-  double g0 = zone_E(m, Z.z, Z.pref, Z.lnuc, j) * m.winv[j];
-  double g1 = zone_E(m, Z.z, Z.pref, Z.lnuc, j + 1) * m.winv[j + 1];
-  glin = (1.0 - fr) * g0 + fr * g1;
-  double r2 = rng_u(s, m.seed);
-  return r2 * Z.gm < glin;
-}
-
-static __device__ void emit_finish(const DevModel &m, const EmitZone &Z, double lnu, double glin, Ph &p,
-                                   LocalStats &ls);
-
-// The frequency rejection of the 32 superphotons of a warp at once; every lane of the warp calls it
-// (have = false: the lane has no superphoton).  Sequentially (as the method states it, and as a lane
-// alone would run it), superphoton i evaluates its proposals k = 0, 1, ... from its own stream
-// positions and takes the first accepted one.  Here each round hands
-// the next proposals of the p pending superphotons to all 32 lanes (lane L evaluates proposal k0 + L/p
-// of the (L mod p)-th pending superphoton, whose zone data and stream it reads by shuffles), and each
-// superphoton takes its lowest accepted proposal of the round.  Draws, the accepted proposal, ln nu,
-// g_lin and the stream position afterwards are those of the sequential loop (the stream is counter
-// based); the lanes no longer wait for a warp's slowest acceptance.  Proposals past the first accepted
-// one are evaluated and dropped.
-// BATCH: the superphotons of a warp may belong to different models of a batched run (sm[model]);
-// otherwise every one belongs to m.
-template <bool BATCH>
-static __device__ void emit_nu_warp(const DevModel &m, const DevModel *sm, bool have, int model, const EmitZone &Z,
-                                    uint64_t id, uint32_t &n, double &lnu_out, double &glin_out, LocalStats &ls) {
+// Warp-cooperative rejection sampling.  Sequentially (as the method states it, and as a lane alone
+// would run it), a superphoton evaluates proposals k = 0, 1, ... of a rejection loop, proposal k from
+// its own stream positions n0 + 2k and n0 + 2k + 1, and takes the first accepted one.  coop_reject
+// runs the loops of the 32 superphotons of a warp at once: each round hands the next proposals of the
+// p pending superphotons to all 32 lanes (lane L evaluates proposal k0 + L/p of the (L mod p)-th
+// pending superphoton, whose inputs and stream it reads by shuffles), and each superphoton takes its
+// lowest accepted proposal of the round.  The draws, the accepted proposal, its values and the stream
+// position afterwards are those of the sequential loop (the stream is counter based), with its cap of
+// kMaxRej proposals (the last one then stands); the lanes no longer wait for a warp's slowest
+// acceptance, and proposals past the first accepted one are evaluated and dropped.  Every lane of the
+// warp calls it (have = false: no loop for this lane).  Pol supplies the inputs Par, the result Val,
+// their shuffles and one proposal, eval(model, Par, stream, Val) -> accepted.  BATCH: the superphotons
+// of a warp may belong to different models of a batched run (sm[model]); otherwise every one belongs
+// to m.
+template <bool BATCH, typename Pol>
+static __device__ void coop_reject(const DevModel &m, const DevModel *sm, bool have, int model,
+                                   const typename Pol::Par &par, uint64_t id, uint32_t &n, typename Pol::Val &out,
+                                   LocalStats &ls) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   bool done = !have;
   int it = 0;   // proposals of this lane's superphoton evaluated so far
-  lnu_out = 0.0;
-  glin_out = 0.0;
   while (true) {
     const unsigned P = __ballot_sync(FULL, !done);
     if (!P) break;
@@ -147,23 +130,19 @@ static __device__ void emit_nu_warp(const DevModel &m, const DevModel *sm, bool 
     unsigned rest = P;   // the lane of the rank-th pending superphoton: drop the rank lowest set bits
     for (int i = 0; i < rank; ++i) rest &= rest - 1u;
     const int owner = __ffs(rest) - 1;
-    EmitZone Zo;
-    Zo.z = __shfl_sync(FULL, Z.z, owner);
-    Zo.pref = __shfl_sync(FULL, Z.pref, owner);
-    Zo.lnuc = __shfl_sync(FULL, Z.lnuc, owner);
-    Zo.gm = __shfl_sync(FULL, Z.gm, owner);
+    const typename Pol::Par po = Pol::shfl(par, owner);
     const uint64_t ido = __shfl_sync(FULL, id, owner);
     const uint32_t no = __shfl_sync(FULL, n, owner);
     const int ito = __shfl_sync(FULL, it, owner);
     const int mo = BATCH ? __shfl_sync(FULL, model, owner) : 0;
     const bool valid = ito + k < kMaxRej;
     bool acc = false;
-    double lnu = 0.0, glin = 0.0;
+    typename Pol::Val v = Pol::zero();
     if (valid) {
       Rng s;
       rng_init(s, ido, no + 2u * (uint32_t)k);
-      if constexpr (BATCH) acc = nu_proposal(sm[mo], Zo, s, lnu, glin);
-      else acc = nu_proposal(m, Zo, s, lnu, glin);
+      if constexpr (BATCH) acc = Pol::eval(sm[mo], po, s, v);
+      else acc = Pol::eval(m, po, s, v);
     }
     // lanes working for the same superphoton; its proposals rise with the lane index
     const unsigned grp = __match_any_sync(FULL, owner);
@@ -178,20 +157,18 @@ static __device__ void emit_nu_warp(const DevModel &m, const DevModel *sm, bool 
     const int last_o = __shfl_sync(FULL, last, src);
     const int cnt_o = __shfl_sync(FULL, cnt, src);
     const int pick = win_o >= 0 ? win_o : (last_o >= 0 ? last_o : lane);
-    const double lnu_p = __shfl_sync(FULL, lnu, pick), glin_p = __shfl_sync(FULL, glin, pick);
+    const typename Pol::Val vp = Pol::shfl(v, pick);
     if (!done) {
       if (win_o >= 0) {
         const int kw = (win_o - myrank) / np;
         n += 2u * (uint32_t)(kw + 1);
-        lnu_out = lnu_p;
-        glin_out = glin_p;
+        out = vp;
         done = true;
       } else {
         n += 2u * (uint32_t)cnt_o;
         it += cnt_o;
         if (it >= kMaxRej) {   // the sequential loop's cap: its last proposal stands
-          lnu_out = lnu_p;
-          glin_out = glin_p;
+          out = vp;
           ls.rejcap++;
           done = true;
         }
@@ -199,6 +176,84 @@ static __device__ void emit_nu_warp(const DevModel &m, const DevModel *sm, bool 
     }
   }
 }
+
+// Frequency proposal: ln nu uniform over the table (r1), accepted when r2 gm < g_lin(ln nu).
+struct NuPol {
+  using Par = EmitZone;
+  struct Val {
+    double lnu, glin;
+  };
+  __device__ static Val zero() { return {0.0, 0.0}; }
+  __device__ static Par shfl(const Par &p, int src) {
+    return {__shfl_sync(0xffffffffu, p.z, src), __shfl_sync(0xffffffffu, p.pref, src),
+            __shfl_sync(0xffffffffu, p.lnuc, src), __shfl_sync(0xffffffffu, p.gm, src)};
+  }
+  __device__ static Val shfl(const Val &v, int src) {
+    return {__shfl_sync(0xffffffffu, v.lnu, src), __shfl_sync(0xffffffffu, v.glin, src)};
+  }
+  __device__ static bool eval(const DevModel &m, const Par &Z, Rng &s, Val &v) {
+    double r1 = rng_u(s, m.seed);
+    v.lnu = m.lnu_min + r1 * m.dlntot;
+    double fj = (v.lnu - m.lnu_min) / m.dlnu;
+    int j = min(max((int)floor(fj), 0), m.n_nu - 2);
+    double fr = fj - j;
+    double g0 = zone_E(m, Z.z, Z.pref, Z.lnuc, j) * m.winv[j];
+    double g1 = zone_E(m, Z.z, Z.pref, Z.lnuc, j + 1) * m.winv[j + 1];
+    v.glin = (1.0 - fr) * g0 + fr * g1;
+    double r2 = rng_u(s, m.seed);
+    return r2 * Z.gm < v.glin;
+  }
+};
+
+// Direction relative to b, thermal synchrotron: cos(theta) uniform (r3), accepted with
+// j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c (r4 jmax < sin th G(K0 / sin th)).
+struct ThPol {
+  struct Par {
+    double K0, jmax;
+  };
+  struct Val {
+    double cth;
+  };
+  __device__ static Val zero() { return {0.0}; }
+  __device__ static Par shfl(const Par &p, int src) {
+    return {__shfl_sync(0xffffffffu, p.K0, src), __shfl_sync(0xffffffffu, p.jmax, src)};
+  }
+  __device__ static Val shfl(const Val &v, int src) { return {__shfl_sync(0xffffffffu, v.cth, src)}; }
+  __device__ static bool eval(const DevModel &m, const Par &q, Rng &s, Val &v) {
+    double r3 = rng_u(s, m.seed);
+    v.cth = 2.0 * r3 - 1.0;
+    double r4 = rng_u(s, m.seed);
+    double sth = sqrt(1.0 - v.cth * v.cth);
+    return r4 * q.jmax < sth * Gsyn_t(m.ftab, q.K0 / sth);
+  }
+};
+
+// Direction relative to b, kappa electrons: accepted with sin(th) J(X / sin th, w) / J(X, w), X = nu/nu_B.
+struct ThKPol {
+  struct Par {
+    double lX, lw, jmax;
+  };
+  struct Val {
+    double cth;
+  };
+  __device__ static Val zero() { return {0.0}; }
+  __device__ static Par shfl(const Par &p, int src) {
+    return {__shfl_sync(0xffffffffu, p.lX, src), __shfl_sync(0xffffffffu, p.lw, src),
+            __shfl_sync(0xffffffffu, p.jmax, src)};
+  }
+  __device__ static Val shfl(const Val &v, int src) { return {__shfl_sync(0xffffffffu, v.cth, src)}; }
+  __device__ static bool eval(const DevModel &m, const Par &q, Rng &s, Val &v) {
+    double r3 = rng_u(s, m.seed);
+    v.cth = 2.0 * r3 - 1.0;
+    double r4 = rng_u(s, m.seed);
+    double sth = sqrt(1.0 - v.cth * v.cth);
+    double jt = sth > 0.0 ? sth * kap_interp(m.kapJ, q.lX - log(sth), q.lw) : 0.0;
+    return r4 * q.jmax < jt;
+  }
+};
+
+static __device__ void emit_post(const DevModel &m, const EmitZone &Z, double lnu, double glin, double jsum,
+                                 double cth, Ph &p);
 
 // Emission for the 32 lanes of a warp (every lane calls it; have = false: no superphoton).
 // BATCH: lane's superphoton belongs to model `model` of the batch descriptors sm (m is not read).
@@ -209,55 +264,53 @@ static __device__ void emit_warp(const DevModel &m, const DevModel *sm, bool hav
   EmitZone Z = {0, 0.0, 0.0, 1.0};
   if (have) Z = emit_zone(mine, uid);
   uint32_t n = 0u;
-  double lnu, glin;
-  emit_nu_warp<BATCH>(m, sm, have, model, Z, (uint64_t)uid, n, lnu, glin, ls);
+  NuPol::Val nv = NuPol::zero();
+  coop_reject<BATCH, NuPol>(m, sm, have, model, Z, (uint64_t)uid, n, nv, ls);
+  const double lnu = nv.lnu, glin = nv.glin;
+  // the zone's emissivities at that frequency; with bremsstrahlung on, the process is drawn in
+  // proportion to the two angle-integrated emissivities (bremsstrahlung is isotropic)
+  double jsyn = 0.0, jbr = 0.0;
+  int kind = 0;   // direction: 0 isotropic, 1 thermal synchrotron, 2 kappa synchrotron
+  ThPol::Par tp = {1.0, 1.0};
+  ThKPol::Par kp = {0.0, 0.0, 1.0};
+  if (have) {
+    const int64_t z = Z.z;
+    const double pref = Z.pref, lnuc = Z.lnuc;
+    jsyn = (pref == 0.0) ? 0.0
+           : (mine.kappa > 0.0) ? pref * kap_interp(mine.kapI, lnu - lnuc, mine.zlnw[z])
+                                : pref * F_of_lnK(mine, lnu - lnuc);
+    jbr = (mine.brems && mine.zbq[z] > 0.0) ? mine.zbq[z] * exp_t(mine.ftab, -exp_t(mine.ftab, lnu) / mine.zbnt[z])
+                                            : 0.0;
+    bool synchrotron = true;
+    if (mine.brems) {
+      Rng s;
+      rng_init(s, (uint64_t)uid, n);
+      synchrotron = rng_u(s, mine.seed) * (jsyn + jbr) < jsyn;
+      n += 1u;
+    }
+    if (synchrotron && mine.kappa > 0.0) {
+      const double lX = lnu - lnuc, lw = mine.zlnw[z];
+      kp = {lX, lw, kap_interp(mine.kapJ, lX, lw)};
+      kind = 2;
+    } else if (synchrotron) {
+      const double K0 = exp_t(mine.ftab, lnu - lnuc);
+      tp = {K0, Gsyn_t(mine.ftab, K0)};
+      kind = 1;
+    }
+  }
+  ThPol::Val tv = ThPol::zero();
+  coop_reject<BATCH, ThPol>(m, sm, have && kind == 1, model, tp, (uint64_t)uid, n, tv, ls);
+  ThKPol::Val kv = ThKPol::zero();
+  coop_reject<BATCH, ThKPol>(m, sm, have && kind == 2, model, kp, (uint64_t)uid, n, kv, ls);
   if (!have) return;
   rng_init(p.s, (uint64_t)uid, n);
-  emit_finish(mine, Z, lnu, glin, p, ls);
+  double cth = kind == 1 ? tv.cth : kind == 2 ? kv.cth : 2.0 * rng_u(p.s, mine.seed) - 1.0;
+  emit_post(mine, Z, lnu, glin, jsyn + jbr, cth, p);
 }
 
-static __device__ void emit_finish(const DevModel &m, const EmitZone &Z, double lnu, double glin, Ph &p,
-                                   LocalStats &ls) {
+static __device__ void emit_post(const DevModel &m, const EmitZone &Z, double lnu, double glin, double jsum,
+                                 double cth, Ph &p) {
   const int64_t z = Z.z;
-  const double pref = Z.pref, lnuc = Z.lnuc;
-  int it;
-  const double jsyn = (pref == 0.0) ? 0.0
-                      : (m.kappa > 0.0) ? pref * kap_interp(m.kapI, lnu - lnuc, m.zlnw[z])
-                                        : pref * F_of_lnK(m, lnu - lnuc);
-  const double jbr = (m.brems && m.zbq[z] > 0.0) ? m.zbq[z] * exp_t(m.ftab, -exp_t(m.ftab, lnu) / m.zbnt[z]) : 0.0;
-  // with bremsstrahlung on, the process is drawn in proportion to the two angle-integrated
-  // emissivities; bremsstrahlung is isotropic
-  bool synchrotron = true;
-  if (m.brems) synchrotron = rng_u(p.s, m.seed) * (jsyn + jbr) < jsyn;
-  double cth = 0.0;
-  if (synchrotron && m.kappa > 0.0) {
-    // kappa: accept with j(theta)/j(pi/2) = sin(th) J(X / sin th, w) / J(X, w), X = nu / nu_B
-    const double lX = lnu - lnuc, lw = m.zlnw[z];
-    const double jmax = kap_interp(m.kapJ, lX, lw);
-    for (it = 0; it < kMaxRej; ++it) {
-      double r3 = rng_u(p.s, m.seed);
-      cth = 2.0 * r3 - 1.0;
-      double r4 = rng_u(p.s, m.seed);
-      double sth = sqrt(1.0 - cth * cth);
-      double jt = sth > 0.0 ? sth * kap_interp(m.kapJ, lX - log(sth), lw) : 0.0;
-      if (r4 * jmax < jt) break;
-    }
-    if (it == kMaxRej) ls.rejcap++;
-  } else if (synchrotron) {
-    // direction relative to b: accept with j(theta)/j(pi/2) = sin(th) G(K/sin th) / G(K), K = nu/nu_c
-    double K0 = exp_t(m.ftab, lnu - lnuc);
-    double jmax = Gsyn_t(m.ftab, K0);
-    for (it = 0; it < kMaxRej; ++it) {
-      double r3 = rng_u(p.s, m.seed);
-      cth = 2.0 * r3 - 1.0;
-      double r4 = rng_u(p.s, m.seed);
-      double sth = sqrt(1.0 - cth * cth);
-      if (r4 * jmax < sth * Gsyn_t(m.ftab, K0 / sth)) break;
-    }
-    if (it == kMaxRej) ls.rejcap++;
-  } else {
-    cth = 2.0 * rng_u(p.s, m.seed) - 1.0;
-  }
   double phi = 2.0 * rng_u(p.s, m.seed);   // units of pi
   double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
   double eps = exp_t(m.ftab, lnu) * (kHPL / (kME * kCL * kCL));
@@ -289,7 +342,7 @@ static __device__ void emit_finish(const DevModel &m, const EmitZone &Z, double 
   }
   // weight w(nu) g(nu) / g_lin(nu) = int dOmega j_nu(nu) / g_lin(nu): the proposal follows the
   // piecewise-linear target, the weight restores the zone's exact dN/dln(nu) (section 2.3)
-  p.w = glin > 0.0 ? (jsyn + jbr) / glin : 0.0;
+  p.w = glin > 0.0 ? jsum / glin : 0.0;
   p.nsc = 0;
 }
 
