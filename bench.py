@@ -331,9 +331,11 @@ def form_entry(st, ms, ref_value=None):
     return r
 
 
-def config_forms(name, p, g, jobs, spin, dim, dev, timer, flush, peaks, weights, ref=None, mixed_forms=True):
+def config_forms(name, p, g, jobs, spin, dim, dev, timer, flush, peaks, weights, ref=None, mixed_forms=True,
+                 oracle_sums=None):
     """Plain FP64 (unless ref = (stats, sums, ms) of it is given), mixed, and mixed + surrogate forms of one
-    configuration on the same jobs; spectrum errors against the plain FP64 sums of each seed."""
+    configuration on the same jobs; spectrum errors against the plain FP64 sums of each seed, and, when
+    oracle_sums (the oracle's sums of the seed-1 job) is given, against the oracle too."""
     import torch
     from paper_2602_13198_gb300 import mc
     fp64_peak, fp32_peak, hbm_peak, bf16_peak = peaks
@@ -348,6 +350,8 @@ def config_forms(name, p, g, jobs, spin, dim, dev, timer, flush, peaks, weights,
     e = form_entry(st0, ms0)
     e["roofline"] = fp64_roofline(st0, spin, dim, fp64_peak, "k_push_fp64<in-grid, %s>" % spin,
                                   TRAFFIC_B_PER_PH.get((name, "fp64")), hbm_peak)
+    if oracle_sums is not None and 1 in sums0:
+        e["spectrum_error_vs_oracle"] = error_block([(sums0[1], oracle_sums)])
     out["plain_fp64"] = e
     if not mixed_forms:
         return out
@@ -365,6 +369,8 @@ def config_forms(name, p, g, jobs, spin, dim, dev, timer, flush, peaks, weights,
         torch.cuda.empty_cache()
         e = form_entry(st, ms, out["plain_fp64"]["value"])
         e["spectrum_error"] = error_block([(sums[s], sums0[s]) for s in sums])
+        if oracle_sums is not None and 1 in sums:
+            e["spectrum_error_vs_oracle"] = error_block([(sums[1], oracle_sums)])
         if prec == "split":
             e["roofline"] = split_roofline(st, spin, fp64_peak, "k_push_%s<in-grid, %s> (FP64 geodesic, FP32 rest)"
                                            % ("sur" if sur else "split", spin))
@@ -616,6 +622,7 @@ def main():
                                  TRAFFIC_B_PER_PH.get(("c4", "fp64")), hbm_peak, fp32_peak)
 
     cpu = None
+    oracle_c1_spec = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -639,8 +646,7 @@ def main():
         # device forms of the same jobs
         per = {}
         for cname, (pc, gc), n_s in (("c3_torus_2d", synth.torus(), 1e7),
-                                     ("c2_scattering_sphere_tau_0.1", synth.scattering_sphere(1e-1), 1e7),
-                                     ("c1_thin_sphere", synth.sphere("ks"), 1e5)):
+                                     ("c2_scattering_sphere_tau_0.1", synth.scattering_sphere(1e-1), 1e7)):
             omc = oracle.Model(pc, gc)
             totc = omc.prepare(n_s, 1)
             rc, uc, dtc, nc = oracle_sample(omc, totc, 0, totc, 3.0, cores)
@@ -648,6 +654,18 @@ def main():
                           "sample": "first %d primaries (%d superphotons) of the seed-1 job at N_s = %.0e, %.1f s"
                                     % (nc, uc, n_s, dtc)}
             del omc
+        # the thin sphere's whole job (N_s = 1e5): its spectrum is also the oracle reference of the
+        # thin-sphere forms below
+        omc = oracle.Model(*synth.sphere("ks"))
+        omc.prepare(1e5, 1)
+        t0 = time.perf_counter()
+        rc1 = omc.run(nthreads=cores)
+        dtc = time.perf_counter() - t0
+        uc = rc1["stats"]["n_emit"] + rc1["stats"]["n_child"]
+        oracle_c1_spec = rc1["spec"]
+        per["c1_thin_sphere"] = {"value": uc / dtc, "unit": UNIT, "cores": cores,
+                                 "sample": "the whole seed-1 job at N_s = 1e5 (%d superphotons), %.1f s" % (uc, dtc)}
+        del omc
         cpu["per_config"] = per
 
     forms = None
@@ -702,7 +720,7 @@ def main():
         forms["c2_scattering_sphere"] = dict(agg, workload=WORKLOAD_C2)
         p1, g1 = synth.sphere("ks")
         forms["c1_thin_sphere"] = dict(config_forms("c1", p1, g1, [(1e5, 1, 0, 1)], "schw", 2, dev, timer, flush,
-                                                    peaks, weights), workload=WORKLOAD_C1)
+                                                    peaks, weights, oracle_sums=oracle_c1_spec), workload=WORKLOAD_C1)
         if not args.no_survey:
             forms["c5_survey"] = survey_forms(args, dev, timer, flush, peaks, weights)
 
