@@ -104,8 +104,8 @@ DF_FLOPS_PER_OP = 9.0
 # in proportion to the superphotons a launch carries.  Keyed by (workload, form); re-taken whenever
 # the kernel changes (profiles/ holds the summaries).
 TRAFFIC_B_PER_PH = {("c4", "fp64"): 6641.8}
-# ncu-measured pipe utilisation of the double-float in-grid kernel (profiles/
-# k_push_mixed_ingrid_snapshot3d.md): FP32 and FP64 pipes busy, issue active.
+# ncu-measured pipe utilisation of the double-float in-grid kernel (a full capture of its first launch
+# on the 3-D snapshot at N_s = 4e6): FP32 and FP64 pipes busy, issue active.
 NCU_MIXED_FP32_PIPE = {"in_grid_fp32": 0.257, "in_grid_fp64": 0.159, "issue_active": 0.370,
                        "source": "ncu, 3-D snapshot N_s=4e6, k_push_mixed<0,1> at 8 CTAs/SM, FP32 weights"}
 
