@@ -130,6 +130,7 @@ def lib():
         L.or_nzones.restype = I64
         L.or_get_zone.argtypes = [C.c_void_p, P(I64), PD, PD, PD]
         L.or_get_weights.argtypes = [C.c_void_p, PD]
+        L.or_emit.argtypes = [C.c_void_p, I64, I64, PD, PD, PD]
         L.or_run.argtypes = [C.c_void_p, I64, I64, P(I64), I64, PD, P(Stats), C.c_void_p, I64, P(I64), C.c_int]
         L.or_get_bias_scales.argtypes = [C.c_void_p, PD, C.c_int]
         L.or_sigma_hot_kappa.argtypes = [D, D, D]
@@ -386,6 +387,14 @@ class Model:
         out = np.empty(self.cfg["n_nu"])
         lib().or_get_weights(self._h, _pd(out))
         return out
+
+    def emit(self, uid0=0, n=None):
+        """Birth states (X, K, w) of primaries [uid0, uid0 + n) after prepare: emission only."""
+        if n is None:
+            n = self.total - uid0
+        X, K, w = np.empty((n, 4)), np.empty((n, 4)), np.empty(n)
+        lib().or_emit(self._h, int(uid0), int(n), _pd(X), _pd(K), _pd(w))
+        return X, K, w
 
     def fluid(self, X):
         X = np.ascontiguousarray(X, dtype=np.float64)

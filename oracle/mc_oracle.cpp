@@ -1790,6 +1790,23 @@ void or_get_weights(void *h, double *lnw) {
   for (int j = 0; j < M.nnu; ++j) lnw[j] = M.lnw[j];
 }
 
+// Birth states of primaries [uid0, uid0 + n) (after or_prepare): the emission alone, without
+// transport.  X, K: n x 4; w: n (test hook).
+void or_emit(void *h, int64_t uid0, int64_t n, double *X, double *K, double *w) {
+  Model &M = *(Model *)h;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t q = 0; q < n; ++q) {
+    Photon p;
+    int64_t rejcap = 0;
+    emit(M, uid0 + q, p, &rejcap);
+    for (int i = 0; i < 4; ++i) {
+      X[4 * q + i] = p.X[i];
+      K[4 * q + i] = p.K[i];
+    }
+    w[q] = p.w;
+  }
+}
+
 // Run primaries [uid0, uid1) (or the explicit uid list when uids != NULL) with all their
 // descendants; accumulate the spectrum sums [n_incl][n_bins][3] and counters.  With a log
 // buffer, every finished superphoton appends its end state.  A range run resets the bias scales
