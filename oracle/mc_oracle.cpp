@@ -17,9 +17,12 @@
 // and u's projection orthogonal to the normal observer equal to U^i; b^mu against an independent
 // linear solve of b.u = 0, b^i u^t - b^t u^i = B^i; Theta_e at the beta -> infinity, beta = 1 and
 // beta -> 0 points of the temperature model; e_a.e_b = eta_ab with e_0 = u and e_3 = b/|b|; and a
-// primitive field linear in (x1, x2, x3) reproduced exactly, clamped and periodic as read.  No
-// function is "parity unpinned".  One composite result has no independent reference: the spectra
-// of the GRMHD-like tori, built from the pinned parts above.
+// primitive field linear in (x1, x2, x3) reproduced exactly, clamped and periodic as read.  The
+// emission on those tori (weights, zone counts, frequency sampling) is pinned by its sums: the
+// birth weights against the emitted photon number and weight x h nu against the emitted power,
+// both computed from the zone volumes and the synchrotron fit outside the oracle.  No function is
+// "parity unpinned".  The tori's recorded spectra, which add the transport, are built from these
+// pinned parts and compared between the oracle and the CUDA path.
 //
 // Build: g++ -O2 -std=c++17 -fopenmp -shared -fPIC mc_oracle.cpp -o libmc_oracle.so
 
